@@ -1,0 +1,69 @@
+"""Pins for the hybrid scheme (Alg. 3) in the oracle.
+
+* Prop. 3.12: with a connected partition graph the iterates converge to the
+  unique minimiser of Eq. (entropic-transport), here the brute-force global
+  Sinkhorn solution on an 8 x 8 grid;
+* the objective never increases along A, B and flow steps (Lemma 3.6, Prop. 3.10,
+  block coordinate descent);
+* every flow update has a non-positive optimal value (stationary flow feasible).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense
+from oracle.domdec import embed
+from oracle.hybrid import OracleDD
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_hybrid_converges_to_global_minimiser():
+    N, s = 8, 2
+    mu = synth.gaussian_mixture(N, 2, (0.1, 0.3), 1e-2, seed=10)
+    nu = synth.gaussian_mixture(N, 2, (0.1, 0.3), 1e-2, seed=11)
+    eps = 2.0 / N ** 2
+    pistar, _ = dense.global_sinkhorn(mu, nu, eps, 1.0 / N, tol=1e-13)
+    Estar = dense.objective(pistar, mu, nu, dense.cost_matrix(N, N, 1.0 / N), eps)
+    boxes = synth.boxes_from_coupling(mu.shape, s, *synth.knothe_rosenblatt(mu, nu))
+    o = OracleDD(mu, nu, eps, s, boxes=boxes, tol=1e-11)
+    g = o.geom
+    for _ in range(16):
+        a, b, f = o.step()
+    err = sum(np.abs(embed(o.boxes[i], 0, 0, N, N)
+                     - pistar[dense.cell_rows(g, i)].sum(axis=0).reshape(N, N)).sum() for i in range(g.nb))
+    assert err < 1e-7
+    assert abs(b["E"] - Estar) / Estar < 1e-9
+
+
+def test_objective_monotone_with_flow_updates():
+    N, s = 16, 2
+    mu = synth.four_bumps(N)
+    eps = 1.0 / N ** 2
+    boxes = synth.boxes_from_coupling(mu.shape, s, *synth.rotation_coupling(mu))
+    o = OracleDD(mu, mu, eps, s, boxes=boxes, tol=1e-10)
+    E = []
+    for _ in range(3):
+        a, b, f = o.step()
+        assert f["value"] <= 1e-16
+        E += [a["E"], b["E"]]
+    assert all(E[k + 1] <= E[k] + 1e-13 for k in range(len(E) - 1))
+    # the first flow update removes curl: a strictly negative optimal value
+    assert o.history[2][1] < -1e-4
+
+
+def test_golden_dd32_trajectory_regenerates():
+    """The stored trajectory was written by tests/golden/make_golden.py from the oracle only."""
+    path = os.path.join(GOLDEN, "dd32_k0.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    gold = json.load(open(path))
+    mu, nu, eps, p = synth.workload("dd32", 0)
+    o = OracleDD(mu, nu, eps, p["s"], tol=p["tol"])
+    a = o.iterate(0)
+    assert a["E"] == pytest.approx(gold["steps"][0]["E"], rel=1e-12)
+    assert max(a["iters"]) == gold["steps"][0]["iters_max"]
