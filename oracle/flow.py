@@ -66,7 +66,10 @@ def min_cost_flow(nbr, cbar, m):
     rows = np.concatenate([ii, nb + jj])
     A = sp.csr_matrix((np.ones(2 * na), (rows, np.concatenate([cols, cols]))), shape=(2 * nb, na))
     b = np.concatenate([m, m])
-    res = linprog(cbar[ii, kk], A_eq=A, b_eq=b, bounds=(0, None), method="highs")
+    # tight feasibility tolerances: HiGHS' defaults (1e-7) let flows go slightly
+    # negative, which violates w >= 0 of the flow definition (Section 3.1)
+    res = linprog(cbar[ii, kk], A_eq=A, b_eq=b, bounds=(0, None), method="highs-ds",
+                  options=dict(primal_feasibility_tolerance=1e-10, dual_feasibility_tolerance=1e-10))
     if res.status != 0:
         raise RuntimeError("min-cost flow LP failed: " + res.message)
     w = np.zeros((nb, 5))
