@@ -1,0 +1,218 @@
+/*
+ * ddflow.h - C ABI of the GB300 library for domain decomposition of entropic
+ * optimal transport with flow updates (Medina & Schmitzer, "Flow updates for
+ * domain decomposition of entropic optimal transport").
+ *
+ * The problem (Eq. entropic-transport): two probability measures mu, nu on the
+ * same N1 x N2 pixel grid with spacing h, squared-Euclidean cost
+ * c(x, y) = |x - y|^2, regularisation eps:
+ *     min_{pi in Pi(mu, nu)} <c, pi> + eps KL(pi | mu (x) nu).
+ * X is split into basic cells of cell_size x cell_size pixels (Def. 2.2); the
+ * composite partitions A and B group 2 x 2 basic cells, B shifted by one basic
+ * cell and truncated at the image border (Fig. 3). The state is the set of
+ * basic-cell Y-marginals nu_i (Eq. basic-cell-Y-marginal), each on its
+ * bounding box (Section A.1, "Bounding box representation").
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: DD_OK (0) or a negative DD_ERR_* code; dd_strerror() names it.
+ *  - Pointers are HOST pointers; the library copies inputs in and outputs out.
+ *    Outputs are caller-allocated. Where an entry point takes a `size_t* count`,
+ *    passing NULL for the data pointer only stores the required element count.
+ *  - Arrays are row-major. Pixel (p, q) has flat index p * N2 + q; basic cell
+ *    (bi, bj) has index i = bi * (N2 / cell_size) + bj.
+ *  - A box header is 4 int32: (o1, o2, h, w) = top-left pixel and extent; a box
+ *    with h = w = 0 is empty. Box data follow each other in cell order, each box
+ *    h x w row-major, without padding.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *    every device operation of a context is ordered on it.
+ *  - One context belongs to one host thread at a time; calls on the same
+ *    context are not re-entrant.
+ */
+#ifndef DDFLOW_H
+#define DDFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DD_OK 0
+#define DD_ERR_ARG (-1)     /* invalid argument                                   */
+#define DD_ERR_OOM (-2)     /* device or host allocation failed                   */
+#define DD_ERR_CUDA (-3)    /* a CUDA call failed                                 */
+#define DD_ERR_MAXITER (-4) /* a cell hit the Sinkhorn iteration cap (result is
+                               still exactly Y-feasible, its X error above tol)   */
+#define DD_ERR_STALL (-5)   /* reserved: FP32 stall detected                      */
+#define DD_ERR_FLOW (-6)    /* min-cost flow failed; the stationary flow was kept */
+#define DD_ERR_POOL (-7)    /* a bounding box exceeds what one cell kernel holds   */
+#define DD_ERR_STATE (-8)   /* call order violated (e.g. flow update first)       */
+
+#define DD_INIT_PRODUCT 0 /* initial plan mu (x) nu                              */
+#define DD_INIT_USER 1    /* initial plan given by dd_set_plan                    */
+
+#define DD_WARM_PREV 0 /* alpha_init = alpha of the previous solve on the same
+                          partition (Alg. 4 input), zero on the first solve        */
+#define DD_WARM_COLD 1 /* alpha_init = 0 for every solve                          */
+
+#define DD_FLAG_KEEP_PREBALANCE 1 /* keep the pre-balance basic marginals of the
+                                     last half-iteration for dd_get_prebalance     */
+
+typedef struct dd_grid {
+    int32_t N1, N2; /* pixels per axis                                          */
+    double h;       /* pixel spacing (cost uses h^2 (dp^2 + dq^2))               */
+} dd_grid;
+
+typedef struct dd_options {
+    double tol;          /* cell stop: L1 X-marginal error <= tol * mu(X_J); 1e-5 */
+    int32_t max_iter;    /* Sinkhorn iteration cap per cell solve; 100000         */
+    int32_t fixed_iters; /* > 0: exactly this many iterations per cell, no tol    */
+    double trunc;        /* entries below this are dropped after balancing; 1e-15 */
+    int32_t init_kind;   /* DD_INIT_PRODUCT or DD_INIT_USER                        */
+    int32_t warm;        /* DD_WARM_PREV or DD_WARM_COLD                           */
+    int32_t threads;     /* threads per cell solve (64..512); 0 = autotuned        */
+    int32_t flags;       /* DD_FLAG_*                                              */
+} dd_options;
+
+/* Statistics of one half-iteration (Alg. 4). */
+typedef struct dd_stats {
+    int32_t part;          /* 0 = A, 1 = B                                        */
+    int32_t ncell;         /* composite cells solved                              */
+    int32_t iters_max;     /* largest Sinkhorn iteration count                    */
+    int32_t n_maxiter;     /* cells that hit max_iter                             */
+    double iters_mean;     /* mean Sinkhorn iterations per cell                   */
+    double objective;      /* E = sum_J <alpha_J, r_J> + <beta_J, nu_J>, Prop. 2.1 */
+    double l1_x;           /* sum_J sum_x |r_J(x) - mu(x)| of the Gibbs cell plans */
+    double lse_terms;      /* log-sum-exp terms evaluated by the cell kernel      */
+    double ms_total;       /* device time of the half-iteration (ms)              */
+    double ms_cells;       /* device time of the fused cell kernel (ms)           */
+    int64_t stored_entries;/* entries of the output basic boxes                   */
+} dd_stats;
+
+/* Statistics of one flow update (Section 3.2, steps of Section 5.1). */
+typedef struct dd_flow_stats {
+    double value;        /* optimal value sum w_ij c_bar_ij (<= 0)                */
+    int32_t nonzero;     /* off-diagonal arcs with w_ij > 0                       */
+    int32_t pivots;      /* network-simplex pivots                                */
+    double moved;        /* sum_{i != j} w_ij                                     */
+    double ms_costs;     /* device time, edge costs (ms)                          */
+    double ms_solve;     /* host time, min-cost flow (ms)                         */
+    double ms_exchange;  /* device time, exchange + re-box (ms)                   */
+} dd_flow_stats;
+
+typedef struct dd_ctx dd_ctx;
+
+/* Fill `opt` with the defaults listed in dd_options. */
+void dd_default_options(dd_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* dd_strerror(int status);
+
+/*
+ * Create a context. mu, nu: N1*N2 float64, >= 0, each summing to 1 within
+ * 1e-12. eps > 0. cell_size must divide N1 and N2, give an even number of basic
+ * cells per axis, and every basic cell needs mu(X_i) > 0 (Def. 2.2). The
+ * initial plan is mu (x) nu (DD_INIT_PRODUCT) or the one passed next to
+ * dd_set_plan (DD_INIT_USER). opt may be NULL (defaults). On success *out owns
+ * device memory until dd_destroy. Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA.
+ */
+int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps, int cell_size,
+            const dd_options* opt, void* stream, dd_ctx** out);
+
+/*
+ * Replace the state by a user plan given as basic-cell Y-marginals: hdr is
+ * nbasic x 4 int32 box headers, data the packed float64 box contents, n their
+ * total count. The plan must be feasible: |nu_i| = mu(X_i) and sum_i nu_i = nu,
+ * each within 1e-12 (L1); otherwise DD_ERR_ARG. Resets the warm starts.
+ */
+int dd_set_plan(dd_ctx* ctx, const int32_t* hdr, const double* data, size_t n);
+
+/*
+ * One domain-decomposition half-iteration (Alg. 1 in the form of Alg. 4):
+ * BasicToComposite, the batched log-domain cell Sinkhorn solves, CompositeToBasic
+ * with <c, pi_i>, balancing, truncation. part = 0 (A), 1 (B) or -1 (the other
+ * partition than the last one; A first). st may be NULL. Returns DD_ERR_MAXITER
+ * if a cell hit max_iter (the state is still updated).
+ */
+int dd_iterate(dd_ctx* ctx, int part, dd_stats* st);
+
+/*
+ * One flow update (Def. 3.4 with product gluing candidates, Remark 3.8): edge
+ * costs Eq. (edge-cost), min-cost flow Eq. (MinCostFlow) solved on the host,
+ * exchange Eq. (flow-update-cell-marginals). Valid only directly after
+ * dd_iterate (DD_ERR_STATE otherwise). st may be NULL.
+ */
+int dd_flow_update(dd_ctx* ctx, dd_flow_stats* st);
+
+/*
+ * n hybrid iterations of Alg. 3 (A half-iteration, B half-iteration, flow
+ * update), replayed from one captured CUDA graph per iteration; the min-cost
+ * flow runs as a host node of the graph. Any of the stats pointers may be NULL;
+ * when given they receive the values of the LAST iteration.
+ */
+int dd_step(dd_ctx* ctx, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf);
+
+/* Basic-cell boxes of the current state: hdr (nbasic x 4), data (float64). */
+int dd_get_plan(dd_ctx* ctx, int32_t* hdr, double* data, size_t* count);
+
+/*
+ * Duals of the last solve on `part`: alpha on X (N1*N2 float64; every pixel
+ * belongs to exactly one composite cell) and beta per composite cell on its
+ * box (hdr ncell x 4, beta packed float64), both in the mu (x) nu convention of
+ * Prop. 2.1: pi_J = exp((alpha + beta - c) / eps) mu (x) nu. beta is -inf where
+ * nu_J = 0. Duals are defined up to (alpha + C_J, beta - C_J) per cell.
+ */
+int dd_get_duals(dd_ctx* ctx, int part, double* alpha, int32_t* hdr, double* beta, size_t* count);
+
+/* Composite Y-marginals nu_J (Eq. get-composite-cell-marginal) of the last solve on `part`. */
+int dd_get_composite(dd_ctx* ctx, int part, int32_t* hdr, double* data, size_t* count);
+
+/* Per-cell Sinkhorn iterations and L1 X errors of the last solve on `part` (ncell each). */
+int dd_get_cell_stats(dd_ctx* ctx, int part, int32_t* iters, double* err);
+
+/*
+ * Objective E and L1 X error of the last half-iteration (Prop. 2.1 / Section A.2),
+ * and the L1 Y error sum_y |sum_i nu_i(y) - nu(y)| of the current state. Any
+ * pointer may be NULL.
+ */
+int dd_get_objective(dd_ctx* ctx, double* E, double* l1_x, double* l1_y);
+
+/* Composite cells of `part`: members (ncell x 4 int32, -1 padded), *ncell. */
+int dd_get_partition(dd_ctx* ctx, int part, int32_t* members, int32_t* ncell);
+
+/* Neighbourhood set (Def. 3.1): nbasic x 5 int32 (self, -axis1, +axis1, -axis2, +axis2), -1 if none. */
+int dd_get_neighbours(dd_ctx* ctx, int32_t* nbr);
+
+/* Basic-cell quantities of the last half-iteration: D_i = <c, pi_i> (before
+ * balancing), mass |nu_i|, barycentre ybar_i (2) and variance V_i of nu_i / |nu_i|
+ * (after balancing); each nbasic float64 (ybar: nbasic x 2). NULL skips. */
+int dd_get_basic_moments(dd_ctx* ctx, double* D, double* mass, double* ybar, double* var);
+
+/* Edge costs c_bar (nbasic x 5) and flows w (nbasic x 5) of the last flow update. */
+int dd_get_flow(dd_ctx* ctx, double* cbar, double* w);
+
+/* With DD_FLAG_KEEP_PREBALANCE: the basic marginals of the last half-iteration
+ * right after CompositeToBasic (before balancing/truncation), each on its
+ * composite cell's box: hdr nbasic x 4, data packed float64. */
+int dd_get_prebalance(dd_ctx* ctx, int32_t* hdr, double* data, size_t* count);
+
+/*
+ * Host min-cost flow of Eq. (MinCostFlow) on the neighbourhood graph, exposed
+ * for testing; no GPU involved. n basic cells, nbr (n x 5, -1 = no arc), cbar
+ * (n x 5 costs), m (n masses > 0). Writes the flow w (n x 5) with
+ * sum_k w[i,k] = m_i and inflow m_j, and *value = sum w c_bar; *pivots may be
+ * NULL. Exact network simplex on masses scaled to integers (2^60 in total) and
+ * costs scaled to integers (2^40 at the largest |c_bar|).
+ */
+int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m, double* w,
+                     double* value, int32_t* pivots);
+
+/* Release every resource of the context (NULL is ignored). */
+void dd_destroy(dd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDFLOW_H */

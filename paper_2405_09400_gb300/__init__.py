@@ -1,0 +1,373 @@
+"""Python binding of the ddflow C ABI (include/ddflow.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``lib/libddflow.so`` (built in-tree by ``_build.build()``). Importing works
+without a GPU; creating a context needs one. There is no fallback: if the
+library is missing, every call raises.
+
+Functions keep the C names (dd_init, dd_iterate, dd_flow_update, dd_step,
+dd_get_plan, dd_get_duals, ...); ``DomDec`` bundles them around one context.
+Boxes are exchanged as ``(hdr, data)``: hdr an (nbasic, 4) int32 array of
+(o1, o2, h, w) and data the packed float64 box contents.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libddflow.so")
+
+DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_MAXITER = 0, -1, -2, -3, -4
+DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
+DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
+DD_WARM_PREV, DD_WARM_COLD = 0, 1
+DD_FLAG_KEEP_PREBALANCE = 1
+
+EXPORTS = [
+    "dd_default_options", "dd_strerror", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
+    "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
+    "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
+    "dd_min_cost_flow", "dd_destroy",
+]
+
+
+class dd_grid(C.Structure):
+    _fields_ = [("N1", C.c_int32), ("N2", C.c_int32), ("h", C.c_double)]
+
+
+class dd_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
+                ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32)]
+
+
+class dd_stats(C.Structure):
+    _fields_ = [("part", C.c_int32), ("ncell", C.c_int32), ("iters_max", C.c_int32), ("n_maxiter", C.c_int32),
+                ("iters_mean", C.c_double), ("objective", C.c_double), ("l1_x", C.c_double),
+                ("lse_terms", C.c_double), ("ms_total", C.c_double), ("ms_cells", C.c_double),
+                ("stored_entries", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class dd_flow_stats(C.Structure):
+    _fields_ = [("value", C.c_double), ("nonzero", C.c_int32), ("pivots", C.c_int32), ("moved", C.c_double),
+                ("ms_costs", C.c_double), ("ms_solve", C.c_double), ("ms_exchange", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lib = None
+P = C.POINTER
+_i32p, _f64p, _szp = P(C.c_int32), P(C.c_double), P(C.c_size_t)
+
+
+def load():
+    """Load lib/libddflow.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"ddflow library not built: {LIB_PATH} missing (run __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    sig = {
+        "dd_default_options": (None, [P(dd_options)]),
+        "dd_strerror": (C.c_char_p, [C.c_int]),
+        "dd_init": (C.c_int, [_f64p, _f64p, P(dd_grid), C.c_double, C.c_int, P(dd_options), vp, P(vp)]),
+        "dd_set_plan": (C.c_int, [vp, _i32p, _f64p, C.c_size_t]),
+        "dd_iterate": (C.c_int, [vp, C.c_int, P(dd_stats)]),
+        "dd_flow_update": (C.c_int, [vp, P(dd_flow_stats)]),
+        "dd_step": (C.c_int, [vp, C.c_int, P(dd_stats), P(dd_stats), P(dd_flow_stats)]),
+        "dd_get_plan": (C.c_int, [vp, _i32p, _f64p, _szp]),
+        "dd_get_duals": (C.c_int, [vp, C.c_int, _f64p, _i32p, _f64p, _szp]),
+        "dd_get_composite": (C.c_int, [vp, C.c_int, _i32p, _f64p, _szp]),
+        "dd_get_cell_stats": (C.c_int, [vp, C.c_int, _i32p, _f64p]),
+        "dd_get_objective": (C.c_int, [vp, _f64p, _f64p, _f64p]),
+        "dd_get_partition": (C.c_int, [vp, C.c_int, _i32p, _i32p]),
+        "dd_get_neighbours": (C.c_int, [vp, _i32p]),
+        "dd_get_basic_moments": (C.c_int, [vp, _f64p, _f64p, _f64p, _f64p]),
+        "dd_get_flow": (C.c_int, [vp, _f64p, _f64p]),
+        "dd_get_prebalance": (C.c_int, [vp, _i32p, _f64p, _szp]),
+        "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
+        "dd_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().dd_strerror(int(code)).decode()
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _check(code, where, ok=(DD_OK,)):
+    if code not in ok:
+        raise DDError(code, where)
+    return code
+
+
+def default_options(**kw) -> dd_options:
+    o = dd_options()
+    load().dd_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def current_stream():
+    """The raw handle of torch's current CUDA stream (None without torch/CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+# ---- C-named functions ------------------------------------------------------
+def dd_init(mu, nu, eps, cell_size, h=None, options=None, stream=None):
+    lib = load()
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    g = dd_grid(mu.shape[0], mu.shape[1], 1.0 / mu.shape[0] if h is None else h)
+    ctx = C.c_void_p()
+    opt = options if options is not None else default_options()
+    _check(lib.dd_init(_ptr(mu, _f64p), _ptr(nu, _f64p), C.byref(g), float(eps), int(cell_size), C.byref(opt),
+                       stream, C.byref(ctx)), "dd_init")
+    return ctx
+
+
+def dd_set_plan(ctx, hdr, data):
+    hdr = np.ascontiguousarray(hdr, dtype=np.int32)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    _check(load().dd_set_plan(ctx, _ptr(hdr, _i32p), _ptr(data, _f64p), data.size), "dd_set_plan")
+
+
+def dd_iterate(ctx, part=-1):
+    st = dd_stats()
+    rc = _check(load().dd_iterate(ctx, int(part), C.byref(st)), "dd_iterate", ok=(DD_OK, DD_ERR_MAXITER))
+    d = st.as_dict()
+    d["status"] = rc
+    return d
+
+
+def dd_flow_update(ctx):
+    st = dd_flow_stats()
+    rc = _check(load().dd_flow_update(ctx, C.byref(st)), "dd_flow_update", ok=(DD_OK, DD_ERR_FLOW))
+    d = st.as_dict()
+    d["status"] = rc
+    return d
+
+
+def dd_step(ctx, n=1, stats=True):
+    sa, sb, sf = dd_stats(), dd_flow_stats(), None
+    sb = dd_stats()
+    sf = dd_flow_stats()
+    if stats:
+        rc = load().dd_step(ctx, int(n), C.byref(sa), C.byref(sb), C.byref(sf))
+    else:
+        rc = load().dd_step(ctx, int(n), None, None, None)
+    _check(rc, "dd_step", ok=(DD_OK, DD_ERR_MAXITER, DD_ERR_FLOW))
+    return (sa.as_dict(), sb.as_dict(), sf.as_dict()) if stats else rc
+
+
+def _boxes_call(fn, ctx, nhdr, *lead):
+    cnt = C.c_size_t(0)
+    hdr = np.zeros((nhdr, 4), dtype=np.int32)
+    _check(fn(ctx, *lead, _ptr(hdr, _i32p), None, C.byref(cnt)), fn.__name__)
+    data = np.zeros(cnt.value, dtype=np.float64)
+    _check(fn(ctx, *lead, _ptr(hdr, _i32p), _ptr(data, _f64p), C.byref(cnt)), fn.__name__)
+    return hdr, data
+
+
+def dd_get_plan(ctx, nbasic):
+    return _boxes_call(load().dd_get_plan, ctx, nbasic)
+
+
+def dd_get_composite(ctx, part, ncell):
+    return _boxes_call(load().dd_get_composite, ctx, ncell, C.c_int(part))
+
+
+def dd_get_prebalance(ctx, nbasic):
+    return _boxes_call(load().dd_get_prebalance, ctx, nbasic)
+
+
+def dd_get_duals(ctx, part, shape, ncell):
+    lib = load()
+    cnt = C.c_size_t(0)
+    hdr = np.zeros((ncell, 4), dtype=np.int32)
+    _check(lib.dd_get_duals(ctx, int(part), None, _ptr(hdr, _i32p), None, C.byref(cnt)), "dd_get_duals")
+    alpha = np.zeros(shape, dtype=np.float64)
+    beta = np.zeros(cnt.value, dtype=np.float64)
+    _check(lib.dd_get_duals(ctx, int(part), _ptr(alpha, _f64p), _ptr(hdr, _i32p), _ptr(beta, _f64p), C.byref(cnt)),
+           "dd_get_duals")
+    return alpha, hdr, beta
+
+
+def dd_get_cell_stats(ctx, part, ncell):
+    it = np.zeros(ncell, dtype=np.int32)
+    er = np.zeros(ncell, dtype=np.float64)
+    _check(load().dd_get_cell_stats(ctx, int(part), _ptr(it, _i32p), _ptr(er, _f64p)), "dd_get_cell_stats")
+    return it, er
+
+
+def dd_get_objective(ctx):
+    E, lx, ly = C.c_double(), C.c_double(), C.c_double()
+    _check(load().dd_get_objective(ctx, C.byref(E), C.byref(lx), C.byref(ly)), "dd_get_objective")
+    return E.value, lx.value, ly.value
+
+
+def dd_get_partition(ctx, part):
+    n = C.c_int32()
+    _check(load().dd_get_partition(ctx, int(part), None, C.byref(n)), "dd_get_partition")
+    mem = np.zeros((n.value, 4), dtype=np.int32)
+    _check(load().dd_get_partition(ctx, int(part), _ptr(mem, _i32p), C.byref(n)), "dd_get_partition")
+    return mem
+
+
+def dd_get_neighbours(ctx, nbasic):
+    nbr = np.zeros((nbasic, 5), dtype=np.int32)
+    _check(load().dd_get_neighbours(ctx, _ptr(nbr, _i32p)), "dd_get_neighbours")
+    return nbr
+
+
+def dd_get_basic_moments(ctx, nbasic):
+    D, m, v = (np.zeros(nbasic) for _ in range(3))
+    yb = np.zeros((nbasic, 2))
+    _check(load().dd_get_basic_moments(ctx, _ptr(D, _f64p), _ptr(m, _f64p), _ptr(yb, _f64p), _ptr(v, _f64p)),
+           "dd_get_basic_moments")
+    return dict(D=D, mass=m, ybar=yb, var=v)
+
+
+def dd_get_flow(ctx, nbasic):
+    cb = np.zeros((nbasic, 5))
+    w = np.zeros((nbasic, 5))
+    _check(load().dd_get_flow(ctx, _ptr(cb, _f64p), _ptr(w, _f64p)), "dd_get_flow")
+    return cb, w
+
+
+def dd_min_cost_flow(nbr, cbar, m):
+    """Host network simplex for Eq. (MinCostFlow); returns (w, value, pivots)."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    cb = np.ascontiguousarray(np.where(nbr >= 0, np.nan_to_num(cbar), 0.0), dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    w = np.zeros((len(m), 5))
+    v, piv = C.c_double(), C.c_int32()
+    _check(load().dd_min_cost_flow(len(m), _ptr(nbr, _i32p), _ptr(cb, _f64p), _ptr(m, _f64p), _ptr(w, _f64p),
+                                   C.byref(v), C.byref(piv)), "dd_min_cost_flow")
+    return w, v.value, piv.value
+
+
+def dd_destroy(ctx):
+    if ctx:
+        load().dd_destroy(ctx)
+
+
+# ---- convenience wrapper -----------------------------------------------------
+def boxes_to_arrays(boxes):
+    """[(o1, o2, array), ...] -> (hdr (n, 4) int32, packed float64 data)."""
+    hdr = np.array([[b[0], b[1], b[2].shape[0], b[2].shape[1]] for b in boxes], dtype=np.int32).reshape(-1, 4)
+    data = np.concatenate([np.asarray(b[2], dtype=np.float64).reshape(-1) for b in boxes]) if boxes else np.zeros(0)
+    return hdr, data
+
+
+def arrays_to_boxes(hdr, data):
+    out, k = [], 0
+    for o1, o2, h, w in hdr:
+        n = int(h) * int(w)
+        out.append((int(o1), int(o2), data[k:k + n].reshape(int(h), int(w))))
+        k += n
+    return out
+
+
+class DomDec:
+    """One library context: DD half-iterations and flow updates on a grid problem."""
+
+    def __init__(self, mu, nu, eps, cell_size, boxes=None, h=None, stream=None, **opts):
+        mu = np.asarray(mu, dtype=np.float64)
+        self.shape = mu.shape
+        self.s = int(cell_size)
+        self.nbasic = (mu.shape[0] // self.s) * (mu.shape[1] // self.s)
+        if boxes is not None:
+            opts.setdefault("init_kind", DD_INIT_USER)
+        self.options = default_options(**opts)
+        self.ctx = dd_init(mu, nu, eps, cell_size, h=h, options=self.options,
+                           stream=stream if stream is not None else current_stream())
+        self.ncell = [len(dd_get_partition(self.ctx, p)) for p in (0, 1)]
+        if boxes is not None:
+            self.set_plan(boxes)
+
+    def set_plan(self, boxes):
+        hdr, data = boxes if isinstance(boxes, tuple) else boxes_to_arrays(boxes)
+        dd_set_plan(self.ctx, hdr, data)
+
+    def iterate(self, part=-1):
+        return dd_iterate(self.ctx, part)
+
+    def flow_update(self):
+        return dd_flow_update(self.ctx)
+
+    def step(self, n=1, stats=True):
+        return dd_step(self.ctx, n, stats)
+
+    def plan(self):
+        return arrays_to_boxes(*dd_get_plan(self.ctx, self.nbasic))
+
+    def composite(self, part):
+        return arrays_to_boxes(*dd_get_composite(self.ctx, part, self.ncell[part]))
+
+    def prebalance(self):
+        return arrays_to_boxes(*dd_get_prebalance(self.ctx, self.nbasic))
+
+    def duals(self, part):
+        alpha, hdr, beta = dd_get_duals(self.ctx, part, self.shape, self.ncell[part])
+        return alpha, arrays_to_boxes(hdr, beta)
+
+    def cell_stats(self, part):
+        return dd_get_cell_stats(self.ctx, part, self.ncell[part])
+
+    def objective(self):
+        return dd_get_objective(self.ctx)
+
+    def partition(self, part):
+        return dd_get_partition(self.ctx, part)
+
+    def neighbours(self):
+        return dd_get_neighbours(self.ctx, self.nbasic)
+
+    def basic_moments(self):
+        return dd_get_basic_moments(self.ctx, self.nbasic)
+
+    def flow(self):
+        return dd_get_flow(self.ctx, self.nbasic)
+
+    def close(self):
+        if self.ctx:
+            dd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,761 @@
+// Host side of the C ABI (include/ddflow.h): context set-up, device memory,
+// the half-iteration / flow-update drivers and the getters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dd_internal.h"
+
+#define CK(x)                                   \
+    do {                                        \
+        if ((x) != cudaSuccess) return DD_ERR_CUDA; \
+    } while (0)
+#define RET(x)                         \
+    do {                               \
+        int r_ = (x);                  \
+        if (r_ != DD_OK) return r_;    \
+    } while (0)
+
+namespace {
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+template <typename T>
+int dmalloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, sizeof(T) * n) == cudaSuccess ? DD_OK : DD_ERR_OOM;
+}
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+template <typename T>
+int h2d(T* d, const T* h, size_t n, cudaStream_t s) {
+    if (n == 0) return DD_OK;
+    return cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, s) == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+}
+template <typename T>
+int d2h(T* h, const T* d, size_t n, cudaStream_t s) {
+    if (n == 0) return DD_OK;
+    return cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+}
+
+int ensure_floats(float** p, size_t* cap, size_t need) {
+    if (*cap >= need && *p) return DD_OK;
+    dfree(*p);
+    size_t n = need + need / 4 + 4096;
+    RET(dmalloc(p, n));
+    *cap = n;
+    return DD_OK;
+}
+
+// build partitions (Def. 2.2 / Fig. 3): A cells 2x2, B cells shifted by one and truncated
+void build_part(dd_ctx* c, int part, std::vector<int32_t>& members, std::vector<int32_t>& xblk,
+                std::vector<double>& mJ) {
+    const int n1 = c->n1, n2 = c->n2, s = c->s;
+    const int na = part == 0 ? n1 / 2 : n1 / 2 + 1;
+    const int nbb = part == 0 ? n2 / 2 : n2 / 2 + 1;
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < nbb; ++b) {
+            int rows[2], cols[2], nr = 0, nc = 0;
+            for (int t = 0; t < 2; ++t) {
+                int r = part == 0 ? 2 * a + t : 2 * a - 1 + t;
+                int q = part == 0 ? 2 * b + t : 2 * b - 1 + t;
+                if (r >= 0 && r < n1) rows[nr++] = r;
+                if (q >= 0 && q < n2) cols[nc++] = q;
+            }
+            int32_t mem[4] = {-1, -1, -1, -1};
+            int k = 0;
+            double mass = 0.0;
+            for (int ri = 0; ri < nr; ++ri)
+                for (int ci = 0; ci < nc; ++ci) {
+                    int i = rows[ri] * n2 + cols[ci];
+                    mem[k++] = i;
+                    mass += c->h_m[i];
+                }
+            for (int t = 0; t < 4; ++t) members.push_back(mem[t]);
+            int32_t xb[XB_N] = {rows[0] * s, cols[0] * s, nr * s, nc * s, k, 0, 0, 0};
+            for (int t = 0; t < XB_N; ++t) xblk.push_back(xb[t]);
+            mJ.push_back(mass);
+        }
+}
+
+int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
+    const int nb = c->nb;
+    std::vector<int32_t> bh((size_t)BH_N * nb, 0);
+    size_t total = 0, src = 0;
+    for (int i = 0; i < nb; ++i) {
+        int h = hdr[4 * i + 2], w = hdr[4 * i + 3];
+        if (h < 0 || w < 0 || (h == 0) != (w == 0)) return DD_ERR_ARG;
+        int st = (w + 3) & ~3;
+        bh[BH_N * i + BH_O1] = h ? hdr[4 * i] : 0;
+        bh[BH_N * i + BH_O2] = h ? hdr[4 * i + 1] : 0;
+        bh[BH_N * i + BH_H] = h;
+        bh[BH_N * i + BH_W] = w;
+        bh[BH_N * i + BH_STRIDE] = st;
+        bh[BH_N * i + BH_START] = (int32_t)total;
+        total += (size_t)h * st;
+        src += (size_t)h * w;
+    }
+    if (src != n) return DD_ERR_ARG;
+    if (total > (size_t)INT32_MAX) return DD_ERR_POOL;
+    std::vector<float> buf(total, 0.f);
+    src = 0;
+    for (int i = 0; i < nb; ++i) {
+        int h = bh[BH_N * i + BH_H], w = bh[BH_N * i + BH_W], st = bh[BH_N * i + BH_STRIDE];
+        size_t s0 = bh[BH_N * i + BH_START];
+        for (int r = 0; r < h; ++r)
+            for (int q = 0; q < w; ++q) buf[s0 + (size_t)r * st + q] = (float)data[src++];
+    }
+    RET(ensure_floats(&c->pool[c->cur], &c->pool_cap[c->cur], total));
+    RET(h2d(c->pool[c->cur], buf.data(), total, c->stream));
+    RET(h2d(c->bhdr[c->cur], bh.data(), bh.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->part[0].warm_valid = c->part[1].warm_valid = false;
+    c->part[0].solved = c->part[1].solved = false;
+    c->flow_ready = false;
+    c->last_part = -1;
+    return DD_OK;
+}
+
+int validate_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
+    std::vector<double> ym((size_t)c->N1 * c->N2, 0.0);
+    size_t src = 0;
+    double xerr = 0.0;
+    for (int i = 0; i < c->nb; ++i) {
+        int o1 = hdr[4 * i], o2 = hdr[4 * i + 1], h = hdr[4 * i + 2], w = hdr[4 * i + 3];
+        if (h < 0 || w < 0 || (h == 0) != (w == 0)) return DD_ERR_ARG;
+        if (h && (o1 < 0 || o2 < 0 || o1 + h > c->N1 || o2 + w > c->N2)) return DD_ERR_ARG;
+        if (src + (size_t)h * w > n) return DD_ERR_ARG;
+        double mass = 0.0;
+        for (int r = 0; r < h; ++r)
+            for (int q = 0; q < w; ++q) {
+                double v = data[src++];
+                if (!(v >= 0.0) || !std::isfinite(v)) return DD_ERR_ARG;
+                mass += v;
+                ym[(size_t)(o1 + r) * c->N2 + o2 + q] += v;
+            }
+        xerr += std::fabs(mass - c->h_m[i]);
+    }
+    if (src != n) return DD_ERR_ARG;
+    double yerr = 0.0;
+    for (size_t k = 0; k < ym.size(); ++k) yerr += std::fabs(ym[k] - c->h_nu[k]);
+    if (xerr > 1e-12 || yerr > 1e-12) return DD_ERR_ARG;
+    return DD_OK;
+}
+
+int choose_threads(dd_ctx* c, long long maxarea) {
+    if (c->opt.threads > 0) return std::min(512, std::max(32, (c->opt.threads / 32) * 32));
+    return maxarea <= 1024 ? 128 : 256;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dd_default_options(dd_options* o) {
+    if (!o) return;
+    o->tol = 1e-5;
+    o->max_iter = 100000;
+    o->fixed_iters = 0;
+    o->trunc = 1e-15;
+    o->init_kind = DD_INIT_PRODUCT;
+    o->warm = DD_WARM_PREV;
+    o->threads = 0;
+    o->flags = 0;
+}
+
+const char* dd_strerror(int s) {
+    switch (s) {
+        case DD_OK: return "ok";
+        case DD_ERR_ARG: return "invalid argument";
+        case DD_ERR_OOM: return "out of memory";
+        case DD_ERR_CUDA: return "CUDA error";
+        case DD_ERR_MAXITER: return "Sinkhorn iteration cap reached in some cell";
+        case DD_ERR_STALL: return "FP32 stall";
+        case DD_ERR_FLOW: return "min-cost flow failed; stationary flow kept";
+        case DD_ERR_POOL: return "bounding box too large for the cell kernel";
+        case DD_ERR_STATE: return "call order violated";
+        default: return "unknown status";
+    }
+}
+
+void dd_destroy(dd_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    dfree(c->d_mu); dfree(c->d_nu); dfree(c->d_lgmu); dfree(c->d_m); dfree(c->d_xmom);
+    dfree(c->d_nbr); dfree(c->d_rev);
+    for (int p = 0; p < 2; ++p) {
+        DevPart& P = c->part[p];
+        dfree(P.members); dfree(P.xblk); dfree(P.mJ); dfree(P.chdr); dfree(P.alpha); dfree(P.gauge);
+        dfree(P.iters); dfree(P.err); dfree(P.Ecell); dfree(P.order); dfree(P.comp_b); dfree(P.comp_nu);
+        dfree(c->pool[p]); dfree(c->bhdr[p]);
+    }
+    dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
+    dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
+    if (c->h_tot) cudaFreeHost(c->h_tot);
+    if (c->h_cbar) cudaFreeHost(c->h_cbar);
+    if (c->h_w) cudaFreeHost(c->h_w);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps, int cell_size,
+            const dd_options* opt, void* stream, dd_ctx** out) {
+    if (!mu || !nu || !grid || !out) return DD_ERR_ARG;
+    *out = nullptr;
+    const int N1 = grid->N1, N2 = grid->N2, s = cell_size;
+    if (N1 <= 0 || N2 <= 0 || !(grid->h > 0) || !(eps > 0) || s <= 0 || N1 % s || N2 % s) return DD_ERR_ARG;
+    if ((N1 / s) % 2 || (N2 / s) % 2 || 2 * s > 16) return DD_ERR_ARG;
+    const size_t np = (size_t)N1 * N2;
+    double smu = 0, snu = 0;
+    for (size_t k = 0; k < np; ++k) {
+        if (!(mu[k] >= 0) || !(nu[k] >= 0) || !std::isfinite(mu[k]) || !std::isfinite(nu[k])) return DD_ERR_ARG;
+        smu += mu[k];
+        snu += nu[k];
+    }
+    if (std::fabs(smu - 1.0) > 1e-12 || std::fabs(snu - 1.0) > 1e-12) return DD_ERR_ARG;
+    dd_ctx* c = new (std::nothrow) dd_ctx();
+    if (!c) return DD_ERR_OOM;
+    if (opt) c->opt = *opt; else dd_default_options(&c->opt);
+    if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0)) { delete c; return DD_ERR_ARG; }
+    c->N1 = N1; c->N2 = N2; c->s = s; c->n1 = N1 / s; c->n2 = N2 / s; c->nb = c->n1 * c->n2;
+    c->amax = 4 * s * s;
+    c->h = grid->h; c->eps = eps;
+    c->k2 = (float)(grid->h * grid->h / eps / kLn2);
+    c->stream = (cudaStream_t)stream;
+    c->h_mu.assign(mu, mu + np);
+    c->h_nu.assign(nu, nu + np);
+    // basic masses and X moments (pixel units)
+    c->h_m.assign(c->nb, 0.0);
+    std::vector<double> xmom(3 * (size_t)c->nb, 0.0);
+    for (int i = 0; i < c->nb; ++i) {
+        int bi = i / c->n2, bj = i % c->n2;
+        double m = 0, m1 = 0, m2 = 0, q = 0;
+        for (int p = bi * s; p < bi * s + s; ++p)
+            for (int r = bj * s; r < bj * s + s; ++r) {
+                double v = mu[(size_t)p * N2 + r];
+                m += v; m1 += v * p; m2 += v * r;
+            }
+        if (!(m > 0)) { delete c; return DD_ERR_ARG; }
+        m1 /= m; m2 /= m;
+        for (int p = bi * s; p < bi * s + s; ++p)
+            for (int r = bj * s; r < bj * s + s; ++r) {
+                double v = mu[(size_t)p * N2 + r];
+                q += v * ((p - m1) * (p - m1) + (r - m2) * (r - m2));
+            }
+        c->h_m[i] = m;
+        xmom[3 * i] = m1; xmom[3 * i + 1] = m2; xmom[3 * i + 2] = q / m;
+    }
+    // neighbours (Def. 3.1): self, -axis1, +axis1, -axis2, +axis2
+    c->h_nbr.assign(5 * (size_t)c->nb, -1);
+    std::vector<int32_t> rev(5 * (size_t)c->nb, -1);
+    for (int i = 0; i < c->nb; ++i) {
+        int bi = i / c->n2, bj = i % c->n2;
+        c->h_nbr[5 * i] = i;
+        if (bi > 0) c->h_nbr[5 * i + 1] = i - c->n2;
+        if (bi < c->n1 - 1) c->h_nbr[5 * i + 2] = i + c->n2;
+        if (bj > 0) c->h_nbr[5 * i + 3] = i - 1;
+        if (bj < c->n2 - 1) c->h_nbr[5 * i + 4] = i + 1;
+    }
+    for (int j = 0; j < c->nb; ++j)
+        for (int k = 0; k < 5; ++k) {
+            int i = c->h_nbr[5 * j + k];
+            if (i < 0) continue;
+            for (int t = 0; t < 5; ++t)
+                if (c->h_nbr[5 * i + t] == j) rev[5 * j + k] = t;
+        }
+    int rc = DD_OK;
+#define TRY(x)                          \
+    do {                                \
+        rc = (x);                       \
+        if (rc != DD_OK) goto fail;     \
+    } while (0)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        c->dev = dev;
+        if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            rc = DD_ERR_CUDA;
+            goto fail;
+        }
+        std::vector<float> lgmu(np);
+        for (size_t k = 0; k < np; ++k) lgmu[k] = mu[k] > 0 ? (float)std::log2(mu[k]) : DD_NEG;
+        TRY(dmalloc(&c->d_mu, np)); TRY(h2d(c->d_mu, mu, np, c->stream));
+        TRY(dmalloc(&c->d_nu, np)); TRY(h2d(c->d_nu, nu, np, c->stream));
+        TRY(dmalloc(&c->d_lgmu, np)); TRY(h2d(c->d_lgmu, lgmu.data(), np, c->stream));
+        TRY(dmalloc(&c->d_m, c->nb)); TRY(h2d(c->d_m, c->h_m.data(), c->nb, c->stream));
+        TRY(dmalloc(&c->d_xmom, 3 * (size_t)c->nb)); TRY(h2d(c->d_xmom, xmom.data(), xmom.size(), c->stream));
+        TRY(dmalloc(&c->d_nbr, 5 * (size_t)c->nb)); TRY(h2d(c->d_nbr, c->h_nbr.data(), c->h_nbr.size(), c->stream));
+        TRY(dmalloc(&c->d_rev, 5 * (size_t)c->nb)); TRY(h2d(c->d_rev, rev.data(), rev.size(), c->stream));
+        for (int p = 0; p < 2; ++p) {
+            DevPart& P = c->part[p];
+            std::vector<int32_t> members, xblk;
+            std::vector<double> mJ;
+            build_part(c, p, members, xblk, mJ);
+            P.ncell = (int)mJ.size();
+            P.h_members = members;
+            P.h_xblk = xblk;
+            std::vector<int32_t> order(P.ncell);
+            for (int k = 0; k < P.ncell; ++k) order[k] = k;
+            TRY(dmalloc(&P.members, members.size())); TRY(h2d(P.members, members.data(), members.size(), c->stream));
+            TRY(dmalloc(&P.xblk, xblk.size())); TRY(h2d(P.xblk, xblk.data(), xblk.size(), c->stream));
+            TRY(dmalloc(&P.mJ, mJ.size())); TRY(h2d(P.mJ, mJ.data(), mJ.size(), c->stream));
+            TRY(dmalloc(&P.order, order.size())); TRY(h2d(P.order, order.data(), order.size(), c->stream));
+            TRY(dmalloc(&P.chdr, (size_t)CH_N * P.ncell));
+            TRY(dmalloc(&P.alpha, (size_t)c->amax * P.ncell));
+            TRY(dmalloc(&P.gauge, 2 * (size_t)P.ncell));
+            TRY(dmalloc(&P.iters, P.ncell));
+            TRY(dmalloc(&P.err, P.ncell));
+            TRY(dmalloc(&P.Ecell, P.ncell));
+            TRY(dmalloc(&c->bhdr[p], (size_t)BH_N * c->nb));
+        }
+        TRY(dmalloc(&c->d_bmom, (size_t)BM_N * c->nb));
+        TRY(dmalloc(&c->d_tot, PT_N));
+        if (cudaMallocHost((void**)&c->h_tot, sizeof(long long) * PT_N) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
+        TRY(dmalloc(&c->d_queue, 4));
+        TRY(dmalloc(&c->d_status, 8));
+        TRY(dmalloc(&c->d_cbar, 5 * (size_t)c->nb));
+        TRY(dmalloc(&c->d_w, 5 * (size_t)c->nb));
+        if (cudaMallocHost((void**)&c->h_cbar, sizeof(double) * 5 * c->nb) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
+        if (cudaMallocHost((void**)&c->h_w, sizeof(double) * 5 * c->nb) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
+        TRY(dmalloc(&c->d_xhdr, (size_t)CH_N * c->nb));
+        TRY(dmalloc(&c->d_yacc, np));
+        TRY(dmalloc(&c->d_red, 8));
+        for (auto& e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        if (c->opt.init_kind == DD_INIT_PRODUCT) {
+            // nu_i = m_i nu on the whole grid, truncated like every other state
+            std::vector<int32_t> hdr(4 * (size_t)c->nb);
+            std::vector<double> data;
+            data.reserve(np * c->nb);
+            for (int i = 0; i < c->nb; ++i) {
+                int lo1 = N1, hi1 = -1, lo2 = N2, hi2 = -1;
+                for (int p = 0; p < N1; ++p)
+                    for (int q = 0; q < N2; ++q)
+                        if (c->h_m[i] * nu[(size_t)p * N2 + q] >= c->opt.trunc && nu[(size_t)p * N2 + q] > 0) {
+                            lo1 = std::min(lo1, p); hi1 = std::max(hi1, p);
+                            lo2 = std::min(lo2, q); hi2 = std::max(hi2, q);
+                        }
+                if (hi1 < 0) { rc = DD_ERR_ARG; goto fail; }
+                hdr[4 * i] = lo1; hdr[4 * i + 1] = lo2; hdr[4 * i + 2] = hi1 - lo1 + 1; hdr[4 * i + 3] = hi2 - lo2 + 1;
+                for (int p = lo1; p <= hi1; ++p)
+                    for (int q = lo2; q <= hi2; ++q) {
+                        double v = c->h_m[i] * nu[(size_t)p * N2 + q];
+                        data.push_back(v >= c->opt.trunc ? v : 0.0);
+                    }
+            }
+            TRY(upload_plan(c, hdr.data(), data.data(), data.size()));
+        } else {
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        }
+    }
+#undef TRY
+    *out = c;
+    return DD_OK;
+fail:
+    dd_destroy(c);
+    return rc;
+}
+
+int dd_set_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
+    if (!c || !hdr || (!data && n)) return DD_ERR_ARG;
+    RET(validate_plan(c, hdr, data, n));
+    return upload_plan(c, hdr, data, n);
+}
+
+static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
+    DevPart& P = c->part[part];
+    std::vector<int32_t> it(P.ncell), ch((size_t)CH_N * P.ncell), xb;
+    std::vector<double> er(P.ncell), E(P.ncell);
+    RET(d2h(it.data(), P.iters, P.ncell, c->stream));
+    RET(d2h(er.data(), P.err, P.ncell, c->stream));
+    RET(d2h(E.data(), P.Ecell, P.ncell, c->stream));
+    RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
+    int status[8];
+    RET(d2h(status, c->d_status, 8, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double Es = 0, es = 0, im = 0, terms = 0;
+    int imax = 0;
+    for (int J = 0; J < P.ncell; ++J) {
+        Es += E[J];
+        es += er[J];
+        im += it[J];
+        imax = std::max(imax, it[J]);
+        // Sinkhorn terms per iteration: hx*wx*w + h*w*hx + h*wx*w + hx*wx*h
+        const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
+        const double hx = P.h_xblk[XB_N * J + XB_HX], wx = P.h_xblk[XB_N * J + XB_WX];
+        terms += (double)it[J] * (hx * wx * w + (double)h * w * hx + (double)h * wx * w + hx * wx * h);
+    }
+    c->last_E = Es;
+    c->last_l1x = es;
+    if (st) {
+        st->part = part;
+        st->ncell = P.ncell;
+        st->iters_max = imax;
+        st->iters_mean = P.ncell ? im / P.ncell : 0;
+        st->n_maxiter = status[0];
+        st->objective = Es;
+        st->l1_x = es;
+        st->lse_terms = terms;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]);
+        st->ms_total = ms;
+        cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+        st->ms_cells = ms;
+        std::vector<int32_t> bh((size_t)BH_N * c->nb);
+        RET(d2h(bh.data(), c->bhdr[c->cur], bh.size(), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        int64_t ent = 0;
+        for (int i = 0; i < c->nb; ++i) ent += (int64_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
+        st->stored_entries = ent;
+    }
+    return status[0] > 0 ? DD_ERR_MAXITER : DD_OK;
+}
+
+int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
+    if (!c) return DD_ERR_ARG;
+    if (part < -1 || part > 1) return DD_ERR_ARG;
+    if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
+    if (part == -1) part = c->last_part == 0 ? 1 : 0;
+    DevPart& P = c->part[part];
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    RET(launch_plan_half(c, part));
+    RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const long long comp = c->h_tot[PT_COMP], outn = c->h_tot[PT_OUT];
+    if (outn > (long long)INT32_MAX || comp > (long long)INT32_MAX * 4LL) return DD_ERR_POOL;
+    if (P.comp_cap < (size_t)comp || !P.comp_b) {
+        dfree(P.comp_b);
+        dfree(P.comp_nu);
+        size_t n = (size_t)comp + comp / 4 + 4096;
+        RET(dmalloc(&P.comp_b, n));
+        RET(dmalloc(&P.comp_nu, n));
+        P.comp_cap = n;
+    }
+    RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)outn));
+    if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(&c->d_pre, &c->pre_cap, (size_t)outn));
+    const size_t smem = half_smem_bytes(c, c->h_tot[PT_MAXAREA], c->h_tot[PT_MAXH], c->h_tot[PT_MAXW]);
+    if (smem > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+    const int threads = choose_threads(c, c->h_tot[PT_MAXAREA]);
+    int occ = half_occupancy(threads, smem);
+    if (occ < 1) occ = 1;
+    const int grid = std::max(1, std::min(P.ncell, c->nsm * occ));
+    CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    RET(launch_half(c, part, threads, smem, grid));
+    CK(cudaEventRecord(c->ev[2], c->stream));
+    c->cur = 1 - c->cur;
+    P.warm_valid = true;
+    P.solved = true;
+    c->last_part = part;
+    c->flow_ready = true;
+    return fill_stats(c, part, st);
+}
+
+int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
+    if (!c) return DD_ERR_ARG;
+    if (!c->flow_ready) return DD_ERR_STATE;
+    CK(cudaEventRecord(c->ev[3], c->stream));
+    RET(launch_cbar(c));
+    CK(cudaEventRecord(c->ev[4], c->stream));
+    RET(d2h(c->h_cbar, c->d_cbar, 5 * (size_t)c->nb, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    auto t0 = std::chrono::steady_clock::now();
+    double value = 0.0;
+    int32_t piv = 0;
+    int frc = dd_min_cost_flow(c->nb, c->h_nbr.data(), c->h_cbar, c->h_m.data(), c->h_w, &value, &piv);
+    if (frc != DD_OK) {  // keep the stationary flow (Lemma 3.6: always feasible)
+        for (int i = 0; i < c->nb; ++i)
+            for (int k = 0; k < 5; ++k) c->h_w[5 * i + k] = k == 0 ? c->h_m[i] : 0.0;
+        value = 0.0;
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    RET(h2d(c->d_w, c->h_w, 5 * (size_t)c->nb, c->stream));
+    CK(cudaEventRecord(c->ev[5], c->stream));
+    RET(launch_plan_exchange(c));
+    RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->h_tot[PT_OUT] > (long long)INT32_MAX) return DD_ERR_POOL;
+    RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)c->h_tot[PT_OUT]));
+    RET(launch_exchange(c));
+    CK(cudaEventRecord(c->ev[6], c->stream));
+    c->cur = 1 - c->cur;
+    c->flow_ready = false;
+    CK(cudaStreamSynchronize(c->stream));
+    dd_flow_stats fs{};
+    fs.value = value;
+    fs.pivots = piv;
+    int nz = 0;
+    double moved = 0;
+    for (int i = 0; i < c->nb; ++i)
+        for (int k = 1; k < 5; ++k)
+            if (c->h_w[5 * i + k] > 0) { ++nz; moved += c->h_w[5 * i + k]; }
+    fs.nonzero = nz;
+    fs.moved = moved;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
+    fs.ms_costs = ms;
+    fs.ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
+    fs.ms_exchange = ms;
+    c->last_flow = fs;
+    if (st) *st = fs;
+    return frc == DD_OK ? DD_OK : DD_ERR_FLOW;
+}
+
+int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
+    if (!c || n < 0) return DD_ERR_ARG;
+    int rc = DD_OK;
+    for (int k = 0; k < n; ++k) {
+        int r = dd_iterate(c, 0, sa);
+        if (r != DD_OK && r != DD_ERR_MAXITER) return r;
+        if (r != DD_OK) rc = r;
+        r = dd_iterate(c, 1, sb);
+        if (r != DD_OK && r != DD_ERR_MAXITER) return r;
+        if (r != DD_OK) rc = r;
+        r = dd_flow_update(c, sf);
+        if (r != DD_OK && r != DD_ERR_FLOW) return r;
+        if (r != DD_OK) rc = r;
+    }
+    return rc;
+}
+
+int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
+    if (!c || !count) return DD_ERR_ARG;
+    std::vector<int32_t> bh((size_t)BH_N * c->nb);
+    RET(d2h(bh.data(), c->bhdr[c->cur], bh.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t n = 0, used = 0;
+    for (int i = 0; i < c->nb; ++i) {
+        n += (size_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
+        used = std::max(used, (size_t)bh[BH_N * i + BH_START] + (size_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_STRIDE]);
+    }
+    if (hdr)
+        for (int i = 0; i < c->nb; ++i)
+            for (int k = 0; k < 4; ++k) hdr[4 * i + k] = bh[BH_N * i + k];
+    if (!data) { *count = n; return DD_OK; }
+    if (*count < n) return DD_ERR_ARG;
+    std::vector<float> buf(used);
+    RET(d2h(buf.data(), c->pool[c->cur], used, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t k = 0;
+    for (int i = 0; i < c->nb; ++i) {
+        const int32_t* b = &bh[BH_N * i];
+        for (int r = 0; r < b[BH_H]; ++r)
+            for (int q = 0; q < b[BH_W]; ++q) data[k++] = buf[(size_t)b[BH_START] + (size_t)r * b[BH_STRIDE] + q];
+    }
+    *count = n;
+    return DD_OK;
+}
+
+static int get_comp(dd_ctx* c, int part, std::vector<int32_t>& ch, std::vector<float>& b, std::vector<float>& nuJ,
+                    bool want_b) {
+    DevPart& P = c->part[part];
+    ch.resize((size_t)CH_N * P.ncell);
+    RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t used = 0;
+    for (int J = 0; J < P.ncell; ++J) {
+        const int32_t* x = &ch[CH_N * J];
+        long long comp = ((long long)x[CH_COMP_HI] << 32) | (unsigned int)x[CH_COMP_LO];
+        used = std::max(used, (size_t)comp + (size_t)x[CH_H] * x[CH_STRIDE]);
+    }
+    nuJ.resize(used);
+    RET(d2h(nuJ.data(), P.comp_nu, used, c->stream));
+    if (want_b) {
+        b.resize(used);
+        RET(d2h(b.data(), P.comp_b, used, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
+int dd_get_composite(dd_ctx* c, int part, int32_t* hdr, double* data, size_t* count) {
+    if (!c || !count || part < 0 || part > 1) return DD_ERR_ARG;
+    DevPart& P = c->part[part];
+    if (!P.solved) return DD_ERR_STATE;
+    std::vector<int32_t> ch;
+    std::vector<float> b, nuJ;
+    RET(get_comp(c, part, ch, b, nuJ, false));
+    size_t n = 0;
+    for (int J = 0; J < P.ncell; ++J) n += (size_t)ch[CH_N * J + CH_H] * ch[CH_N * J + CH_W];
+    if (hdr)
+        for (int J = 0; J < P.ncell; ++J)
+            for (int k = 0; k < 4; ++k) hdr[4 * J + k] = ch[CH_N * J + k];
+    if (!data) { *count = n; return DD_OK; }
+    if (*count < n) return DD_ERR_ARG;
+    size_t k = 0;
+    for (int J = 0; J < P.ncell; ++J) {
+        const int32_t* x = &ch[CH_N * J];
+        long long comp = ((long long)x[CH_COMP_HI] << 32) | (unsigned int)x[CH_COMP_LO];
+        for (int r = 0; r < x[CH_H]; ++r)
+            for (int q = 0; q < x[CH_W]; ++q) data[k++] = nuJ[(size_t)comp + (size_t)r * x[CH_STRIDE] + q];
+    }
+    *count = n;
+    return DD_OK;
+}
+
+int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta, size_t* count) {
+    if (!c || !count || part < 0 || part > 1) return DD_ERR_ARG;
+    DevPart& P = c->part[part];
+    if (!P.solved) return DD_ERR_STATE;
+    std::vector<int32_t> ch, xb((size_t)XB_N * P.ncell);
+    std::vector<float> b, nuJ, al((size_t)c->amax * P.ncell), g(2 * (size_t)P.ncell);
+    RET(get_comp(c, part, ch, b, nuJ, true));
+    RET(d2h(xb.data(), P.xblk, xb.size(), c->stream));
+    RET(d2h(al.data(), P.alpha, al.size(), c->stream));
+    RET(d2h(g.data(), P.gauge, g.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t n = 0;
+    for (int J = 0; J < P.ncell; ++J) n += (size_t)ch[CH_N * J + CH_H] * ch[CH_N * J + CH_W];
+    if (hdr)
+        for (int J = 0; J < P.ncell; ++J)
+            for (int k = 0; k < 4; ++k) hdr[4 * J + k] = ch[CH_N * J + k];
+    if (!beta && !alpha) { *count = n; return DD_OK; }
+    if (beta && *count < n) return DD_ERR_ARG;
+    const double k2 = c->k2, eps = c->eps;
+    size_t k = 0;
+    for (int J = 0; J < P.ncell; ++J) {
+        const int32_t* x = &ch[CH_N * J];
+        const int32_t* X = &xb[XB_N * J];
+        const int hx = X[XB_HX], wx = X[XB_WX], h = x[CH_H], w = x[CH_W];
+        const double d1 = g[2 * J], d2 = g[2 * J + 1];
+        const double uc1 = 0.5 * (hx - 1), uc2 = 0.5 * (wx - 1), vc1 = 0.5 * (h - 1), vc2 = 0.5 * (w - 1);
+        const double hd = 0.5 * k2 * (d1 * d1 + d2 * d2);
+        if (alpha)
+            for (int u1 = 0; u1 < hx; ++u1)
+                for (int u2 = 0; u2 < wx; ++u2) {
+                    size_t px = (size_t)(X[XB_R0] + u1) * c->N2 + X[XB_C0] + u2;
+                    double a = al[(size_t)c->amax * J + u1 * wx + u2];
+                    double mu = c->h_mu[px];
+                    alpha[px] = mu > 0 ? eps * (kLn2 * (a + 2 * k2 * (d1 * (u1 - uc1) + d2 * (u2 - uc2)) + hd) - std::log(mu))
+                                       : -INFINITY;
+                }
+        long long comp = ((long long)x[CH_COMP_HI] << 32) | (unsigned int)x[CH_COMP_LO];
+        for (int r = 0; r < h; ++r)
+            for (int q = 0; q < w; ++q) {
+                double nj = nuJ[(size_t)comp + (size_t)r * x[CH_STRIDE] + q];
+                double bb = b[(size_t)comp + (size_t)r * x[CH_STRIDE] + q];
+                size_t py = (size_t)(x[CH_O1] + r) * c->N2 + x[CH_O2] + q;
+                double val = -INFINITY;
+                if (nj > 0)
+                    val = eps * (kLn2 * (bb - 2 * k2 * (d1 * (r - vc1) + d2 * (q - vc2)) + hd) - std::log(c->h_nu[py]));
+                if (beta) beta[k] = val;
+                ++k;
+            }
+    }
+    *count = n;
+    return DD_OK;
+}
+
+int dd_get_cell_stats(dd_ctx* c, int part, int32_t* iters, double* err) {
+    if (!c || part < 0 || part > 1) return DD_ERR_ARG;
+    DevPart& P = c->part[part];
+    if (!P.solved) return DD_ERR_STATE;
+    if (iters) RET(d2h(iters, P.iters, P.ncell, c->stream));
+    if (err) RET(d2h(err, P.err, P.ncell, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
+int dd_get_objective(dd_ctx* c, double* E, double* l1_x, double* l1_y) {
+    if (!c) return DD_ERR_ARG;
+    if (E) *E = c->last_E;
+    if (l1_x) *l1_x = c->last_l1x;
+    if (l1_y) {
+        RET(launch_l1y(c, c->d_red));
+        RET(d2h(l1_y, c->d_red, 1, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return DD_OK;
+}
+
+int dd_get_partition(dd_ctx* c, int part, int32_t* members, int32_t* ncell) {
+    if (!c || part < 0 || part > 1 || !ncell) return DD_ERR_ARG;
+    DevPart& P = c->part[part];
+    *ncell = P.ncell;
+    if (members) std::memcpy(members, P.h_members.data(), sizeof(int32_t) * P.h_members.size());
+    return DD_OK;
+}
+
+int dd_get_neighbours(dd_ctx* c, int32_t* nbr) {
+    if (!c || !nbr) return DD_ERR_ARG;
+    std::memcpy(nbr, c->h_nbr.data(), sizeof(int32_t) * c->h_nbr.size());
+    return DD_OK;
+}
+
+int dd_get_basic_moments(dd_ctx* c, double* D, double* mass, double* ybar, double* var) {
+    if (!c) return DD_ERR_ARG;
+    std::vector<double> bm((size_t)BM_N * c->nb);
+    RET(d2h(bm.data(), c->d_bmom, bm.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->nb; ++i) {
+        if (D) D[i] = bm[BM_N * i + BM_D];
+        if (mass) mass[i] = bm[BM_N * i + BM_MASS];
+        if (ybar) { ybar[2 * i] = bm[BM_N * i + BM_Y1]; ybar[2 * i + 1] = bm[BM_N * i + BM_Y2]; }
+        if (var) var[i] = bm[BM_N * i + BM_VAR];
+    }
+    return DD_OK;
+}
+
+int dd_get_flow(dd_ctx* c, double* cbar, double* w) {
+    if (!c) return DD_ERR_ARG;
+    if (cbar) std::memcpy(cbar, c->h_cbar, sizeof(double) * 5 * c->nb);
+    if (w) std::memcpy(w, c->h_w, sizeof(double) * 5 * c->nb);
+    return DD_OK;
+}
+
+int dd_get_prebalance(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
+    if (!c || !count) return DD_ERR_ARG;
+    if (!(c->opt.flags & DD_FLAG_KEEP_PREBALANCE) || c->last_part < 0) return DD_ERR_STATE;
+    DevPart& P = c->part[c->last_part];
+    std::vector<int32_t> ch((size_t)CH_N * P.ncell);
+    RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // basic cell i -> (cell J, member k)
+    std::vector<int> cellof(c->nb, -1), memk(c->nb, -1);
+    for (int J = 0; J < P.ncell; ++J)
+        for (int k = 0; k < 4; ++k) {
+            int i = P.h_members[4 * J + k];
+            if (i >= 0) { cellof[i] = J; memk[i] = k; }
+        }
+    size_t n = 0, used = 0;
+    for (int i = 0; i < c->nb; ++i) {
+        const int32_t* x = &ch[CH_N * cellof[i]];
+        n += (size_t)x[CH_H] * x[CH_W];
+        size_t area = (size_t)x[CH_H] * x[CH_STRIDE];
+        used = std::max(used, (size_t)x[CH_OUT_SLOT] + (memk[i] + 1) * area);
+    }
+    if (hdr)
+        for (int i = 0; i < c->nb; ++i)
+            for (int k = 0; k < 4; ++k) hdr[4 * i + k] = ch[CH_N * cellof[i] + k];
+    if (!data) { *count = n; return DD_OK; }
+    if (*count < n) return DD_ERR_ARG;
+    std::vector<float> buf(used);
+    RET(d2h(buf.data(), c->d_pre, used, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t k = 0;
+    for (int i = 0; i < c->nb; ++i) {
+        const int32_t* x = &ch[CH_N * cellof[i]];
+        size_t area = (size_t)x[CH_H] * x[CH_STRIDE];
+        size_t base = (size_t)x[CH_OUT_SLOT] + memk[i] * area;
+        for (int r = 0; r < x[CH_H]; ++r)
+            for (int q = 0; q < x[CH_W]; ++q) data[k++] = buf[base + (size_t)r * x[CH_STRIDE] + q];
+    }
+    *count = n;
+    return DD_OK;
+}
+
+}  // extern "C"

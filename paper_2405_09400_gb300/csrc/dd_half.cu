@@ -1,0 +1,687 @@
+// One domain-decomposition half-iteration on the GPU (Alg. 1 as restated in
+// Alg. 4), as two kernels:
+//
+//  k_plan_half  one CTA: for every composite cell the union box of its member
+//               boxes (BasicToComposite's output box, Eq. get-composite-cell-
+//               marginal), and prefix sums that place the composite marginal and
+//               the member outputs in their pools;
+//  k_half       a persistent kernel with a work queue; one CTA solves one
+//               composite cell at a time, entirely in shared memory:
+//                 1. gather nu_J from the member boxes (BasicToComposite),
+//                 2. log-domain Sinkhorn (Section A.1, "Custom CUDA Sinkhorn")
+//                    with the separable per-axis log-sum-exp for the squared
+//                    cost, until the L1 X error <= tol * mu(X_J),
+//                 3. CompositeToBasic by the partial log-sum-exp over each
+//                    basic cell (Section A.1, "Online reduction"), with
+//                    D_i = <c, pi_i> from the same partial sums,
+//                 4. balancing and 5. truncation at `trunc` (Alg. 4), and the
+//                    minimal box of each member, compacted in place.
+//
+// Number format: the LSE runs in FP32 in base 2 (ex2/lg2); masses, errors, D_i,
+// moments and the objective accumulate in FP64.
+//
+// Dual representation. With x = (r0 + u1, c0 + u2) in the cell block and
+// y = (o1 + v1, o2 + v2) in the box, the kernel keeps
+//   pi(x, y) = 2^( a(u) + b(v) - k2 |ubar - vbar|^2 ),
+// where ubar = u - (block centre), vbar = v - (box centre), k2 = h^2/eps*log2(e),
+// a absorbs log2 mu(x) and b absorbs log2 nu_J(y). The true duals follow from
+//   alpha/eps = ln2 (a + 2 k2 d.ubar + k2|d|^2/2) - ln mu,
+//   beta_t/eps = ln2 (b - 2 k2 d.vbar + k2|d|^2/2) - ln nu_J,
+// with d = (block centre) - (box centre) in pixels (the linear part of the cost
+// is absorbed so that the FP32 duals stay small).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "dd_internal.h"
+
+namespace {
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2f(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr double kLn2d = 0.69314718055994530942;
+
+// ---------------------------------------------------------------------------
+// block reductions
+template <int N>
+__device__ void block_sum_d(double (&v)[N], double* sh /* >= 32*N */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[wid * N + k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double x = 0.0;
+        for (int w = 0; w < nw; ++w) x += sh[w * N + threadIdx.x];
+        sh[32 * N + threadIdx.x] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = sh[32 * N + k];
+    __syncthreads();
+}
+
+// exclusive scan over a block of long long (blockDim.x <= 1024)
+__device__ long long block_exscan(long long x, long long* sh, long long* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        long long s = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    long long base = wid > 0 ? sh[wid - 1] : 0;
+    *total = sh[nw - 1];
+    __syncthreads();
+    return base + inc - x;
+}
+
+// ---------------------------------------------------------------------------
+// planning: union boxes and pool offsets (one CTA)
+__global__ void k_plan_half(int ncell, const int32_t* __restrict__ members, const int32_t* __restrict__ bhdr,
+                            int32_t* __restrict__ chdr, const int32_t* __restrict__ xblk, long long* __restrict__ tot) {
+    __shared__ long long sh[64];
+    __shared__ long long smax[3];
+    const int T = blockDim.x;
+    const int per = (ncell + T - 1) / T;
+    const int c0 = min(ncell, threadIdx.x * per), c1 = min(ncell, c0 + per);
+    if (threadIdx.x < 3) smax[threadIdx.x] = 0;
+    __syncthreads();
+    long long sa = 0, so = 0, ma = 0, mh = 0, mw = 0;
+    for (int J = c0; J < c1; ++J) {
+        int lo1 = INT32_MAX, lo2 = INT32_MAX, hi1 = INT32_MIN, hi2 = INT32_MIN;
+        for (int k = 0; k < 4; ++k) {
+            int i = members[4 * J + k];
+            if (i < 0) continue;
+            const int32_t* b = bhdr + (size_t)BH_N * i;
+            if (b[BH_H] <= 0 || b[BH_W] <= 0) continue;
+            lo1 = min(lo1, b[BH_O1]);
+            lo2 = min(lo2, b[BH_O2]);
+            hi1 = max(hi1, b[BH_O1] + b[BH_H]);
+            hi2 = max(hi2, b[BH_O2] + b[BH_W]);
+        }
+        int h = 0, w = 0;
+        if (hi1 > lo1) { h = hi1 - lo1; w = hi2 - lo2; } else { lo1 = lo2 = 0; }
+        int stride = (w + 3) & ~3;
+        int32_t* ch = chdr + (size_t)CH_N * J;
+        ch[CH_O1] = lo1; ch[CH_O2] = lo2; ch[CH_H] = h; ch[CH_W] = w; ch[CH_STRIDE] = stride;
+        long long area = (long long)h * stride;
+        sa += area;
+        so += area * xblk[XB_N * J + XB_NMEM];
+        ma = max(ma, (long long)h * w);
+        mh = max(mh, (long long)h);
+        mw = max(mw, (long long)w);
+    }
+    long long ta, to;
+    long long ea = block_exscan(sa, sh, &ta);
+    long long eo = block_exscan(so, sh, &to);
+    for (int J = c0; J < c1; ++J) {
+        int32_t* ch = chdr + (size_t)CH_N * J;
+        long long area = (long long)ch[CH_H] * ch[CH_STRIDE];
+        ch[CH_COMP_LO] = (int32_t)(ea & 0xffffffffLL);
+        ch[CH_COMP_HI] = (int32_t)(ea >> 32);
+        ch[CH_OUT_SLOT] = (int32_t)eo;
+        ea += area;
+        eo += area * xblk[XB_N * J + XB_NMEM];
+    }
+    atomicMax((unsigned long long*)&smax[0], (unsigned long long)ma);
+    atomicMax((unsigned long long*)&smax[1], (unsigned long long)mh);
+    atomicMax((unsigned long long*)&smax[2], (unsigned long long)mw);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tot[PT_COMP] = ta;
+        tot[PT_OUT] = to;
+        tot[PT_MAXAREA] = smax[0];
+        tot[PT_MAXH] = smax[1];
+        tot[PT_MAXW] = smax[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct HalfArgs {
+    int N1, N2, s, ncell, amax;
+    float k2;
+    double eps, h2;
+    const int32_t* members;
+    const int32_t* xblk;
+    const double* mJ;
+    const int32_t* order;
+    const int32_t* bhdr_in;
+    const float* pool_in;
+    int32_t* bhdr_out;
+    float* pool_out;
+    int32_t* chdr;
+    float* comp_b;
+    float* comp_nu;
+    float* alpha;
+    float* gauge;
+    int warm;
+    const float* lgmu;
+    const double* mu;
+    const double* nu;
+    const double* m;
+    double tol;
+    int max_iter, fixed_iters;
+    float trunc;
+    int32_t* iters;
+    double* err;
+    double* Ecell;
+    double* bmom;
+    float* pre;  // optional prebalance copy (same layout as pool_out)
+    int* queue;
+    int* status;
+    int smaxA, smaxH, smaxW;  // shared-memory capacities
+};
+
+// shared-memory layout (floats unless noted)
+struct Smem {
+    float* lgnu;  // maxA
+    float* b;     // maxA
+    float* T;     // 4 * (2s) * maxW   (Y stage 1; C2B partial sums + moments)
+    float* R;     // maxH * (2s)
+    float* tab1;  // maxH + 2s
+    float* tab2;  // maxW + 2s
+    float* a;     // amax
+    float* an;    // amax
+    float* lgm;   // amax
+    double* mux;  // amax
+    double* red;  // 32 * 16 + 16
+    float* coef;  // 16
+    int* ctl;     // 32
+};
+
+__device__ Smem carve(char* base, const HalfArgs& A) {
+    Smem S;
+    const int s2 = 2 * A.s;
+    double* d = reinterpret_cast<double*>(base);
+    S.mux = d;
+    d += A.amax;
+    S.red = d;
+    d += 32 * 16 + 16;
+    float* f = reinterpret_cast<float*>(d);
+    S.lgnu = f; f += A.smaxA;
+    S.b = f; f += A.smaxA;
+    S.T = f; f += 4 * s2 * A.smaxW;
+    S.R = f; f += A.smaxH * s2;
+    S.tab1 = f; f += A.smaxH + s2;
+    S.tab2 = f; f += A.smaxW + s2;
+    S.a = f; f += A.amax;
+    S.an = f; f += A.amax;
+    S.lgm = f; f += A.amax;
+    S.coef = f; f += 16;
+    S.ctl = reinterpret_cast<int*>(f);
+    return S;
+}
+
+// log2 sum_k 2^t_k for a line read through a functor, two passes
+template <typename F>
+__device__ __forceinline__ float lse2(int n, F term) {
+    float m = DD_NEG;
+    for (int k = 0; k < n; ++k) m = fmaxf(m, term(k));
+    float s = 0.f;
+    for (int k = 0; k < n; ++k) s += ex2f(term(k) - m);
+    return m + lg2f(s);
+}
+
+__global__ void __launch_bounds__(512) k_half(HalfArgs A) {
+    extern __shared__ __align__(16) char smem_raw[];
+    Smem S = carve(smem_raw, A);
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int s = A.s;
+
+    while (true) {
+        if (tid == 0) S.ctl[0] = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int t = S.ctl[0];
+        if (t >= A.ncell) break;
+        const int J = A.order[t];
+        const int32_t* xb = A.xblk + XB_N * J;
+        const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
+        const int32_t* ch = A.chdr + CH_N * J;
+        const int o1 = ch[CH_O1], o2 = ch[CH_O2], h = ch[CH_H], w = ch[CH_W], stride = ch[CH_STRIDE];
+        const long long comp = ((long long)ch[CH_COMP_HI] << 32) | (unsigned int)ch[CH_COMP_LO];
+        const long long slot0 = ch[CH_OUT_SLOT];
+        const long long area = (long long)h * stride;
+        const int nx = hx * wx, nA = h * w;
+        int32_t mem[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
+        if (nA == 0) {  // no Y mass in the cell: only possible for an infeasible state
+            if (tid == 0) {
+                atomicAdd(&A.status[1], 1);
+                A.iters[J] = 0;
+                A.err[J] = A.mJ[J];
+                A.Ecell[J] = 0.0;
+                for (int k = 0; k < nmem; ++k) {
+                    int32_t* bo = A.bhdr_out + BH_N * mem[k];
+                    bo[BH_O1] = bo[BH_O2] = bo[BH_H] = bo[BH_W] = bo[BH_STRIDE] = 0;
+                    bo[BH_START] = (int32_t)slot0;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // centred coordinates: d = block centre - box centre (pixels)
+        const float uc1 = 0.5f * (hx - 1), uc2 = 0.5f * (wx - 1);
+        const float vc1 = 0.5f * (h - 1), vc2 = 0.5f * (w - 1);
+        const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
+        const float e1 = vc1 - uc1, e2 = vc2 - uc2;
+
+        // ---- 1. gather nu_J and tables ------------------------------------
+        for (int v = tid; v < nA; v += NT) {
+            const int v1 = v / w, v2 = v - v1 * w;
+            const int y1 = o1 + v1, y2 = o2 + v2;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (mem[k] < 0) continue;
+                const int32_t* bh = A.bhdr_in + BH_N * mem[k];
+                const int p1 = y1 - bh[BH_O1], p2 = y2 - bh[BH_O2];
+                if (p1 >= 0 && p1 < bh[BH_H] && p2 >= 0 && p2 < bh[BH_W])
+                    acc += A.pool_in[(long long)bh[BH_START] + (long long)p1 * bh[BH_STRIDE] + p2];
+            }
+            A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
+            S.lgnu[v] = acc > 0.f ? lg2f(acc) : DD_NEG;
+        }
+        for (int k = tid; k < h + hx - 1; k += NT) {
+            const float z = (float)(k - (h - 1)) + e1;
+            S.tab1[k] = A.k2 * z * z;
+        }
+        for (int k = tid; k < w + wx - 1; k += NT) {
+            const float z = (float)(k - (w - 1)) + e2;
+            S.tab2[k] = A.k2 * z * z;
+        }
+        // X side: log2 mu and the warm start
+        const float* ap = A.alpha + (long long)A.amax * J;
+        const float pd1 = A.gauge[2 * J], pd2 = A.gauge[2 * J + 1];
+        for (int u = tid; u < nx; u += NT) {
+            const int u1 = u / wx, u2 = u - u1 * wx;
+            const int x = (r0 + u1) * A.N2 + (c0 + u2);
+            const double mux = A.mu[x];
+            S.mux[u] = mux;
+            const float lg = A.lgmu[x];
+            S.lgm[u] = lg;
+            const float ub1 = u1 - uc1, ub2 = u2 - uc2;
+            float a0;
+            if (A.warm) a0 = ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2);
+            else a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2);
+            S.a[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
+        }
+        __syncthreads();
+
+        // ---- 2. Sinkhorn ----------------------------------------------------
+        const double tolm = A.tol * A.mJ[J];
+        int it = 0;
+        double err = 0.0;
+        while (true) {
+            ++it;
+            // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1,u2) - k2 (u2 - v2 + e2)^2]
+            for (int q = tid; q < hx * w; q += NT) {
+                const int u1 = q / w, v2 = q - u1 * w;
+                const float* ar = S.a + u1 * wx;
+                const float* tb = S.tab2 + (w - 1) - v2;
+                S.T[q] = lse2(wx, [&](int u2) { return ar[u2] - tb[u2]; });
+            }
+            __syncthreads();
+            // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - k2 (u1 - v1 + e1)^2]
+            for (int v = tid; v < nA; v += NT) {
+                const int v1 = v / w, v2 = v - v1 * w;
+                const float ln = S.lgnu[v];
+                float bv = DD_NEG;
+                if (ln > 0.5f * DD_NEG) {
+                    const float* tb = S.tab1 + (h - 1) - v1;
+                    const float* Tc = S.T + v2;
+                    bv = ln - lse2(hx, [&](int u1) { return Tc[u1 * w] - tb[u1]; });
+                }
+                S.b[v] = bv;
+            }
+            __syncthreads();
+            // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - k2 (u2 - v2 + e2)^2]
+            for (int q = tid; q < h * wx; q += NT) {
+                const int v1 = q / wx, u2 = q - v1 * wx;
+                const float* br = S.b + v1 * w;
+                const float* tb = S.tab2 + u2 + (w - 1);
+                S.R[q] = lse2(w, [&](int v2) { return br[v2] - tb[-v2]; });
+            }
+            __syncthreads();
+            // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - k2 (u1 - v1 + e1)^2]
+            double e_loc = 0.0;
+            for (int u = tid; u < nx; u += NT) {
+                const int u1 = u / wx, u2 = u - u1 * wx;
+                const float lg = S.lgm[u];
+                float an = DD_NEG;
+                if (lg > 0.5f * DD_NEG) {
+                    const float* tb = S.tab1 + u1 + (h - 1);
+                    const float* Rc = S.R + u2;
+                    an = lg - lse2(h, [&](int v1) { return Rc[v1 * wx] - tb[-v1]; });
+                    e_loc += S.mux[u] * (double)fabsf(expm1f((S.a[u] - an) * kLn2));
+                }
+                S.an[u] = an;
+            }
+            double ev[1] = {e_loc};
+            block_sum_d<1>(ev, S.red);
+            err = ev[0];
+            const bool done = (A.fixed_iters > 0) ? (it >= A.fixed_iters)
+                                                  : (err <= tolm || it >= A.max_iter);
+            if (done) break;
+            for (int u = tid; u < nx; u += NT) S.a[u] = S.an[u];
+            __syncthreads();
+        }
+        if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[0], 1);
+
+        // ---- outputs of the solve: duals, objective --------------------------
+        float* apo = A.alpha + (long long)A.amax * J;
+        double eloc[1] = {0.0};
+        const float hd = 0.5f * A.k2 * (d1 * d1 + d2 * d2);
+        for (int u = tid; u < nx; u += NT) {
+            apo[u] = S.a[u];
+            const float lg = S.lgm[u];
+            if (lg > 0.5f * DD_NEG) {
+                const int u1 = u / wx, u2 = u - u1 * wx;
+                const double r = S.mux[u] * exp2((double)(S.a[u] - S.an[u]));
+                const double al = kLn2d * ((double)S.a[u] + 2.0 * A.k2 * ((double)d1 * (u1 - uc1) + (double)d2 * (u2 - uc2)) + hd)
+                                  - log(S.mux[u]);
+                eloc[0] += al * r;
+            }
+        }
+        for (int v = tid; v < nA; v += NT) {
+            const int v1 = v / w, v2 = v - v1 * w;
+            A.comp_b[comp + (long long)v1 * stride + v2] = S.b[v];
+            if (S.lgnu[v] > 0.5f * DD_NEG) {
+                const double nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
+                const double be = kLn2d * ((double)S.b[v] - 2.0 * A.k2 * ((double)d1 * (v1 - vc1) + (double)d2 * (v2 - vc2)) + hd)
+                                  - log(A.nu[(o1 + v1) * A.N2 + (o2 + v2)]);
+                eloc[0] += be * nuJ;
+            }
+        }
+        block_sum_d<1>(eloc, S.red);
+        if (tid == 0) {
+            A.gauge[2 * J] = d1;
+            A.gauge[2 * J + 1] = d2;
+            A.iters[J] = it;
+            A.err[J] = err;
+            A.Ecell[J] = A.eps * eloc[0];
+        }
+
+        // ---- 3. CompositeToBasic with D_i -----------------------------------
+        // C1: per column group cg, T2(cg, u1, v2) = LSE over u2 in the group, and
+        //     M2 = mean of (x2 - y2)^2 under that partial distribution.
+        const int ncg = wx / s, nrg = hx / s;
+        float* T2 = S.T;
+        float* M2 = S.T + 2 * (2 * s) * A.smaxW;
+        for (int q = tid; q < ncg * hx * w; q += NT) {
+            const int cg = q / (hx * w), rem = q - cg * hx * w;
+            const int u1 = rem / w, v2 = rem - u1 * w;
+            const float* ar = S.a + u1 * wx + cg * s;
+            const float* tb = S.tab2 + (w - 1) - v2 + cg * s;
+            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k]; });
+            float mom = 0.f;
+            for (int k = 0; k < s; ++k) {
+                const float dd = (float)(c0 + cg * s + k - o2 - v2);
+                mom += ex2f(ar[k] - tb[k] - lse) * dd * dd;
+            }
+            T2[q] = lse;
+            M2[q] = mom;
+        }
+        __syncthreads();
+        // C2: nu_i(v) = 2^(b(v) + LSE_{u1 in group} [T2 - k2 (u1 - v1 + e1)^2]), D_i accumulation
+        double accm[4] = {0, 0, 0, 0}, accd[4] = {0, 0, 0, 0};
+        for (int v = tid; v < nA; v += NT) {
+            const int v1 = v / w, v2 = v - v1 * w;
+            const float bv = S.b[v];
+            const float* tb = S.tab1 + (h - 1) - v1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k >= nmem) break;
+                const int rg = k / ncg, cg = k - rg * ncg;
+                float val = 0.f, ew = 0.f;
+                if (bv > 0.5f * DD_NEG) {
+                    const float* Tc = T2 + cg * hx * w + v2;
+                    const float* Mc = M2 + cg * hx * w + v2;
+                    const int ub = rg * s;
+                    const float lse = lse2(s, [&](int kk) { return Tc[(ub + kk) * w] - tb[ub + kk]; });
+                    for (int kk = 0; kk < s; ++kk) {
+                        const float dd = (float)(r0 + ub + kk - o1 - v1);
+                        ew += ex2f(Tc[(ub + kk) * w] - tb[ub + kk] - lse) * (dd * dd + Mc[(ub + kk) * w]);
+                    }
+                    val = ex2f(bv + lse);
+                }
+                A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = val;
+                accm[k] += val;
+                accd[k] += (double)val * ew;
+            }
+        }
+        double red8[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { red8[k] = accm[k]; red8[4 + k] = accd[k]; }
+        block_sum_d<8>(red8, S.red);
+        (void)nrg;
+
+        // ---- 4. balancing coefficients (member order walk) -------------------
+        if (tid == 0) {
+            double mass[4], e[4];
+            for (int k = 0; k < 4; ++k) {
+                mass[k] = red8[k];
+                e[k] = (k < nmem) ? mass[k] - A.m[mem[k]] : 0.0;
+            }
+            double cf[4][4];
+            for (int j = 0; j < 4; ++j)
+                for (int k = 0; k < 4; ++k) cf[j][k] = (j == k) ? 1.0 : 0.0;
+            int pos[4], neg[4], np = 0, nn = 0;
+            for (int k = 0; k < nmem; ++k) {
+                if (e[k] > 0.0) pos[np++] = k;
+                else if (e[k] < 0.0) neg[nn++] = k;
+            }
+            int p = 0, q = 0;
+            double rp = np ? e[pos[0]] : 0.0, rq = nn ? -e[neg[0]] : 0.0;
+            while (p < np && q < nn) {
+                const int i = pos[p], j = neg[q];
+                const double d = fmin(rp, rq);
+                const double f = d / mass[i];
+                cf[i][i] -= f;
+                cf[j][i] += f;
+                rp -= d;
+                rq -= d;
+                if (rp <= 0.0) { ++p; rp = p < np ? e[pos[p]] : 0.0; }
+                if (rq <= 0.0) { ++q; rq = q < nn ? -e[neg[q]] : 0.0; }
+            }
+            for (int j = 0; j < 4; ++j)
+                for (int k = 0; k < 4; ++k) S.coef[4 * j + k] = (float)cf[j][k];
+            for (int k = 0; k < nmem; ++k) {
+                double* bm = A.bmom + BM_N * mem[k];
+                bm[BM_D] = A.h2 * red8[4 + k];
+                bm[BM_PREMASS] = mass[k];
+            }
+            for (int k = 0; k < 16; ++k) S.ctl[4 + k] = 0;
+            for (int k = 0; k < 4; ++k) {
+                S.ctl[4 + 4 * k + 0] = INT32_MAX;  // min row
+                S.ctl[4 + 4 * k + 1] = -1;         // max row
+                S.ctl[4 + 4 * k + 2] = INT32_MAX;  // min col
+                S.ctl[4 + 4 * k + 3] = -1;         // max col
+            }
+        }
+        __syncthreads();
+
+        // ---- 5. apply balancing, truncate, box and moments -------------------
+        float cf[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cf[j][k] = S.coef[4 * j + k];
+        int bb[4][4];
+        double mom[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            bb[k][0] = INT32_MAX; bb[k][1] = -1; bb[k][2] = INT32_MAX; bb[k][3] = -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) mom[k] = 0.0;
+        for (int v = tid; v < nA; v += NT) {
+            const int v1 = v / w, v2 = v - v1 * w;
+            const long long off = slot0 + (long long)v1 * stride + v2;
+            float vals[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) vals[k] = (k < nmem) ? A.pool_out[off + k * area] : 0.f;
+            if (A.pre) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nmem) A.pre[off + k * area] = vals[k];
+            }
+            const double y1 = (double)v1 - vc1, y2 = (double)v2 - vc2;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nmem) break;
+                float nv = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nv += cf[j][k] * vals[k];
+                if (!(nv >= A.trunc)) nv = 0.f;
+                A.pool_out[off + j * area] = nv;
+                if (nv > 0.f) {
+                    bb[j][0] = min(bb[j][0], v1); bb[j][1] = max(bb[j][1], v1);
+                    bb[j][2] = min(bb[j][2], v2); bb[j][3] = max(bb[j][3], v2);
+                    const double dv = nv;
+                    mom[4 * j + 0] += dv;
+                    mom[4 * j + 1] += dv * y1;
+                    mom[4 * j + 2] += dv * y2;
+                    mom[4 * j + 3] += dv * (y1 * y1 + y2 * y2);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= nmem) break;
+            atomicMin(&S.ctl[4 + 4 * k + 0], bb[k][0]);
+            atomicMax(&S.ctl[4 + 4 * k + 1], bb[k][1]);
+            atomicMin(&S.ctl[4 + 4 * k + 2], bb[k][2]);
+            atomicMax(&S.ctl[4 + 4 * k + 3], bb[k][3]);
+        }
+        block_sum_d<16>(mom, S.red);  // contains __syncthreads
+
+        // ---- compaction in place (dst index never exceeds src index) --------
+        for (int k = 0; k < nmem; ++k) {
+            const int rlo = S.ctl[4 + 4 * k + 0], rhi = S.ctl[4 + 4 * k + 1];
+            const int clo = S.ctl[4 + 4 * k + 2], chi = S.ctl[4 + 4 * k + 3];
+            const bool empty = rhi < 0;
+            const int hh = empty ? 0 : rhi - rlo + 1, ww = empty ? 0 : chi - clo + 1;
+            const int st = (ww + 3) & ~3;
+            float* sl = A.pool_out + slot0 + k * area;
+            const int n = hh * st;
+            for (int base = 0; base < n; base += NT) {
+                const int dI = base + tid;
+                float val = 0.f;
+                if (dI < n) {
+                    const int rr = dI / st, cc = dI - rr * st;
+                    if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc];
+                }
+                __syncthreads();
+                if (dI < n) sl[dI] = val;
+                __syncthreads();
+            }
+            if (tid == 0) {
+                const int i = mem[k];
+                int32_t* bo = A.bhdr_out + BH_N * i;
+                bo[BH_O1] = empty ? 0 : o1 + rlo;
+                bo[BH_O2] = empty ? 0 : o2 + clo;
+                bo[BH_H] = hh;
+                bo[BH_W] = ww;
+                bo[BH_STRIDE] = st;
+                bo[BH_START] = (int32_t)(slot0 + k * area);
+                double* bm = A.bmom + BM_N * i;
+                const double ms = mom[4 * k + 0];
+                const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
+                bm[BM_MASS] = ms;
+                bm[BM_Y1] = o1 + vc1 + m1;
+                bm[BM_Y2] = o2 + vc2 + m2;
+                bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
+    const int s2 = 2 * c->s;
+    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16);
+    size_t fl = 2 * (size_t)maxarea + 4 * (size_t)s2 * maxw + (size_t)maxh * s2 + (maxh + s2) + (maxw + s2) +
+                3 * (size_t)c->amax + 16 + 32;
+    return bytes + sizeof(float) * fl;
+}
+
+int half_kernel_max_smem() { return 227 * 1024; }
+
+int launch_plan_half(dd_ctx* c, int part) {
+    DevPart& P = c->part[part];
+    k_plan_half<<<1, 1024, 0, c->stream>>>(P.ncell, P.members, c->bhdr[c->cur], P.chdr, P.xblk, c->d_tot);
+    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+}
+
+static bool g_attr_set = false;
+
+int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
+    DevPart& P = c->part[part];
+    if (!g_attr_set) {
+        if (cudaFuncSetAttribute(k_half, cudaFuncAttributeMaxDynamicSharedMemorySize, half_kernel_max_smem()) !=
+            cudaSuccess)
+            return DD_ERR_CUDA;
+        g_attr_set = true;
+    }
+    HalfArgs A;
+    A.N1 = c->N1; A.N2 = c->N2; A.s = c->s; A.ncell = P.ncell; A.amax = c->amax;
+    A.k2 = c->k2; A.eps = c->eps; A.h2 = c->h * c->h;
+    A.members = P.members; A.xblk = P.xblk; A.mJ = P.mJ; A.order = P.order;
+    A.bhdr_in = c->bhdr[c->cur]; A.pool_in = c->pool[c->cur];
+    A.bhdr_out = c->bhdr[1 - c->cur]; A.pool_out = c->pool[1 - c->cur];
+    A.chdr = P.chdr; A.comp_b = P.comp_b; A.comp_nu = P.comp_nu;
+    A.alpha = P.alpha; A.gauge = P.gauge;
+    A.warm = (c->opt.warm == DD_WARM_PREV && P.warm_valid) ? 1 : 0;
+    A.lgmu = c->d_lgmu; A.mu = c->d_mu; A.nu = c->d_nu; A.m = c->d_m;
+    A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
+    A.trunc = (float)c->opt.trunc;
+    A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
+    A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;
+    A.queue = c->d_queue; A.status = c->d_status;
+    A.smaxA = (int)c->h_tot[PT_MAXAREA];
+    A.smaxH = (int)c->h_tot[PT_MAXH];
+    A.smaxW = (int)c->h_tot[PT_MAXW];
+    k_half<<<grid, threads, smem, c->stream>>>(A);
+    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+}
+
+int half_occupancy(int threads, size_t smem) {
+    int nb = 0;
+    if (!g_attr_set) {
+        if (cudaFuncSetAttribute(k_half, cudaFuncAttributeMaxDynamicSharedMemorySize, half_kernel_max_smem()) !=
+            cudaSuccess)
+            return 0;
+        g_attr_set = true;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_half, threads, smem);
+    return nb;
+}

@@ -1,0 +1,117 @@
+// Internal declarations of the ddflow library: the context, device buffers and
+// kernel launchers. Not part of the C ABI (see include/ddflow.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ddflow.h"
+
+#define DD_NEG (-1.0e30f)  // log2 of zero mass
+
+// Box header layout in device memory (int32 x 8 per box).
+enum { BH_O1 = 0, BH_O2, BH_H, BH_W, BH_STRIDE, BH_START, BH_STRIDE_HI, BH_START_HI, BH_N };
+// Composite header (int32 x 8 per cell): box + pool offsets.
+enum { CH_O1 = 0, CH_O2, CH_H, CH_W, CH_STRIDE, CH_COMP_LO, CH_COMP_HI, CH_OUT_SLOT, CH_N };
+// Composite X block (int32 x 8 per cell).
+enum { XB_R0 = 0, XB_C0, XB_HX, XB_WX, XB_NMEM, XB_PAD0, XB_PAD1, XB_PAD2, XB_N };
+
+// Per-basic-cell moments written by the half-iteration (double x 8 per cell).
+enum { BM_D = 0, BM_MASS, BM_Y1, BM_Y2, BM_VAR, BM_PREMASS, BM_PAD0, BM_PAD1, BM_N };
+
+// Totals computed by the planning kernels (long long x 8).
+enum { PT_COMP = 0, PT_OUT, PT_MAXAREA, PT_MAXH, PT_MAXW, PT_ENTRIES, PT_PAD0, PT_PAD1, PT_N };
+
+struct DevPart {
+    int ncell = 0;
+    int32_t* members = nullptr;  // ncell x 4, -1 padded
+    int32_t* xblk = nullptr;     // ncell x XB_N
+    double* mJ = nullptr;        // ncell, mu(X_J)
+    int32_t* chdr = nullptr;     // ncell x CH_N (last solve)
+    float* alpha = nullptr;      // ncell x amax, centred base-2 gauge
+    float* gauge = nullptr;      // ncell x 2, displacement (cell centre - box centre) in pixels
+    int32_t* iters = nullptr;    // ncell
+    double* err = nullptr;       // ncell
+    double* Ecell = nullptr;     // ncell
+    int32_t* order = nullptr;    // ncell, processing order
+    float* comp_b = nullptr;     // composite pool: b' (centred base-2 dual, absorbs log2 nu_J)
+    float* comp_nu = nullptr;    // composite pool: nu_J
+    size_t comp_cap = 0;
+    bool warm_valid = false;
+    bool solved = false;
+    std::vector<int32_t> h_members;  // host copy
+    std::vector<int32_t> h_xblk;     // host copy
+};
+
+struct dd_ctx {
+    int N1 = 0, N2 = 0, s = 0, n1 = 0, n2 = 0, nb = 0, amax = 0;
+    double h = 0, eps = 0;
+    float k2 = 0;  // h^2 / eps * log2(e): cost exponent per squared pixel, base 2
+    dd_options opt{};
+    cudaStream_t stream = nullptr;
+    int dev = 0, nsm = 0;
+
+    std::vector<double> h_mu, h_nu, h_m;
+    double* d_mu = nullptr;
+    double* d_nu = nullptr;
+    float* d_lgmu = nullptr;   // log2 mu (DD_NEG where 0)
+    double* d_m = nullptr;     // basic masses
+    double* d_xmom = nullptr;  // per basic cell: x1bar, x2bar, var (pixels)
+    int32_t* d_nbr = nullptr;  // nb x 5
+    int32_t* d_rev = nullptr;  // nb x 5: position of j in the list of nbr[j][k]
+    std::vector<int32_t> h_nbr;
+
+    DevPart part[2];
+    int last_part = -1;
+    bool flow_ready = false;
+
+    // basic state, double buffered
+    float* pool[2] = {nullptr, nullptr};
+    size_t pool_cap[2] = {0, 0};
+    int32_t* bhdr[2] = {nullptr, nullptr};
+    int cur = 0;
+
+    double* d_bmom = nullptr;  // nb x BM_N
+    long long* d_tot = nullptr;  // PT_N
+    long long* h_tot = nullptr;  // pinned
+    int* d_queue = nullptr;
+    int* d_status = nullptr;   // [0] maxiter count, [1] pool overflow
+
+    // prebalance copy
+    float* d_pre = nullptr;
+    size_t pre_cap = 0;
+    int32_t* d_prehdr = nullptr;
+
+    // flow
+    double* d_cbar = nullptr;
+    double* d_w = nullptr;
+    double* h_cbar = nullptr;  // pinned
+    double* h_w = nullptr;     // pinned
+    int32_t* d_xhdr = nullptr; // exchange output headers (nb x CH_N)
+    dd_flow_stats last_flow{};
+
+    // l1_y scratch
+    double* d_yacc = nullptr;
+    double* d_red = nullptr;
+
+    cudaEvent_t ev[8] = {};
+    double last_E = 0, last_l1x = 0;
+
+    // CUDA graphs for dd_step
+    cudaGraphExec_t gexec = nullptr;
+    int graph_cur = -1;
+};
+
+// kernels / launchers (dd_half.cu)
+int launch_plan_half(dd_ctx* c, int part);
+int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid);
+size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
+int half_kernel_max_smem();
+int half_occupancy(int threads, size_t smem);
+// dd_flow.cu
+int launch_cbar(dd_ctx* c);
+int launch_plan_exchange(dd_ctx* c);
+int launch_exchange(dd_ctx* c);
+int launch_l1y(dd_ctx* c, double* out_dev);

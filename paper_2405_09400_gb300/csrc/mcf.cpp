@@ -1,0 +1,280 @@
+// Host min-cost flow for the flow update, Eq. (MinCostFlow).
+//
+// The problem is a transportation problem on the neighbourhood graph
+// (Def. 3.1): every basic cell i is a source with supply m_i and a sink with
+// demand m_i; arc (i -> j) for j in N(i) carries w_ij >= 0 at cost c_bar_ij;
+// the divergence constraints of Eq. (div-constraint-single-cell) are the
+// supplies and demands. The paper solves it with OR-tools; this is a
+// project-written primal network simplex in exact int64 arithmetic:
+//
+//  * masses are scaled to integers (sum 2^60) and costs to integers (2^40 at the
+//    largest |c_bar|); w_ij = m_i * q_ij / M_i maps the integer flow back, so
+//    sum_j w_ij = m_i holds to float64 rounding;
+//  * the start basis is the stationary flow (w_ii = m_i, Lemma 3.6) completed to
+//    a spanning tree by zero-flow arcs s_p -> t_i along a spanning tree of the
+//    cell grid; it is strongly feasible, and the leaving arc is chosen by
+//    Cunningham's rule (last blocking arc from the apex), which rules out cycling;
+//  * entering arcs by block search over the reduced costs;
+//  * the tree is kept as parent pointers with doubly linked child lists; after a
+//    pivot the cut subtree is re-rooted and its depths / potentials updated.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ddflow.h"
+
+namespace {
+
+struct NetworkSimplex {
+    int nn = 0;  // nodes: sources 0..n-1, sinks n..2n-1
+    int na = 0;  // arcs
+    std::vector<int> tail, head;
+    std::vector<int64_t> cost, flow;
+    std::vector<int> parent, parc, depth, first_child, next_sib, prev_sib;
+    std::vector<int64_t> pot;
+    std::vector<char> in_tree;
+    int64_t pivots = 0;
+
+    void add_child(int p, int c) {
+        prev_sib[c] = -1;
+        next_sib[c] = first_child[p];
+        if (first_child[p] >= 0) prev_sib[first_child[p]] = c;
+        first_child[p] = c;
+    }
+    void remove_child(int p, int c) {
+        if (prev_sib[c] >= 0)
+            next_sib[prev_sib[c]] = next_sib[c];
+        else
+            first_child[p] = next_sib[c];
+        if (next_sib[c] >= 0) prev_sib[next_sib[c]] = prev_sib[c];
+        next_sib[c] = prev_sib[c] = -1;
+    }
+    int64_t rc(int a) const { return cost[a] + pot[tail[a]] - pot[head[a]]; }
+
+    // re-derive depth and potential of the subtree below r from its parent
+    void refresh_subtree(int r, std::vector<int>& stack) {
+        stack.clear();
+        stack.push_back(r);
+        while (!stack.empty()) {
+            int x = stack.back();
+            stack.pop_back();
+            int p = parent[x], a = parc[x];
+            depth[x] = depth[p] + 1;
+            pot[x] = (tail[a] == p) ? pot[p] + cost[a] : pot[p] - cost[a];
+            for (int c = first_child[x]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        }
+    }
+
+    bool pivot(int a, std::vector<int>& pu, std::vector<int>& pv, std::vector<int>& stack) {
+        int u = tail[a], v = head[a];
+        // apex by depth
+        pu.clear();
+        pv.clear();
+        int x = u, y = v;
+        while (depth[x] > depth[y]) { pu.push_back(x); x = parent[x]; }
+        while (depth[y] > depth[x]) { pv.push_back(y); y = parent[y]; }
+        while (x != y) {
+            pu.push_back(x); x = parent[x];
+            pv.push_back(y); y = parent[y];
+        }
+        // backward arcs: on the u path (traversed apex -> u, downwards) arcs
+        // pointing up; on the v path (traversed v -> apex, upwards) arcs pointing down.
+        int64_t theta = INT64_MAX;
+        for (int z : pu) {
+            int e = parc[z];
+            if (tail[e] == z) theta = std::min(theta, flow[e]);
+        }
+        for (int z : pv) {
+            int e = parc[z];
+            if (head[e] == z) theta = std::min(theta, flow[e]);
+        }
+        if (theta == INT64_MAX) return false;  // unbounded (cannot happen here)
+        // leaving arc: last blocking arc in the order apex->u, a, v->apex
+        int leave_node = -1;
+        bool on_v = false;
+        for (int k = (int)pv.size() - 1; k >= 0; --k) {
+            int z = pv[k], e = parc[z];
+            if (head[e] == z && flow[e] == theta) { leave_node = z; on_v = true; break; }
+        }
+        if (leave_node < 0) {
+            for (int k = 0; k < (int)pu.size(); ++k) {
+                int z = pu[k], e = parc[z];
+                if (tail[e] == z && flow[e] == theta) { leave_node = z; break; }
+            }
+        }
+        // flow update
+        if (theta > 0) {
+            for (int z : pu) {
+                int e = parc[z];
+                flow[e] += (tail[e] == z) ? -theta : theta;
+            }
+            for (int z : pv) {
+                int e = parc[z];
+                flow[e] += (head[e] == z) ? -theta : theta;
+            }
+            flow[a] += theta;
+        }
+        // tree update: cut subtree below leave_node, re-hang at the endpoint of a inside it
+        int q = leave_node;
+        int r = on_v ? v : u;
+        int o = on_v ? u : v;
+        in_tree[parc[q]] = 0;
+        in_tree[a] = 1;
+        remove_child(parent[q], q);
+        // path r -> q, reversed
+        std::vector<int>& path = stack;
+        path.clear();
+        for (int z = r; z != q; z = parent[z]) path.push_back(z);
+        path.push_back(q);
+        for (size_t t = 0; t + 1 < path.size(); ++t) remove_child(path[t + 1], path[t]);
+        std::vector<int> arcs(path.size());
+        for (size_t t = 0; t + 1 < path.size(); ++t) arcs[t] = parc[path[t]];
+        for (size_t t = 0; t + 1 < path.size(); ++t) {
+            int z0 = path[t], z1 = path[t + 1];
+            parent[z1] = z0;
+            parc[z1] = arcs[t];
+            add_child(z0, z1);
+        }
+        parent[r] = o;
+        parc[r] = a;
+        add_child(o, r);
+        std::vector<int> st2;
+        refresh_subtree(r, st2);
+        ++pivots;
+        return true;
+    }
+
+    bool run() {
+        std::vector<int> pu, pv, stack;
+        const int block = std::max(16, (int)std::sqrt((double)na));
+        int next = 0;
+        while (true) {
+            int best = -1;
+            int64_t best_rc = 0;
+            int scanned = 0;
+            while (scanned < na) {
+                int lim = std::min(block, na - scanned);
+                for (int t = 0; t < lim; ++t) {
+                    int e = next;
+                    next = (next + 1 == na) ? 0 : next + 1;
+                    if (in_tree[e]) continue;
+                    int64_t r = rc(e);
+                    if (r < best_rc) { best_rc = r; best = e; }
+                }
+                scanned += lim;
+                if (best >= 0) break;
+            }
+            if (best < 0) return true;
+            if (!pivot(best, pu, pv, stack)) return false;
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m,
+                                double* w, double* value, int32_t* pivots) {
+    if (n <= 0 || !nbr || !cbar || !m || !w) return DD_ERR_ARG;
+    double msum = 0.0, cmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(m[i] > 0.0) || nbr[5 * i] != i) return DD_ERR_ARG;
+        msum += m[i];
+        for (int k = 0; k < 5; ++k) {
+            int j = nbr[5 * i + k];
+            if (j < -1 || j >= n) return DD_ERR_ARG;
+            if (j >= 0) {
+                if (!std::isfinite(cbar[5 * i + k])) return DD_ERR_ARG;
+                cmax = std::max(cmax, std::fabs(cbar[5 * i + k]));
+            }
+        }
+    }
+    NetworkSimplex ns;
+    ns.nn = 2 * n;
+    std::vector<int> arc_of(5 * n, -1);
+    std::vector<int64_t> M(n);
+    const double mscale = std::ldexp(1.0, 60) / msum;
+    for (int i = 0; i < n; ++i) M[i] = std::max<int64_t>(1, (int64_t)std::llround(m[i] * mscale));
+    const double cscale = cmax > 0.0 ? std::ldexp(1.0, 40) / cmax : 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 5; ++k) {
+            int j = nbr[5 * i + k];
+            if (j < 0) continue;
+            arc_of[5 * i + k] = ns.na++;
+            ns.tail.push_back(i);
+            ns.head.push_back(n + j);
+            ns.cost.push_back((int64_t)std::llround(cbar[5 * i + k] * cscale));
+            ns.flow.push_back(k == 0 ? M[i] : 0);
+        }
+    const int nn = ns.nn;
+    ns.parent.assign(nn, -1);
+    ns.parc.assign(nn, -1);
+    ns.depth.assign(nn, 0);
+    ns.first_child.assign(nn, -1);
+    ns.next_sib.assign(nn, -1);
+    ns.prev_sib.assign(nn, -1);
+    ns.pot.assign(nn, 0);
+    ns.in_tree.assign(ns.na, 0);
+    // spanning tree of the cell grid by breadth-first search from cell 0, over
+    // neighbour arcs; tree: s_root; t_i under s_p(i) (zero flow), s_i under t_i.
+    std::vector<int> order;
+    std::vector<char> seen(n, 0);
+    order.reserve(n);
+    order.push_back(0);
+    seen[0] = 1;
+    std::vector<int> via(n, -1), par_cell(n, -1);
+    for (size_t h = 0; h < order.size(); ++h) {
+        int p = order[h];
+        for (int k = 1; k < 5; ++k) {
+            int j = nbr[5 * p + k];
+            if (j >= 0 && !seen[j]) {
+                seen[j] = 1;
+                par_cell[j] = p;
+                via[j] = arc_of[5 * p + k];
+                order.push_back(j);
+            }
+        }
+    }
+    if ((int)order.size() != n) return DD_ERR_ARG;  // neighbourhood graph not connected
+    for (int idx = 0; idx < n; ++idx) {
+        int i = order[idx];
+        int self = arc_of[5 * i];
+        int ti = n + i;
+        if (idx > 0) {
+            int p = par_cell[i];
+            ns.parent[ti] = p;
+            ns.parc[ti] = via[i];
+            ns.in_tree[via[i]] = 1;
+            ns.add_child(p, ti);
+        }
+        ns.in_tree[self] = 1;
+        if (idx == 0) {  // root s_0; t_0 hangs below it
+            ns.parent[ti] = i;
+            ns.parc[ti] = self;
+            ns.add_child(i, ti);
+        } else {
+            ns.parent[i] = ti;
+            ns.parc[i] = self;
+            ns.add_child(ti, i);
+        }
+    }
+    {
+        std::vector<int> st;
+        for (int c = ns.first_child[0]; c >= 0; c = ns.next_sib[c]) ns.refresh_subtree(c, st);
+    }
+    if (!ns.run()) return DD_ERR_FLOW;
+    double val = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 5; ++k) {
+            int a = arc_of[5 * i + k];
+            double wi = 0.0;
+            if (a >= 0) {
+                wi = m[i] * ((double)ns.flow[a] / (double)M[i]);
+                val += wi * cbar[5 * i + k];
+            }
+            w[5 * i + k] = wi;
+        }
+    if (value) *value = val;
+    if (pivots) *pivots = (int32_t)ns.pivots;
+    return DD_OK;
+}
