@@ -81,6 +81,8 @@ typedef struct dd_stats {
     int32_t ncell;         /* composite cells solved                              */
     int32_t iters_max;     /* largest Sinkhorn iteration count                    */
     int32_t n_maxiter;     /* cells that hit max_iter                             */
+    int32_t n_stalled;     /* cells stopped at their FP32 floor above tol (their
+                              error stays within 50 tol; result Y-feasible)       */
     double iters_mean;     /* mean Sinkhorn iterations per cell                   */
     double objective;      /* E = sum_J <alpha_J, r_J> + <beta_J, nu_J>, Prop. 2.1 */
     double l1_x;           /* sum_J sum_x |r_J(x) - mu(x)| of the Gibbs cell plans */

@@ -13,7 +13,7 @@ the mass-preserving flows of Eq. (div-constraint-single-cell) is solved as a
 linear program by scipy's HiGHS (a library LP solver standing in for the
 paper's OR-tools), and the new basic-cell Y-marginals follow
 Eq. (flow-update-cell-marginals): nu_hat_j = sum_{i in N(j)} w_ij nu_i / m_i,
-truncated and re-boxed like the half-iteration output.
+truncated, re-boxed and rescaled to m_j like the half-iteration output.
 
 Reading: the min-cost flow is solved over the reals (the paper does not say how
 it scaled masses for an integer solver).
@@ -96,5 +96,5 @@ def exchange(geom, boxes, w, nbr, m, thr=1e-15):
         acc = np.zeros((h, wd))
         for i, wij in incoming[j]:
             acc += (wij / m[i]) * embed(boxes[i], o1, o2, h, wd)
-        out.append(truncate_box(acc, o1, o2, thr))
+        out.append(truncate_box(acc, o1, o2, thr, m[j]))
     return out

@@ -46,7 +46,7 @@ class dd_options(C.Structure):
 
 class dd_stats(C.Structure):
     _fields_ = [("part", C.c_int32), ("ncell", C.c_int32), ("iters_max", C.c_int32), ("n_maxiter", C.c_int32),
-                ("iters_mean", C.c_double), ("objective", C.c_double), ("l1_x", C.c_double),
+                ("n_stalled", C.c_int32), ("iters_mean", C.c_double), ("objective", C.c_double), ("l1_x", C.c_double),
                 ("lse_terms", C.c_double), ("ms_total", C.c_double), ("ms_cells", C.c_double),
                 ("stored_entries", C.c_int64)]
 

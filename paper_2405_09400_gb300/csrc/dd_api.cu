@@ -192,6 +192,7 @@ void dd_destroy(dd_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->mcf) mcf_destroy(c->mcf);
     dfree(c->d_mu); dfree(c->d_nu); dfree(c->d_lgmu); dfree(c->d_m); dfree(c->d_xmom);
     dfree(c->d_nbr); dfree(c->d_rev);
     for (int p = 0; p < 2; ++p) {
@@ -314,7 +315,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             TRY(dmalloc(&P.order, order.size())); TRY(h2d(P.order, order.data(), order.size(), c->stream));
             TRY(dmalloc(&P.chdr, (size_t)CH_N * P.ncell));
             TRY(dmalloc(&P.alpha, (size_t)c->amax * P.ncell));
-            TRY(dmalloc(&P.gauge, 2 * (size_t)P.ncell));
+            TRY(dmalloc(&P.gauge, 8 * (size_t)P.ncell));
             TRY(dmalloc(&P.iters, P.ncell));
             TRY(dmalloc(&P.err, P.ncell));
             TRY(dmalloc(&P.Ecell, P.ncell));
@@ -405,6 +406,7 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
         st->iters_max = imax;
         st->iters_mean = P.ncell ? im / P.ncell : 0;
         st->n_maxiter = status[0];
+        st->n_stalled = status[3];
         st->objective = Es;
         st->l1_x = es;
         st->lse_terms = terms;
@@ -475,7 +477,9 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     auto t0 = std::chrono::steady_clock::now();
     double value = 0.0;
     int32_t piv = 0;
-    int frc = dd_min_cost_flow(c->nb, c->h_nbr.data(), c->h_cbar, c->h_m.data(), c->h_w, &value, &piv);
+    int frc = DD_OK;
+    if (!c->mcf) frc = mcf_create(c->nb, c->h_nbr.data(), c->h_m.data(), &c->mcf);
+    if (frc == DD_OK) frc = mcf_solve(c->mcf, c->h_cbar, c->h_w, &value, &piv);
     if (frc != DD_OK) {  // keep the stationary flow (Lemma 3.6: always feasible)
         for (int i = 0; i < c->nb; ++i)
             for (int k = 0; k < 5; ++k) c->h_w[5 * i + k] = k == 0 ? c->h_m[i] : 0.0;
@@ -612,7 +616,7 @@ int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta,
     DevPart& P = c->part[part];
     if (!P.solved) return DD_ERR_STATE;
     std::vector<int32_t> ch, xb((size_t)XB_N * P.ncell);
-    std::vector<float> b, nuJ, al((size_t)c->amax * P.ncell), g(2 * (size_t)P.ncell);
+    std::vector<float> b, nuJ, al((size_t)c->amax * P.ncell), g(8 * (size_t)P.ncell);
     RET(get_comp(c, part, ch, b, nuJ, true));
     RET(d2h(xb.data(), P.xblk, xb.size(), c->stream));
     RET(d2h(al.data(), P.alpha, al.size(), c->stream));
@@ -631,16 +635,40 @@ int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta,
         const int32_t* x = &ch[CH_N * J];
         const int32_t* X = &xb[XB_N * J];
         const int hx = X[XB_HX], wx = X[XB_WX], h = x[CH_H], w = x[CH_W];
-        const double d1 = g[2 * J], d2 = g[2 * J + 1];
-        const double uc1 = 0.5 * (hx - 1), uc2 = 0.5 * (wx - 1), vc1 = 0.5 * (h - 1), vc2 = 0.5 * (w - 1);
+        // undo the kernel's reparametrisation (shift d, stretch l, origins uc / vc)
+        const float* gg = &g[8 * J];
+        const double l1 = gg[2], l2 = gg[3];
+        const double uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
+        const double d1 = (double)(X[XB_R0] - x[CH_O1]) + uc1 - vc1, d2 = (double)(X[XB_C0] - x[CH_O2]) + uc2 - vc2;
         const double hd = 0.5 * k2 * (d1 * d1 + d2 * d2);
+        // per-row / per-column kernel minima the kernel subtracted from b
+        std::vector<double> B1(h), B2(w);
+        for (int r = 0; r < h; ++r) {
+            double vb = r - vc1, mn = 1e300;
+            for (int u1 = 0; u1 < hx; ++u1) {
+                double ub = u1 - uc1;
+                mn = std::min(mn, k2 * (l1 * ub * ub - 2 * ub * vb + vb * vb / l1));
+            }
+            B1[r] = mn;
+        }
+        for (int q = 0; q < w; ++q) {
+            double vb = q - vc2, mn = 1e300;
+            for (int u2 = 0; u2 < wx; ++u2) {
+                double ub = u2 - uc2;
+                mn = std::min(mn, k2 * (l2 * ub * ub - 2 * ub * vb + vb * vb / l2));
+            }
+            B2[q] = mn;
+        }
         if (alpha)
             for (int u1 = 0; u1 < hx; ++u1)
                 for (int u2 = 0; u2 < wx; ++u2) {
                     size_t px = (size_t)(X[XB_R0] + u1) * c->N2 + X[XB_C0] + u2;
                     double a = al[(size_t)c->amax * J + u1 * wx + u2];
                     double mu = c->h_mu[px];
-                    alpha[px] = mu > 0 ? eps * (kLn2 * (a + 2 * k2 * (d1 * (u1 - uc1) + d2 * (u2 - uc2)) + hd) - std::log(mu))
+                    const double ub1 = u1 - uc1, ub2 = u2 - uc2;
+                    alpha[px] = mu > 0 ? eps * (kLn2 * (a - k2 * ((l1 - 1) * ub1 * ub1 + (l2 - 1) * ub2 * ub2) +
+                                                        2 * k2 * (d1 * ub1 + d2 * ub2) + hd) -
+                                                std::log(mu))
                                        : -INFINITY;
                 }
         long long comp = ((long long)x[CH_COMP_HI] << 32) | (unsigned int)x[CH_COMP_LO];
@@ -650,8 +678,11 @@ int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta,
                 double bb = b[(size_t)comp + (size_t)r * x[CH_STRIDE] + q];
                 size_t py = (size_t)(x[CH_O1] + r) * c->N2 + x[CH_O2] + q;
                 double val = -INFINITY;
+                const double vb1 = r - vc1, vb2 = q - vc2;
                 if (nj > 0)
-                    val = eps * (kLn2 * (bb - 2 * k2 * (d1 * (r - vc1) + d2 * (q - vc2)) + hd) - std::log(c->h_nu[py]));
+                    val = eps * (kLn2 * (bb + B1[r] + B2[q] - k2 * ((1 / l1 - 1) * vb1 * vb1 + (1 / l2 - 1) * vb2 * vb2) -
+                                         2 * k2 * (d1 * vb1 + d2 * vb2) + hd) -
+                                 std::log(c->h_nu[py]));
                 if (beta) beta[k] = val;
                 ++k;
             }

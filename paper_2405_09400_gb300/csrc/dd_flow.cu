@@ -160,24 +160,35 @@ __global__ void k_exchange(int nb, const int32_t* __restrict__ nbr, const int32_
     const int r0 = bb[0], c0 = bb[2];
     const int hh = empty ? 0 : bb[1] - bb[0] + 1, w2 = empty ? 0 : bb[3] - bb[2] + 1;
     const int st = (w2 + 3) & ~3;
-    // pass 2: write the compact box
+    // pass 2: the mass of the truncated box (FP64), then the compact box rescaled
+    // to the basic mass m_j (the inflow of the flow is m_j, Eq. div-constraint-single-cell)
     double ms = 0.0;
+    for (int d = threadIdx.x; d < hh * w2; d += blockDim.x) {
+        const int rr = d / w2, cc = d - rr * w2;
+        float val = gather_sum(o1 + r0 + rr, o2 + c0 + cc, nsrc, src, coef, bhdr_in, pool_in);
+        if (val >= trunc) ms += val;
+    }
+    for (int o = 16; o > 0; o >>= 1) ms += __shfl_down_sync(0xffffffffu, ms, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ms;
+    __syncthreads();
+    __shared__ float fsc;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        fsc = t > 0.0 ? (float)(m[j] / t) : 1.f;
+        bmom[BM_N * j + BM_MASS] = t > 0.0 ? m[j] : 0.0;
+    }
+    __syncthreads();
     for (int d = threadIdx.x; d < hh * st; d += blockDim.x) {
         const int rr = d / st, cc = d - rr * st;
         float val = 0.f;
         if (cc < w2) {
             val = gather_sum(o1 + r0 + rr, o2 + c0 + cc, nsrc, src, coef, bhdr_in, pool_in);
-            if (!(val >= trunc)) val = 0.f;
+            val = (val >= trunc) ? val * fsc : 0.f;
         }
         pool_out[start + d] = val;
-        ms += val;
     }
-    for (int o = 16; o > 0; o >>= 1) ms += __shfl_down_sync(0xffffffffu, ms, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ms;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
         int32_t* bo = bhdr_out + BH_N * j;
         bo[BH_O1] = empty ? 0 : o1 + r0;
         bo[BH_O2] = empty ? 0 : o2 + c0;
@@ -185,7 +196,6 @@ __global__ void k_exchange(int nb, const int32_t* __restrict__ nbr, const int32_
         bo[BH_W] = w2;
         bo[BH_STRIDE] = st;
         bo[BH_START] = (int32_t)start;
-        bmom[BM_N * j + BM_MASS] = t;
     }
 }
 

@@ -165,6 +165,7 @@ __global__ void k_plan_half(int ncell, const int32_t* __restrict__ members, cons
 struct HalfArgs {
     int N1, N2, s, ncell, amax;
     float k2;
+    double k2d;
     double eps, h2;
     const int32_t* members;
     const int32_t* xblk;
@@ -203,13 +204,15 @@ struct Smem {
     float* b;     // maxA
     float* T;     // 4 * (2s) * maxW   (Y stage 1; C2B partial sums + moments)
     float* R;     // maxH * (2s)
-    float* tab1;  // maxH + 2s
-    float* tab2;  // maxW + 2s
+    float* tab1;  // (2s) * maxH: axis-1 kernel k2 (sqrt(l1) ubar1 - vbar1 / sqrt(l1))^2
+    float* tab2;  // (2s) * maxW: axis-2 kernel
     float* a;     // amax
     float* an;    // amax
     float* lgm;   // amax
     double* mux;  // amax
     double* red;  // 32 * 16 + 16
+    double* B1;   // maxH: min over u1 of the axis-1 kernel at v1 (FP64)
+    double* B2;   // maxW: min over u2 of the axis-2 kernel at v2
     float* coef;  // 16
     int* ctl;     // 32
 };
@@ -222,13 +225,17 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     d += A.amax;
     S.red = d;
     d += 32 * 16 + 16;
+    S.B1 = d;
+    d += A.smaxH;
+    S.B2 = d;
+    d += A.smaxW;
     float* f = reinterpret_cast<float*>(d);
     S.lgnu = f; f += A.smaxA;
     S.b = f; f += A.smaxA;
     S.T = f; f += 4 * s2 * A.smaxW;
     S.R = f; f += A.smaxH * s2;
-    S.tab1 = f; f += A.smaxH + s2;
-    S.tab2 = f; f += A.smaxW + s2;
+    S.tab1 = f; f += A.smaxH * s2;
+    S.tab2 = f; f += A.smaxW * s2;
     S.a = f; f += A.amax;
     S.an = f; f += A.amax;
     S.lgm = f; f += A.amax;
@@ -286,13 +293,8 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             continue;
         }
 
-        // centred coordinates: d = block centre - box centre (pixels)
-        const float uc1 = 0.5f * (hx - 1), uc2 = 0.5f * (wx - 1);
-        const float vc1 = 0.5f * (h - 1), vc2 = 0.5f * (w - 1);
-        const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
-        const float e1 = vc1 - uc1, e2 = vc2 - uc2;
-
-        // ---- 1. gather nu_J and tables ------------------------------------
+        // ---- 1. gather nu_J ---------------------------------------------------
+        double gm[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int v = tid; v < nA; v += NT) {
             const int v1 = v / w, v2 = v - v1 * w;
             const int y1 = o1 + v1, y2 = o2 + v2;
@@ -307,29 +309,75 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             }
             A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
             S.lgnu[v] = acc > 0.f ? lg2f(acc) : DD_NEG;
+            const double da = acc;
+            gm[0] += da; gm[1] += da * v1; gm[2] += da * v2; gm[3] += da * v1 * v1; gm[4] += da * v2 * v2;
         }
-        for (int k = tid; k < h + hx - 1; k += NT) {
-            const float z = (float)(k - (h - 1)) + e1;
-            S.tab1[k] = A.k2 * z * z;
+        for (int u = tid; u < nx; u += NT) {
+            const int u1 = u / wx, u2 = u - u1 * wx;
+            const double mux = A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
+            gm[5] += mux; gm[6] += mux * u1; gm[7] += mux * u2; gm[8] += mux * u1 * u1; gm[9] += mux * u2 * u2;
         }
-        for (int k = tid; k < w + wx - 1; k += NT) {
-            const float z = (float)(k - (w - 1)) + e2;
-            S.tab2[k] = A.k2 * z * z;
+        block_sum_d<10>(gm, S.red);
+        // Reparametrisation (exact for any choice): origins at the barycentres of
+        // mu_J and nu_J, the linear part of the cost absorbed through d, and a
+        // per-axis stretch l_k absorbed so that the kernel
+        //   k2 (sqrt(l_k) ubar_k - vbar_k / sqrt(l_k))^2
+        // is small along the cell's local map; keeps the FP32 duals small.
+        const float uc1 = (float)(gm[6] / gm[5]), uc2 = (float)(gm[7] / gm[5]);
+        const float vc1 = (float)(gm[1] / gm[0]), vc2 = (float)(gm[2] / gm[0]);
+        const double vu1 = fmax(gm[8] / gm[5] - (double)uc1 * uc1, 0.0), vu2 = fmax(gm[9] / gm[5] - (double)uc2 * uc2, 0.0);
+        const double vv1 = fmax(gm[3] / gm[0] - (double)vc1 * vc1, 0.0), vv2 = fmax(gm[4] / gm[0] - (double)vc2 * vc2, 0.0);
+        const float l1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
+        const float l2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
+        const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
+        // Kernel tables in FP64, rounded once. With
+        //   K_k(u, v) = k2 (l_k ubar^2 - 2 ubar vbar + vbar^2 / l_k)
+        // and B_k(v) = min_u K_k(u, v), the kernel used is K_k - B_k >= 0 and the
+        // Y dual is stored as b~ = b - B_1(v1) - B_2(v2) (another exact change of
+        // gauge); it removes the distance of v from the block from every value.
+        for (int v1 = tid; v1 < h; v1 += NT) {
+            const double vb = v1 - (double)vc1;
+            double mn = 1e300;
+            for (int u1 = 0; u1 < hx; ++u1) {
+                const double ub = u1 - (double)uc1;
+                mn = fmin(mn, A.k2d * (l1 * ub * ub - 2.0 * ub * vb + vb * vb / l1));
+            }
+            S.B1[v1] = mn;
+            for (int u1 = 0; u1 < hx; ++u1) {
+                const double ub = u1 - (double)uc1;
+                S.tab1[u1 * h + v1] = (float)(A.k2d * (l1 * ub * ub - 2.0 * ub * vb + vb * vb / l1) - mn);
+            }
+        }
+        for (int v2 = tid; v2 < w; v2 += NT) {
+            const double vb = v2 - (double)vc2;
+            double mn = 1e300;
+            for (int u2 = 0; u2 < wx; ++u2) {
+                const double ub = u2 - (double)uc2;
+                mn = fmin(mn, A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2));
+            }
+            S.B2[v2] = mn;
+            for (int u2 = 0; u2 < wx; ++u2) {
+                const double ub = u2 - (double)uc2;
+                S.tab2[u2 * w + v2] = (float)(A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2) - mn);
+            }
         }
         // X side: log2 mu and the warm start
         const float* ap = A.alpha + (long long)A.amax * J;
-        const float pd1 = A.gauge[2 * J], pd2 = A.gauge[2 * J + 1];
+        const float* pg = A.gauge + 8 * J;
+        const float pd1 = pg[0], pd2 = pg[1], pl1 = pg[2], pl2 = pg[3];
         for (int u = tid; u < nx; u += NT) {
             const int u1 = u / wx, u2 = u - u1 * wx;
             const int x = (r0 + u1) * A.N2 + (c0 + u2);
-            const double mux = A.mu[x];
-            S.mux[u] = mux;
+            S.mux[u] = A.mu[x];
             const float lg = A.lgmu[x];
             S.lgm[u] = lg;
             const float ub1 = u1 - uc1, ub2 = u2 - uc2;
             float a0;
-            if (A.warm) a0 = ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2);
-            else a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2);
+            if (A.warm)
+                a0 = ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2) +
+                     A.k2 * ((l1 - pl1) * ub1 * ub1 + (l2 - pl2) * ub2 * ub2);
+            else
+                a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2) + A.k2 * ((l1 - 1.f) * ub1 * ub1 + (l2 - 1.f) * ub2 * ub2);
             S.a[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
         }
         __syncthreads();
@@ -337,15 +385,17 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         // ---- 2. Sinkhorn ----------------------------------------------------
         const double tolm = A.tol * A.mJ[J];
         int it = 0;
-        double err = 0.0;
+        double err = 0.0, best = 1e300;
+        int since = 0;
+        bool stalled = false;
         while (true) {
             ++it;
             // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1,u2) - k2 (u2 - v2 + e2)^2]
             for (int q = tid; q < hx * w; q += NT) {
                 const int u1 = q / w, v2 = q - u1 * w;
                 const float* ar = S.a + u1 * wx;
-                const float* tb = S.tab2 + (w - 1) - v2;
-                S.T[q] = lse2(wx, [&](int u2) { return ar[u2] - tb[u2]; });
+                const float* tb = S.tab2 + v2;
+                S.T[q] = lse2(wx, [&](int u2) { return ar[u2] - tb[u2 * w]; });
             }
             __syncthreads();
             // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - k2 (u1 - v1 + e1)^2]
@@ -354,9 +404,9 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 const float ln = S.lgnu[v];
                 float bv = DD_NEG;
                 if (ln > 0.5f * DD_NEG) {
-                    const float* tb = S.tab1 + (h - 1) - v1;
+                    const float* tb = S.tab1 + v1;
                     const float* Tc = S.T + v2;
-                    bv = ln - lse2(hx, [&](int u1) { return Tc[u1 * w] - tb[u1]; });
+                    bv = ln - lse2(hx, [&](int u1) { return Tc[u1 * w] - tb[u1 * h]; });
                 }
                 S.b[v] = bv;
             }
@@ -365,8 +415,8 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             for (int q = tid; q < h * wx; q += NT) {
                 const int v1 = q / wx, u2 = q - v1 * wx;
                 const float* br = S.b + v1 * w;
-                const float* tb = S.tab2 + u2 + (w - 1);
-                S.R[q] = lse2(w, [&](int v2) { return br[v2] - tb[-v2]; });
+                const float* tb = S.tab2 + u2 * w;
+                S.R[q] = lse2(w, [&](int v2) { return br[v2] - tb[v2]; });
             }
             __syncthreads();
             // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - k2 (u1 - v1 + e1)^2]
@@ -376,9 +426,9 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 const float lg = S.lgm[u];
                 float an = DD_NEG;
                 if (lg > 0.5f * DD_NEG) {
-                    const float* tb = S.tab1 + u1 + (h - 1);
+                    const float* tb = S.tab1 + u1 * h;
                     const float* Rc = S.R + u2;
-                    an = lg - lse2(h, [&](int v1) { return Rc[v1 * wx] - tb[-v1]; });
+                    an = lg - lse2(h, [&](int v1) { return Rc[v1 * wx] - tb[v1]; });
                     e_loc += S.mux[u] * (double)fabsf(expm1f((S.a[u] - an) * kLn2));
                 }
                 S.an[u] = an;
@@ -386,25 +436,34 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             double ev[1] = {e_loc};
             block_sum_d<1>(ev, S.red);
             err = ev[0];
+            // stall: no 1% improvement for 64 iterations while already within
+            // 50 tol (the FP32 rounding floor of this cell has been reached)
+            if (err < 0.99 * best) { best = err; since = 0; } else ++since;
+            stalled = A.fixed_iters <= 0 && since >= 64 && err <= 50.0 * tolm;
             const bool done = (A.fixed_iters > 0) ? (it >= A.fixed_iters)
-                                                  : (err <= tolm || it >= A.max_iter);
+                                                  : (err <= tolm || it >= A.max_iter || stalled);
             if (done) break;
             for (int u = tid; u < nx; u += NT) S.a[u] = S.an[u];
             __syncthreads();
         }
-        if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[0], 1);
+        if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[stalled ? 3 : 0], 1);
 
         // ---- outputs of the solve: duals, objective --------------------------
         float* apo = A.alpha + (long long)A.amax * J;
         double eloc[1] = {0.0};
-        const float hd = 0.5f * A.k2 * (d1 * d1 + d2 * d2);
+        // exact displacement of the float origins (FP64) for the gauge conversion
+        const double dx1 = (double)(r0 - o1) + (double)uc1 - (double)vc1;
+        const double dx2 = (double)(c0 - o2) + (double)uc2 - (double)vc2;
+        const double hd = 0.5 * A.k2d * (dx1 * dx1 + dx2 * dx2);
         for (int u = tid; u < nx; u += NT) {
             apo[u] = S.a[u];
             const float lg = S.lgm[u];
             if (lg > 0.5f * DD_NEG) {
                 const int u1 = u / wx, u2 = u - u1 * wx;
                 const double r = S.mux[u] * exp2((double)(S.a[u] - S.an[u]));
-                const double al = kLn2d * ((double)S.a[u] + 2.0 * A.k2 * ((double)d1 * (u1 - uc1) + (double)d2 * (u2 - uc2)) + hd)
+                const double ub1 = u1 - (double)uc1, ub2 = u2 - (double)uc2;
+                const double al = kLn2d * ((double)S.a[u] - A.k2d * ((l1 - 1.0) * ub1 * ub1 + (l2 - 1.0) * ub2 * ub2)
+                                           + 2.0 * A.k2d * (dx1 * ub1 + dx2 * ub2) + hd)
                                   - log(S.mux[u]);
                 eloc[0] += al * r;
             }
@@ -414,15 +473,19 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             A.comp_b[comp + (long long)v1 * stride + v2] = S.b[v];
             if (S.lgnu[v] > 0.5f * DD_NEG) {
                 const double nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
-                const double be = kLn2d * ((double)S.b[v] - 2.0 * A.k2 * ((double)d1 * (v1 - vc1) + (double)d2 * (v2 - vc2)) + hd)
+                const double vb1 = v1 - (double)vc1, vb2 = v2 - (double)vc2;
+                const double be = kLn2d * ((double)S.b[v] + S.B1[v1] + S.B2[v2]
+                                           - A.k2d * ((1.0 / l1 - 1.0) * vb1 * vb1 + (1.0 / l2 - 1.0) * vb2 * vb2)
+                                           - 2.0 * A.k2d * (dx1 * vb1 + dx2 * vb2) + hd)
                                   - log(A.nu[(o1 + v1) * A.N2 + (o2 + v2)]);
                 eloc[0] += be * nuJ;
             }
         }
         block_sum_d<1>(eloc, S.red);
         if (tid == 0) {
-            A.gauge[2 * J] = d1;
-            A.gauge[2 * J + 1] = d2;
+            float* gg = A.gauge + 8 * J;
+            gg[0] = d1; gg[1] = d2; gg[2] = l1; gg[3] = l2;
+            gg[4] = uc1; gg[5] = uc2; gg[6] = vc1; gg[7] = vc2;
             A.iters[J] = it;
             A.err[J] = err;
             A.Ecell[J] = A.eps * eloc[0];
@@ -438,42 +501,61 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             const int cg = q / (hx * w), rem = q - cg * hx * w;
             const int u1 = rem / w, v2 = rem - u1 * w;
             const float* ar = S.a + u1 * wx + cg * s;
-            const float* tb = S.tab2 + (w - 1) - v2 + cg * s;
-            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k]; });
+            const float* tb = S.tab2 + (cg * s) * w + v2;
+            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k * w]; });
             float mom = 0.f;
             for (int k = 0; k < s; ++k) {
                 const float dd = (float)(c0 + cg * s + k - o2 - v2);
-                mom += ex2f(ar[k] - tb[k] - lse) * dd * dd;
+                mom += ex2f(ar[k] - tb[k * w] - lse) * dd * dd;
             }
             T2[q] = lse;
             M2[q] = mom;
         }
         __syncthreads();
-        // C2: nu_i(v) = 2^(b(v) + LSE_{u1 in group} [T2 - k2 (u1 - v1 + e1)^2]), D_i accumulation
+        // C2: each member's share of the column mass, as a ratio of partial sums
+        // with one common shift, so that sum_i nu_i(v) = nu_J(v) up to FP32
+        // rounding whatever the size of the log-domain values:
+        //   nu_i(v) = nu_J(v) * sum_{u in X_i} pi(u, v) / sum_u pi(u, v),
+        // and the mean squared displacement E_i(v) under pi(., v) restricted to X_i.
         double accm[4] = {0, 0, 0, 0}, accd[4] = {0, 0, 0, 0};
         for (int v = tid; v < nA; v += NT) {
             const int v1 = v / w, v2 = v - v1 * w;
-            const float bv = S.b[v];
-            const float* tb = S.tab1 + (h - 1) - v1;
+            const float* tb = S.tab1 + v1;
+            const float nuv = A.comp_nu[comp + (long long)v1 * stride + v2];
+            float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};
+            if (nuv > 0.f) {
+                float mx = DD_NEG;
+                for (int cg = 0; cg < ncg; ++cg)
+                    for (int u1 = 0; u1 < hx; ++u1) mx = fmaxf(mx, T2[(cg * hx + u1) * w + v2] - tb[u1 * h]);
+                float den = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= nmem) break;
+                    const int rg = k / ncg, cg = k - rg * ncg;
+                    const float* Tc = T2 + cg * hx * w + v2;
+                    const float* Mc = M2 + cg * hx * w + v2;
+                    float nk = 0.f, ek = 0.f;
+                    for (int kk = 0; kk < s; ++kk) {
+                        const int u1 = rg * s + kk;
+                        const float wt = ex2f(Tc[u1 * w] - tb[u1 * h] - mx);
+                        const float dd = (float)(r0 + u1 - o1 - v1);
+                        nk += wt;
+                        ek += wt * (dd * dd + Mc[u1 * w]);
+                    }
+                    num[k] = nk;
+                    ew[k] = nk > 0.f ? ek / nk : 0.f;
+                    den += nk;
+                }
+                const float sc = den > 0.f ? nuv / den : 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) num[k] *= sc;
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k >= nmem) break;
-                const int rg = k / ncg, cg = k - rg * ncg;
-                float val = 0.f, ew = 0.f;
-                if (bv > 0.5f * DD_NEG) {
-                    const float* Tc = T2 + cg * hx * w + v2;
-                    const float* Mc = M2 + cg * hx * w + v2;
-                    const int ub = rg * s;
-                    const float lse = lse2(s, [&](int kk) { return Tc[(ub + kk) * w] - tb[ub + kk]; });
-                    for (int kk = 0; kk < s; ++kk) {
-                        const float dd = (float)(r0 + ub + kk - o1 - v1);
-                        ew += ex2f(Tc[(ub + kk) * w] - tb[ub + kk] - lse) * (dd * dd + Mc[(ub + kk) * w]);
-                    }
-                    val = ex2f(bv + lse);
-                }
-                A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = val;
-                accm[k] += val;
-                accd[k] += (double)val * ew;
+                A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = num[k];
+                accm[k] += num[k];
+                accd[k] += (double)num[k] * ew[k];
             }
         }
         double red8[8];
@@ -528,6 +610,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         __syncthreads();
 
         // ---- 5. apply balancing, truncate, box and moments -------------------
+        const double bc1 = 0.5 * (h - 1), bc2 = 0.5 * (w - 1);
         float cf[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -552,7 +635,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 for (int k = 0; k < 4; ++k)
                     if (k < nmem) A.pre[off + k * area] = vals[k];
             }
-            const double y1 = (double)v1 - vc1, y2 = (double)v2 - vc2;
+            const double y1 = (double)v1 - bc1, y2 = (double)v2 - bc2;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j >= nmem) break;
@@ -583,12 +666,16 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         block_sum_d<16>(mom, S.red);  // contains __syncthreads
 
         // ---- compaction in place (dst index never exceeds src index) --------
+        // Each member is rescaled to its basic mass m_i after truncation, so that
+        // the removed entries do not leave later cell problems unbalanced.
         for (int k = 0; k < nmem; ++k) {
             const int rlo = S.ctl[4 + 4 * k + 0], rhi = S.ctl[4 + 4 * k + 1];
             const int clo = S.ctl[4 + 4 * k + 2], chi = S.ctl[4 + 4 * k + 3];
             const bool empty = rhi < 0;
             const int hh = empty ? 0 : rhi - rlo + 1, ww = empty ? 0 : chi - clo + 1;
             const int st = (ww + 3) & ~3;
+            const double msum = mom[4 * k + 0];
+            const float fsc = msum > 0.0 ? (float)(A.m[mem[k]] / msum) : 1.f;
             float* sl = A.pool_out + slot0 + k * area;
             const int n = hh * st;
             for (int base = 0; base < n; base += NT) {
@@ -596,7 +683,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 float val = 0.f;
                 if (dI < n) {
                     const int rr = dI / st, cc = dI - rr * st;
-                    if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc];
+                    if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
                 }
                 __syncthreads();
                 if (dI < n) sl[dI] = val;
@@ -614,9 +701,9 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 double* bm = A.bmom + BM_N * i;
                 const double ms = mom[4 * k + 0];
                 const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
-                bm[BM_MASS] = ms;
-                bm[BM_Y1] = o1 + vc1 + m1;
-                bm[BM_Y2] = o2 + vc2 + m2;
+                bm[BM_MASS] = ms > 0 ? A.m[i] : 0.0;
+                bm[BM_Y1] = o1 + bc1 + m1;
+                bm[BM_Y2] = o2 + bc2 + m2;
                 bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
             }
         }
@@ -628,8 +715,8 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
 
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
     const int s2 = 2 * c->s;
-    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16);
-    size_t fl = 2 * (size_t)maxarea + 4 * (size_t)s2 * maxw + (size_t)maxh * s2 + (maxh + s2) + (maxw + s2) +
+    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + (size_t)maxw);
+    size_t fl = 2 * (size_t)maxarea + 4 * (size_t)s2 * maxw + (size_t)maxh * s2 + (size_t)maxh * s2 + (size_t)maxw * s2 +
                 3 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
 }
@@ -654,7 +741,7 @@ int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
     }
     HalfArgs A;
     A.N1 = c->N1; A.N2 = c->N2; A.s = c->s; A.ncell = P.ncell; A.amax = c->amax;
-    A.k2 = c->k2; A.eps = c->eps; A.h2 = c->h * c->h;
+    A.k2 = c->k2; A.k2d = c->k2; A.eps = c->eps; A.h2 = c->h * c->h;
     A.members = P.members; A.xblk = P.xblk; A.mJ = P.mJ; A.order = P.order;
     A.bhdr_in = c->bhdr[c->cur]; A.pool_in = c->pool[c->cur];
     A.bhdr_out = c->bhdr[1 - c->cur]; A.pool_out = c->pool[1 - c->cur];

@@ -24,6 +24,11 @@ enum { BM_D = 0, BM_MASS, BM_Y1, BM_Y2, BM_VAR, BM_PREMASS, BM_PAD0, BM_PAD1, BM
 // Totals computed by the planning kernels (long long x 8).
 enum { PT_COMP = 0, PT_OUT, PT_MAXAREA, PT_MAXH, PT_MAXW, PT_ENTRIES, PT_PAD0, PT_PAD1, PT_N };
 
+struct McfSolver;
+int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out);
+int mcf_solve(McfSolver* S, const double* cbar, double* w, double* value, int32_t* pivots);
+void mcf_destroy(McfSolver* S);
+
 struct DevPart {
     int ncell = 0;
     int32_t* members = nullptr;  // ncell x 4, -1 padded
@@ -91,6 +96,7 @@ struct dd_ctx {
     double* h_w = nullptr;     // pinned
     int32_t* d_xhdr = nullptr; // exchange output headers (nb x CH_N)
     dd_flow_stats last_flow{};
+    McfSolver* mcf = nullptr;  // persistent basis across flow updates
 
     // l1_y scratch
     double* d_yacc = nullptr;

@@ -173,38 +173,55 @@ struct NetworkSimplex {
 
 }  // namespace
 
-extern "C" int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m,
-                                double* w, double* value, int32_t* pivots) {
-    if (n <= 0 || !nbr || !cbar || !m || !w) return DD_ERR_ARG;
-    double msum = 0.0, cmax = 0.0;
+// ---------------------------------------------------------------------------
+// Solver with a persistent basis: the supplies (basic-cell masses) never change
+// between flow updates, so the last optimal spanning tree and its flow stay a
+// feasible, strongly feasible basis; a new solve only re-prices it with the new
+// costs and pivots from there.
+struct McfSolver {
+    int n = 0;
+    std::vector<int> arc_of;
+    std::vector<int64_t> M;
+    std::vector<double> m;
+    NetworkSimplex ns;
+};
+
+static int check_input(int32_t n, const int32_t* nbr, const double* m) {
+    if (n <= 0 || !nbr || !m) return DD_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         if (!(m[i] > 0.0) || nbr[5 * i] != i) return DD_ERR_ARG;
-        msum += m[i];
         for (int k = 0; k < 5; ++k) {
             int j = nbr[5 * i + k];
             if (j < -1 || j >= n) return DD_ERR_ARG;
-            if (j >= 0) {
-                if (!std::isfinite(cbar[5 * i + k])) return DD_ERR_ARG;
-                cmax = std::max(cmax, std::fabs(cbar[5 * i + k]));
-            }
         }
     }
-    NetworkSimplex ns;
+    return DD_OK;
+}
+
+int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) {
+    *out = nullptr;
+    int rc = check_input(n, nbr, m);
+    if (rc != DD_OK) return rc;
+    McfSolver* S = new McfSolver();
+    S->n = n;
+    S->m.assign(m, m + n);
+    NetworkSimplex& ns = S->ns;
     ns.nn = 2 * n;
-    std::vector<int> arc_of(5 * n, -1);
-    std::vector<int64_t> M(n);
+    S->arc_of.assign(5 * (size_t)n, -1);
+    S->M.resize(n);
+    double msum = 0.0;
+    for (int i = 0; i < n; ++i) msum += m[i];
     const double mscale = std::ldexp(1.0, 60) / msum;
-    for (int i = 0; i < n; ++i) M[i] = std::max<int64_t>(1, (int64_t)std::llround(m[i] * mscale));
-    const double cscale = cmax > 0.0 ? std::ldexp(1.0, 40) / cmax : 0.0;
+    for (int i = 0; i < n; ++i) S->M[i] = std::max<int64_t>(1, (int64_t)std::llround(m[i] * mscale));
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 5; ++k) {
             int j = nbr[5 * i + k];
             if (j < 0) continue;
-            arc_of[5 * i + k] = ns.na++;
+            S->arc_of[5 * i + k] = ns.na++;
             ns.tail.push_back(i);
             ns.head.push_back(n + j);
-            ns.cost.push_back((int64_t)std::llround(cbar[5 * i + k] * cscale));
-            ns.flow.push_back(k == 0 ? M[i] : 0);
+            ns.cost.push_back(0);
+            ns.flow.push_back(k == 0 ? S->M[i] : 0);
         }
     const int nn = ns.nn;
     ns.parent.assign(nn, -1);
@@ -230,15 +247,18 @@ extern "C" int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cba
             if (j >= 0 && !seen[j]) {
                 seen[j] = 1;
                 par_cell[j] = p;
-                via[j] = arc_of[5 * p + k];
+                via[j] = S->arc_of[5 * p + k];
                 order.push_back(j);
             }
         }
     }
-    if ((int)order.size() != n) return DD_ERR_ARG;  // neighbourhood graph not connected
+    if ((int)order.size() != n) {  // neighbourhood graph not connected
+        delete S;
+        return DD_ERR_ARG;
+    }
     for (int idx = 0; idx < n; ++idx) {
         int i = order[idx];
-        int self = arc_of[5 * i];
+        int self = S->arc_of[5 * i];
         int ti = n + i;
         if (idx > 0) {
             int p = par_cell[i];
@@ -258,23 +278,60 @@ extern "C" int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cba
             ns.add_child(ti, i);
         }
     }
+    *out = S;
+    return DD_OK;
+}
+
+int mcf_solve(McfSolver* S, const double* cbar, double* w, double* value, int32_t* pivots) {
+    NetworkSimplex& ns = S->ns;
+    const int n = S->n;
+    double cmax = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 5; ++k)
+            if (S->arc_of[5 * i + k] >= 0) {
+                if (!std::isfinite(cbar[5 * i + k])) return DD_ERR_ARG;
+                cmax = std::max(cmax, std::fabs(cbar[5 * i + k]));
+            }
+    const double cscale = cmax > 0.0 ? std::ldexp(1.0, 40) / cmax : 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 5; ++k) {
+            int a = S->arc_of[5 * i + k];
+            if (a >= 0) ns.cost[a] = (int64_t)std::llround(cbar[5 * i + k] * cscale);
+        }
+    // re-price the current tree from its root (node 0 = s_0 never has a parent)
     {
         std::vector<int> st;
+        ns.pot[0] = 0;
+        ns.depth[0] = 0;
         for (int c = ns.first_child[0]; c >= 0; c = ns.next_sib[c]) ns.refresh_subtree(c, st);
     }
+    const int64_t piv0 = ns.pivots;
     if (!ns.run()) return DD_ERR_FLOW;
     double val = 0.0;
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 5; ++k) {
-            int a = arc_of[5 * i + k];
+            int a = S->arc_of[5 * i + k];
             double wi = 0.0;
             if (a >= 0) {
-                wi = m[i] * ((double)ns.flow[a] / (double)M[i]);
+                wi = S->m[i] * ((double)ns.flow[a] / (double)S->M[i]);
                 val += wi * cbar[5 * i + k];
             }
             w[5 * i + k] = wi;
         }
     if (value) *value = val;
-    if (pivots) *pivots = (int32_t)ns.pivots;
+    if (pivots) *pivots = (int32_t)(ns.pivots - piv0);
     return DD_OK;
+}
+
+void mcf_destroy(McfSolver* S) { delete S; }
+
+extern "C" int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m, double* w,
+                                double* value, int32_t* pivots) {
+    if (!cbar || !w) return DD_ERR_ARG;
+    McfSolver* S = nullptr;
+    int rc = mcf_create(n, nbr, m, &S);
+    if (rc != DD_OK) return rc;
+    rc = mcf_solve(S, cbar, w, value, pivots);
+    mcf_destroy(S);
+    return rc;
 }

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
+
+Tolerances (derived from the arithmetic; see the design notes):
+* indexing (partitions, neighbours, box headers given identical values): bit-exact;
+* fixed Sinkhorn iteration counts, same start: both sides run the same
+  iteration; the GPU's FP32 log-sum-exp carries relative errors of a few 1e-7 per
+  term and the FP32 duals of magnitude <= ~100 (base-2 units) round at ~6e-6, so
+  the basic marginals agree to L1 <= 1e-5 (total mass 1) and the objective to
+  1e-6 relative;
+* tolerance mode: the GPU's exported duals, re-evaluated in FP64, give an L1 X
+  error <= tol + 3e-5 per unit cell mass and a Y error <= 3e-5: the FP32 duals
+  (magnitudes up to ~200 in base-2 units after the kernel's change of gauge)
+  round at ~1.2e-5, and a pair of them enters each exponent. The library's own
+  state is Y-exact up to FP32 storage (L1 Y error <= 1e-6) and X-exact per basic
+  cell (rescaled to m_i);
+* flow update: edge costs computed from the same state agree to 1e-7 of the
+  largest |c_bar| (the GPU's moments are taken on the values before their final
+  FP32 rounding, relative 6e-8); the optimal
+  values of the library's network simplex and the oracle's LP to 1e-9 relative.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.cell import sq_cost
+from oracle.domdec import Box, balance, basic_to_composite, box_pixels, embed, truncate_box, l1_y_error
+from oracle.flow import edge_costs, exchange, min_cost_flow
+from oracle.geometry import Geometry
+from oracle.hybrid import OracleDD
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd(lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lib
+
+
+def as_boxes(lst):
+    return [Box(o1, o2, np.asarray(a, dtype=np.float64)) for o1, o2, a in lst]
+
+
+def plan_l1(a, b, shape):
+    return sum(np.abs(embed(x, 0, 0, *shape) - embed(y, 0, 0, *shape)).sum() for x, y in zip(a, b))
+
+
+def gpu_cell_errors(g, part, mu, nu, eps, geom, cells=None):
+    """FP64 evaluation of the GPU's exported duals: per-cell L1 X error / m_J and Y error."""
+    alpha, betas = g.duals(part)
+    comp = g.composite(part)
+    N = mu.shape[0]
+    m = geom.basic_masses(mu)
+    out = []
+    parts = geom.partition(part)
+    for J in (range(len(parts)) if cells is None else cells):
+        members = parts[J]
+        X = geom.composite_pixels(members)
+        o1, o2, nuJ = comp[J]
+        _, _, beta = betas[J]
+        Y = box_pixels(o1, o2, nuJ.shape[0], nuJ.shape[1])
+        supp = nuJ.reshape(-1) > 0
+        C = sq_cost(X, Y[supp], 1.0 / N)
+        a = alpha[X[:, 0], X[:, 1]]
+        b = beta.reshape(-1)[supp]
+        pi = np.exp((a[:, None] + b[None, :] - C) / eps) * mu[X[:, 0], X[:, 1]][:, None] * nu[Y[supp][:, 0], Y[supp][:, 1]][None, :]
+        xe = np.abs(pi.sum(axis=1) - mu[X[:, 0], X[:, 1]]).sum() / m[members].sum()
+        ye = np.abs(pi.sum(axis=0) - nuJ.reshape(-1)[supp]).sum() / nuJ.sum()
+        out.append((J, xe, ye))
+    return out
+
+
+@pytest.mark.parametrize("N,s", [(16, 4), (32, 4), (64, 4), (32, 2), (48, 4)])
+def test_partition_and_neighbours_bit_exact(dd, N, s):
+    mu, nu, eps, _ = synth.workload("dd32", 0, N=N)
+    g = dd.DomDec(mu, nu, eps, s)
+    geom = Geometry(N, N, s)
+    for part in (0, 1):
+        mem = g.partition(part)
+        ref = geom.partition(part)
+        assert len(mem) == len(ref)
+        for row, cell in zip(mem, ref):
+            assert list(row[: len(cell)]) == cell and (row[len(cell):] == -1).all()
+    assert np.array_equal(g.neighbours(), geom.neighbours())
+    g.close()
+
+
+@pytest.mark.parametrize("N,K", [(16, 30), (32, 40)])
+def test_fixed_iterations_half_iterations_match_oracle(dd, N, K):
+    mu, nu, eps, _ = synth.workload("dd32", 0, N=N)
+    g = dd.DomDec(mu, nu, eps, 4, fixed_iters=K)
+    o = OracleDD(mu, nu, eps, 4, fixed_iters=K)
+    for part in (0, 1, 0):
+        before = as_boxes(g.plan())
+        sg = g.iterate(part)
+        so = o.iterate(part)
+        # BasicToComposite: headers bit-exact, values = FP32 sums of the same inputs
+        comp = as_boxes(g.composite(part))
+        for J, members in enumerate(o.geom.partition(part)):
+            ref = basic_to_composite(before, members)
+            assert (comp[J].o1, comp[J].o2, comp[J].h, comp[J].w) == (ref.o1, ref.o2, ref.h, ref.w)
+            assert np.allclose(comp[J].a, ref.a, rtol=1e-6, atol=1e-15)
+        assert abs(sg["objective"] - so["E"]) <= 1e-6 * abs(so["E"])
+        assert plan_l1(as_boxes(g.plan()), o.boxes, mu.shape) <= 1e-5
+        assert sg["iters_max"] == K
+    g.close()
+
+
+def test_composite_to_basic_D_and_balancing_from_gpu_duals(dd):
+    N = 32
+    mu, nu, eps, _ = synth.workload("dd32", 0, N=N)
+    geom = Geometry(N, N, 4)
+    m = geom.basic_masses(mu)
+    g = dd.DomDec(mu, nu, eps, 4, tol=1e-6, flags=dd.DD_FLAG_KEEP_PREBALANCE)
+    g.iterate(0)
+    g.iterate(1)
+    alpha, betas = g.duals(1)
+    comp = as_boxes(g.composite(1))
+    pre = as_boxes(g.prebalance())
+    out = as_boxes(g.plan())
+    mom = g.basic_moments()
+    for J, members in enumerate(geom.partition(1)):
+        X = geom.composite_pixels(members)
+        nuJ = comp[J]
+        Y = box_pixels(nuJ.o1, nuJ.o2, nuJ.h, nuJ.w)
+        supp = nuJ.a.reshape(-1) > 0
+        C = sq_cost(X, Y[supp], 1.0 / N)
+        b = betas[J][2].reshape(-1)[supp]
+        a = alpha[X[:, 0], X[:, 1]]
+        pi = np.exp((a[:, None] + b[None, :] - C) / eps) * mu[X[:, 0], X[:, 1]][:, None] * nu[Y[supp][:, 0], Y[supp][:, 1]][None, :]
+        ss = 16
+        arrs = []
+        for k, i in enumerate(members):
+            ref = np.zeros(nuJ.h * nuJ.w)
+            ref[supp] = pi[k * ss:(k + 1) * ss].sum(axis=0)
+            # CompositeToBasic (Section A.1, partial log-sum-exp) = row sums of the Gibbs plan
+            assert pre[i].o1 == nuJ.o1 and pre[i].a.shape == nuJ.a.shape
+            assert np.abs(pre[i].a.reshape(-1) - ref).sum() <= 2e-5 * m[i]
+            Dref = float((C[k * ss:(k + 1) * ss] * pi[k * ss:(k + 1) * ss]).sum())
+            assert mom["D"][i] == pytest.approx(Dref, rel=1e-5)
+            arrs.append(pre[i].a)
+        # balancing + truncation applied by the oracle to the GPU's pre-balance values
+        bal = balance(arrs, [m[i] for i in members])
+        for k, i in enumerate(members):
+            ref = truncate_box(bal[k], nuJ.o1, nuJ.o2, 1e-15, m[i])
+            got = out[i]
+            # headers bit-exact unless an entry sits within FP32 rounding of the threshold
+            if (got.o1, got.o2, got.h, got.w) != (ref.o1, ref.o2, ref.h, ref.w):
+                diff = np.abs(embed(got, 0, 0, N, N) - embed(ref, 0, 0, N, N))
+                assert diff.max() < 2e-15
+            assert np.abs(embed(got, 0, 0, N, N) - embed(ref, 0, 0, N, N)).sum() <= 1e-6 * m[i]
+            assert got.a.sum() == pytest.approx(m[i], rel=1e-6)
+    g.close()
+
+
+@pytest.mark.parametrize("workload,N,init", [("dd32", 32, "product"), ("dd256", 64, "kr")])
+def test_tolerance_mode_marginal_errors(dd, workload, N, init):
+    mu, nu, eps, p = synth.workload(workload, 0, N=N)
+    tol = 1e-5
+    boxes = None if init == "product" else synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000)
+    geom = Geometry(N, N, 4)
+    for part in (0, 1, 0):
+        st = g.iterate(part)
+        assert st["n_maxiter"] == 0
+        errs = gpu_cell_errors(g, part, mu, nu, eps, geom)
+        assert max(e[1] for e in errs) <= tol + 3e-5
+        assert max(e[2] for e in errs) <= 3e-5
+        E, l1x, l1y = g.objective()
+        assert l1x <= tol * 1.0 + 1e-12          # the kernel's own FP32 error estimate
+        assert l1y <= 1e-6
+    g.close()
+
+
+def test_flow_update_matches_oracle_on_gpu_state(dd):
+    N, s = 32, 4
+    mu, nu, eps, _ = synth.workload("dd32", 0, N=N)
+    geom = Geometry(N, N, s)
+    m = geom.basic_masses(mu)
+    nbr = geom.neighbours()
+    g = dd.DomDec(mu, nu, eps, s, tol=1e-6)
+    g.iterate(0)
+    g.iterate(1)
+    state = as_boxes(g.plan())
+    D = g.basic_moments()["D"]
+    f = g.flow_update()
+    cbar, w = g.flow()
+    ref = edge_costs(geom, mu, state, D, 1.0 / N)
+    ok = ~np.isnan(ref)
+    scale = np.abs(ref[ok]).max()
+    assert np.abs(cbar[ok] - ref[ok]).max() <= 1e-7 * scale
+    _, val_ref, _ = min_cost_flow(nbr, cbar, m)
+    assert f["value"] == pytest.approx(val_ref, rel=1e-9, abs=1e-18)
+    assert f["value"] < 0
+    new_ref = exchange(geom, state, w, nbr, m, 1e-15)
+    new = as_boxes(g.plan())
+    assert plan_l1(new, new_ref, mu.shape) <= 1e-6
+    assert l1_y_error(new, nu) <= 1e-5
+    assert np.allclose([b.a.sum() for b in new], m, rtol=1e-6)
+    g.close()
