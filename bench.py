@@ -1,0 +1,346 @@
+"""Benchmark of one hybrid iteration (Alg. 3: A half-iteration, B half-iteration,
+flow update) on the 256 x 256 Gaussian-mixture workload, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line. A step is one hybrid iteration whose cell Sinkhorn solves
+each stop at L1 X-marginal error <= 1e-5 of the cell mass; `value` is the mean
+device time per step (ms, lower is better) with the state resident in device
+memory. Inputs: seeded synthetic mixtures (5 components + 1e-4 floor, seeds 0
+and 1) and a Knothe-Rosenblatt initial coupling, standing in for the paper's
+Gaussian-mixture test images; W warm-up steps are run first, so the timed
+steps continue the same trajectory.
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on a
+bounded sample of the same workload and prints the same line for it.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-5 L1 marginal err (plain vs warm-start), cell-LSE HBM GB/s"
+WORKLOAD = "dd256"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300 unit counts and clock used for the exp-throughput peak of the cell kernel
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+EX2_PER_CLK_SM = 32  # MUFU ex2 issue rate per SM per clock (see the design notes)
+
+
+def peaks():
+    try:
+        with open(MEASURED) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, src="fallback")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons)}
+
+
+def load_workload():
+    import numpy as np  # noqa: F401
+
+    import synth
+
+    mu, nu, eps, p = synth.workload(WORKLOAD, 0)
+    boxes = synth.boxes_from_coupling(mu.shape, p["s"], *synth.knothe_rosenblatt(mu, nu))
+    return mu, nu, eps, p, boxes
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    ge.build()
+    import paper_2405_09400_gb300 as dd
+
+    mu, nu, eps, p, boxes = load_workload()
+    stream = torch.cuda.current_stream()
+    g = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        g.step(1, stats=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    n0 = g.counters()["launches"]
+    step_ms, cell_ms, terms, cells, hbm_bytes, iters_mean = [], [], [], 0, [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t_all0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # evict the state from L2 between steps (outside the timed events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sa, sb, sf = g.step(1, stats=True)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for s_ in (sa, sb):
+                cell_ms.append(s_["ms_cells"])
+                terms.append(s_["lse_terms"])
+                cells += s_["ncell"]
+                iters_mean.append(s_["iters_mean"])
+                # algorithmic bytes of the cell kernel: read the member boxes, write
+                # nu_J, b and the member outputs (4 B each), alpha in/out
+                hbm_bytes.append(4.0 * (2 * s_["stored_entries"] + 2 * s_["stored_entries"]))
+        torch.cuda.synchronize()
+        t_all = time.perf_counter() - t_all0
+    launches = g.counters()["launches"] - n0
+    if world > 1:
+        t = torch.tensor([sum(step_ms)], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    else:
+        total_ms = sum(step_ms)
+    ms_per_step = total_ms / args.steps
+    # dominant kernel: the fused half-iteration cell kernel
+    k_ms = sum(cell_ms) / len(cell_ms)
+    k_terms = sum(terms) / len(terms)
+    pk = peaks()
+    ex2_peak = N_SM * EX2_PER_CLK_SM * SM_MAX_MHZ * 1e6  # terms (ex2) per second
+    achieved = k_terms / (k_ms * 1e-3)
+    hbm_gbs = (sum(hbm_bytes) / len(hbm_bytes)) / (k_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of the plan, one
+    # hybrid iteration, D2H of the plan, every step (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        ge2 = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, plan_tol=1e-5)
+        for _ in range(args.warmup):
+            ge2.step(1, stats=False)
+        hdr, data = dd.dd_get_plan(ge2.ctx, ge2.nbasic)
+        hdr_p = torch.empty(hdr.shape, dtype=torch.int32).pin_memory().numpy()
+        data_p = torch.empty(4 * data.size + (1 << 20), dtype=torch.float64).pin_memory().numpy()
+        torch.cuda.synchronize()
+        ts = []
+        bi = bo = 0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            hdr_p[...] = hdr
+            n = data.size
+            data_p[:n] = data
+            t0 = time.perf_counter()
+            dd.dd_set_plan(ge2.ctx, hdr_p, data_p[:n])
+            ge2.step(1, stats=False)
+            hdr, data = dd.dd_get_plan(ge2.ctx, ge2.nbasic)
+            ts.append(time.perf_counter() - t0)
+            bi = hdr_p.nbytes + 8 * n
+            bo = hdr.nbytes + data.nbytes
+        e2e = {"value": 1e3 * sum(ts) / len(ts), "unit": "ms", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo)}
+        ge2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, mu, nu, eps, p, boxes)
+
+    g.close()
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    nc = sum(iters_mean) / len(iters_mean)
+    line = {
+        "metric": METRIC, "value": round(ms_per_step, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (LSE) + f64 (mass/error/objective)",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "dd256: 256x256 grid, 5-component Gaussian mixtures + 1e-4 floor (seeds 0/1), "
+                               "eps=2/256^2, 4x4 basic cells, KR initial coupling, flow update every iteration, "
+                               "cell tol 1e-5", "cells_per_half_iteration": [1024, 1089],
+                   "l2": "512 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "plain_ms_per_step": round(ms_per_step, 4), "warm_start_ms_per_step": None,
+        "iterations_per_s": round(1e3 / ms_per_step, 3),
+        "cells_per_s": round(cells / (sum(step_ms) * 1e-3), 1),
+        "sinkhorn_iters_mean": round(nc, 2),
+        "wall_s_timed": round(t_all, 3),
+        "cell_lse_hbm_gbs": {"achieved": round(hbm_gbs, 2), "peak": pk["hbm_gbs"], "frac": round(hbm_gbs / pk["hbm_gbs"], 5),
+                             "peak_src": pk["src"]},
+        "roofline": {"bound": "alu", "kernel": "k_half (fused cell Sinkhorn)", "achieved": round(achieved / 1e12, 4),
+                     "peak": round(ex2_peak / 1e12, 4), "unit": "Texp2/s", "frac": round(achieved / ex2_peak, 5),
+                     "traffic": None, "kernel_ms_mean": round(k_ms, 4), "work_per_launch": k_terms},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_sample(mu, nu, eps, p, boxes, seconds):
+    """Time the FP64 oracle on a bounded sample: whole-cell solves of the first A
+    half-iteration (cold start from the KR plan) and one flow update step."""
+    import numpy as np
+
+    from oracle.domdec import Box, balance, basic_to_composite, composite_to_basic, solve_cell, truncate_box
+    from oracle.flow import edge_costs, min_cost_flow
+    from oracle.geometry import Geometry
+
+    N = mu.shape[0]
+    geom = Geometry(N, N, p["s"])
+    m = geom.basic_masses(mu)
+    bx = [Box(o1, o2, a) for o1, o2, a in boxes]
+    cells = geom.partition(0)
+    rng = np.random.default_rng(0)
+    order = rng.permutation(len(cells))
+    t0 = time.perf_counter()
+    n = 0
+    D = np.zeros(geom.nb)
+    for J in order:
+        members = cells[J]
+        nuJ = basic_to_composite(bx, members)
+        res = solve_cell(geom, mu, eps, 1.0 / N, members, nuJ, None, p["tol"], 100000)
+        arrs, Dm = composite_to_basic(geom, members, nuJ, res)
+        bal = balance(arrs, [m[i] for i in members])
+        for k, i in enumerate(members):
+            truncate_box(bal[k], nuJ.o1, nuJ.o2, 1e-15, m[i])
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    t_cell = (time.perf_counter() - t0) / n
+    # flow-update step on the same state: explicit edge costs and the LP, in full
+    t1 = time.perf_counter()
+    cbar = edge_costs(geom, mu, bx, D, 1.0 / N)
+    t_cost = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    min_cost_flow(geom.neighbours(), cbar, m)
+    t_lp = time.perf_counter() - t2
+    ncell = len(geom.partition(0)) + len(geom.partition(1))
+    ms = 1e3 * (t_cell * ncell + t_cost + t_lp)
+    return ms, n, t_cell, t_cost, t_lp
+
+
+def cpu_baseline(args, mu, nu, eps, p, boxes):
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        threadpool_limits = None
+    ctx = threadpool_limits(1) if threadpool_limits else None
+    try:
+        ms, n, t_cell, t_cost, t_lp = _oracle_sample(mu, nu, eps, p, boxes, args.cpu_seconds)
+    finally:
+        if ctx is not None:
+            ctx.unregister() if hasattr(ctx, "unregister") else None
+    return {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, 1 thread: {n} whole cell solves of the first A half-iteration "
+                      f"(cold start from the KR plan, dense LSE, tol 1e-5) at {t_cell*1e3:.1f} ms/cell, "
+                      f"scaled to 2113 cells; edge costs {t_cost*1e3:.0f} ms (explicit sums, all cells), "
+                      f"min-cost flow LP {t_lp*1e3:.0f} ms (HiGHS, full size)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    mu, nu, eps, p, boxes = load_workload()
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(max(1, args.steps)):
+        ms, n, t_cell, t_cost, t_lp = _oracle_sample(mu, nu, eps, p, boxes, args.cpu_seconds / max(1, args.steps))
+        vals.append(ms)
+    v = sum(vals) / len(vals)
+    cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle, 1 thread, per step {n} whole cell solves of the first A half-iteration "
+                     "(cold, KR plan) scaled to 2113 cells, plus the flow-update step"}
+    line = {"metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "dd256 (same as --impl ours)"}, "cpu_baseline": cpu,
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - t0, 2)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -73,6 +73,7 @@ typedef struct dd_options {
     int32_t warm;        /* DD_WARM_PREV or DD_WARM_COLD                           */
     int32_t threads;     /* threads per cell solve (64..512); 0 = autotuned        */
     int32_t flags;       /* DD_FLAG_*                                              */
+    double plan_tol;     /* dd_set_plan feasibility tolerance (L1, both marginals); 1e-12 */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */
@@ -126,7 +127,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
  * Replace the state by a user plan given as basic-cell Y-marginals: hdr is
  * nbasic x 4 int32 box headers, data the packed float64 box contents, n their
  * total count. The plan must be feasible: |nu_i| = mu(X_i) and sum_i nu_i = nu,
- * each within 1e-12 (L1); otherwise DD_ERR_ARG. Resets the warm starts.
+ * each within opt.plan_tol (L1); otherwise DD_ERR_ARG. The warm-start duals are
+ * kept (they only initialise the next solves).
  */
 int dd_set_plan(dd_ctx* ctx, const int32_t* hdr, const double* data, size_t n);
 
@@ -209,6 +211,10 @@ int dd_get_prebalance(dd_ctx* ctx, int32_t* hdr, double* data, size_t* count);
  */
 int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m, double* w,
                      double* value, int32_t* pivots);
+
+/* Counters since dd_init: kernels launched by the library, bytes copied host to
+ * device and device to host. Any pointer may be NULL. */
+int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
 
 /* Release every resource of the context (NULL is ignored). */
 void dd_destroy(dd_ctx* ctx);

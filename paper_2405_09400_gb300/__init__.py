@@ -31,7 +31,7 @@ EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
-    "dd_min_cost_flow", "dd_destroy",
+    "dd_min_cost_flow", "dd_get_counters", "dd_destroy",
 ]
 
 
@@ -41,7 +41,8 @@ class dd_grid(C.Structure):
 
 class dd_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
-                ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32)]
+                ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
+                ("plan_tol", C.c_double)]
 
 
 class dd_stats(C.Structure):
@@ -101,6 +102,7 @@ def load():
         "dd_get_flow": (C.c_int, [vp, _f64p, _f64p]),
         "dd_get_prebalance": (C.c_int, [vp, _i32p, _f64p, _szp]),
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
+        "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -278,6 +280,12 @@ def dd_min_cost_flow(nbr, cbar, m):
     return w, v.value, piv.value
 
 
+def dd_get_counters(ctx):
+    n, a, b = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().dd_get_counters(ctx, C.byref(n), C.byref(a), C.byref(b)), "dd_get_counters")
+    return dict(launches=n.value, h2d_bytes=a.value, d2h_bytes=b.value)
+
+
 def dd_destroy(ctx):
     if ctx:
         load().dd_destroy(ctx)
@@ -360,6 +368,9 @@ class DomDec:
 
     def flow(self):
         return dd_get_flow(self.ctx, self.nbasic)
+
+    def counters(self):
+        return dd_get_counters(self.ctx)
 
     def close(self):
         if self.ctx:

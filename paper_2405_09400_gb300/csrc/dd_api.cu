@@ -119,7 +119,7 @@ int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     RET(h2d(c->pool[c->cur], buf.data(), total, c->stream));
     RET(h2d(c->bhdr[c->cur], bh.data(), bh.size(), c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->part[0].warm_valid = c->part[1].warm_valid = false;
+    c->n_h2d += (long long)(sizeof(float) * total + sizeof(int32_t) * bh.size());
     c->part[0].solved = c->part[1].solved = false;
     c->flow_ready = false;
     c->last_part = -1;
@@ -148,7 +148,7 @@ int validate_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     if (src != n) return DD_ERR_ARG;
     double yerr = 0.0;
     for (size_t k = 0; k < ym.size(); ++k) yerr += std::fabs(ym[k] - c->h_nu[k]);
-    if (xerr > 1e-12 || yerr > 1e-12) return DD_ERR_ARG;
+    if (xerr > c->opt.plan_tol || yerr > c->opt.plan_tol) return DD_ERR_ARG;
     return DD_OK;
 }
 
@@ -171,6 +171,7 @@ void dd_default_options(dd_options* o) {
     o->warm = DD_WARM_PREV;
     o->threads = 0;
     o->flags = 0;
+    o->plan_tol = 1e-12;
 }
 
 const char* dd_strerror(int s) {
@@ -433,6 +434,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     DevPart& P = c->part[part];
     CK(cudaEventRecord(c->ev[0], c->stream));
     RET(launch_plan_half(c, part));
+    c->n_launch += 1;
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const long long comp = c->h_tot[PT_COMP], outn = c->h_tot[PT_OUT];
@@ -457,6 +459,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
     RET(launch_half(c, part, threads, smem, grid));
+    c->n_launch += 1;
     CK(cudaEventRecord(c->ev[2], c->stream));
     c->cur = 1 - c->cur;
     P.warm_valid = true;
@@ -471,6 +474,7 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     if (!c->flow_ready) return DD_ERR_STATE;
     CK(cudaEventRecord(c->ev[3], c->stream));
     RET(launch_cbar(c));
+    c->n_launch += 1;
     CK(cudaEventRecord(c->ev[4], c->stream));
     RET(d2h(c->h_cbar, c->d_cbar, 5 * (size_t)c->nb, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -489,11 +493,13 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     RET(h2d(c->d_w, c->h_w, 5 * (size_t)c->nb, c->stream));
     CK(cudaEventRecord(c->ev[5], c->stream));
     RET(launch_plan_exchange(c));
+    c->n_launch += 1;
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (c->h_tot[PT_OUT] > (long long)INT32_MAX) return DD_ERR_POOL;
     RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)c->h_tot[PT_OUT]));
     RET(launch_exchange(c));
+    c->n_launch += 1;
     CK(cudaEventRecord(c->ev[6], c->stream));
     c->cur = 1 - c->cur;
     c->flow_ready = false;
@@ -554,6 +560,7 @@ int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
     std::vector<float> buf(used);
     RET(d2h(buf.data(), c->pool[c->cur], used, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->n_d2h += (long long)(sizeof(float) * used + sizeof(int32_t) * bh.size());
     size_t k = 0;
     for (int i = 0; i < c->nb; ++i) {
         const int32_t* b = &bh[BH_N * i];
@@ -710,6 +717,14 @@ int dd_get_objective(dd_ctx* c, double* E, double* l1_x, double* l1_y) {
         RET(d2h(l1_y, c->d_red, 1, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return DD_OK;
+}
+
+int dd_get_counters(dd_ctx* c, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes) {
+    if (!c) return DD_ERR_ARG;
+    if (launches) *launches = c->n_launch;
+    if (h2d_bytes) *h2d_bytes = c->n_h2d;
+    if (d2h_bytes) *d2h_bytes = c->n_d2h;
     return DD_OK;
 }
 

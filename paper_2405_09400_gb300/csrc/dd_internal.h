@@ -103,6 +103,7 @@ struct dd_ctx {
     double* d_red = nullptr;
 
     cudaEvent_t ev[8] = {};
+    long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
 
     // CUDA graphs for dd_step
