@@ -74,6 +74,9 @@ typedef struct dd_options {
     int32_t threads;     /* threads per cell solve (64..512); 0 = autotuned        */
     int32_t flags;       /* DD_FLAG_*                                              */
     double plan_tol;     /* dd_set_plan feasibility tolerance (L1, both marginals); 1e-12 */
+    double omega;        /* X-update over-relaxation a <- a + omega (X(b) - a): 1 = plain
+                            Sinkhorn (default, the paper's solver), (1, 2) fixed, < 0
+                            adaptive; same fixed point and the same stopping pair      */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */
@@ -211,6 +214,13 @@ int dd_get_prebalance(dd_ctx* ctx, int32_t* hdr, double* data, size_t* count);
  */
 int dd_min_cost_flow(int32_t n, const int32_t* nbr, const double* cbar, const double* m, double* w,
                      double* value, int32_t* pivots);
+
+/* Diagnostics: the raw FP32 values the cell kernel kept for composite cell J of
+ * `part`: its X dual a (hx * wx, base 2, the kernel's gauge), its Y dual b~ on the
+ * composite box (h * w), the 8 gauge parameters (d1, d2, l1, l2, uc1, uc2, vc1,
+ * vc2) and the X block / box (r0, c0, hx, wx, o1, o2, h, w). Buffers hold at
+ * least (2 cell_size)^2, h * w, 8 and 8 entries; pass NULL for b to get h, w. */
+int dd_debug_cell(dd_ctx* ctx, int part, int J, float* a, float* b, float* gauge, int32_t* geom);
 
 /* Counters since dd_init: kernels launched by the library, bytes copied host to
  * device and device to host. Any pointer may be NULL. */

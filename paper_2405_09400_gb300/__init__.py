@@ -31,7 +31,7 @@ EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
-    "dd_min_cost_flow", "dd_get_counters", "dd_destroy",
+    "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_destroy",
 ]
 
 
@@ -42,7 +42,7 @@ class dd_grid(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
-                ("plan_tol", C.c_double)]
+                ("plan_tol", C.c_double), ("omega", C.c_double)]
 
 
 class dd_stats(C.Structure):
@@ -103,6 +103,7 @@ def load():
         "dd_get_prebalance": (C.c_int, [vp, _i32p, _f64p, _szp]),
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
         "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
+        "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -284,6 +285,20 @@ def dd_get_counters(ctx):
     n, a, b = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load().dd_get_counters(ctx, C.byref(n), C.byref(a), C.byref(b)), "dd_get_counters")
     return dict(launches=n.value, h2d_bytes=a.value, d2h_bytes=b.value)
+
+
+def dd_debug_cell(ctx, part, J, amax):
+    """Raw FP32 kernel values of one composite cell (diagnostics)."""
+    _f32p = P(C.c_float)
+    geom = np.zeros(8, dtype=np.int32)
+    _check(load().dd_debug_cell(ctx, int(part), int(J), None, None, None, _ptr(geom, _i32p)), "dd_debug_cell")
+    a = np.zeros(amax, dtype=np.float32)
+    b = np.zeros(int(geom[6]) * int(geom[7]), dtype=np.float32)
+    g = np.zeros(8, dtype=np.float32)
+    _check(load().dd_debug_cell(ctx, int(part), int(J), _ptr(a, _f32p), _ptr(b, _f32p), _ptr(g, _f32p),
+                                _ptr(geom, _i32p)), "dd_debug_cell")
+    hx, wx = int(geom[2]), int(geom[3])
+    return dict(a=a[:hx * wx].reshape(hx, wx), b=b.reshape(int(geom[6]), int(geom[7])), gauge=g, geom=geom)
 
 
 def dd_destroy(ctx):

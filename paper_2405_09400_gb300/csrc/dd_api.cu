@@ -172,6 +172,7 @@ void dd_default_options(dd_options* o) {
     o->threads = 0;
     o->flags = 0;
     o->plan_tol = 1e-12;
+    o->omega = 1.0;
 }
 
 const char* dd_strerror(int s) {
@@ -230,11 +231,16 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     dd_ctx* c = new (std::nothrow) dd_ctx();
     if (!c) return DD_ERR_OOM;
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
-    if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0)) { delete c; return DD_ERR_ARG; }
+    if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
+        (c->opt.omega >= 0.0 && c->opt.omega < 1.0)) {
+        delete c;
+        return DD_ERR_ARG;
+    }
     c->N1 = N1; c->N2 = N2; c->s = s; c->n1 = N1 / s; c->n2 = N2 / s; c->nb = c->n1 * c->n2;
     c->amax = 4 * s * s;
     c->h = grid->h; c->eps = eps;
-    c->k2 = (float)(grid->h * grid->h / eps / kLn2);
+    c->k2d = grid->h * grid->h / eps / kLn2;
+    c->k2 = (float)c->k2d;
     c->stream = (cudaStream_t)stream;
     c->h_mu.assign(mu, mu + np);
     c->h_nu.assign(nu, nu + np);
@@ -449,6 +455,21 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     }
     RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)outn));
     if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(&c->d_pre, &c->pre_cap, (size_t)outn));
+    {
+        // work queue order: longest expected solve first (box area x the cell's
+        // previous Sinkhorn iteration count), so that the slowest cells start at once
+        std::vector<int32_t> ch((size_t)CH_N * P.ncell), itp(P.ncell, 1);
+        RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
+        if (P.warm_valid) RET(d2h(itp.data(), P.iters, P.ncell, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::vector<double> key(P.ncell);
+        for (int J = 0; J < P.ncell; ++J)
+            key[J] = (double)ch[CH_N * J + CH_H] * ch[CH_N * J + CH_W] * std::max(1, itp[J]);
+        std::vector<int32_t> order(P.ncell);
+        for (int J = 0; J < P.ncell; ++J) order[J] = J;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return key[x] > key[y]; });
+        RET(h2d(P.order, order.data(), order.size(), c->stream));
+    }
     const size_t smem = half_smem_bytes(c, c->h_tot[PT_MAXAREA], c->h_tot[PT_MAXH], c->h_tot[PT_MAXW]);
     if (smem > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
     const int threads = choose_threads(c, c->h_tot[PT_MAXAREA]);
@@ -636,7 +657,7 @@ int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta,
             for (int k = 0; k < 4; ++k) hdr[4 * J + k] = ch[CH_N * J + k];
     if (!beta && !alpha) { *count = n; return DD_OK; }
     if (beta && *count < n) return DD_ERR_ARG;
-    const double k2 = c->k2, eps = c->eps;
+    const double k2 = c->k2d, eps = c->eps;
     size_t k = 0;
     for (int J = 0; J < P.ncell; ++J) {
         const int32_t* x = &ch[CH_N * J];
@@ -717,6 +738,27 @@ int dd_get_objective(dd_ctx* c, double* E, double* l1_x, double* l1_y) {
         RET(d2h(l1_y, c->d_red, 1, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return DD_OK;
+}
+
+int dd_debug_cell(dd_ctx* c, int part, int J, float* a, float* b, float* gauge, int32_t* geom) {
+    if (!c || part < 0 || part > 1 || !geom) return DD_ERR_ARG;
+    DevPart& P = c->part[part];
+    if (!P.solved || J < 0 || J >= P.ncell) return DD_ERR_STATE;
+    int32_t ch[CH_N];
+    RET(d2h(ch, P.chdr + (size_t)CH_N * J, CH_N, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int32_t* X = &P.h_xblk[XB_N * J];
+    int32_t gm[8] = {X[XB_R0], X[XB_C0], X[XB_HX], X[XB_WX], ch[CH_O1], ch[CH_O2], ch[CH_H], ch[CH_W]};
+    std::memcpy(geom, gm, sizeof(gm));
+    if (a) RET(d2h(a, P.alpha + (size_t)c->amax * J, (size_t)X[XB_HX] * X[XB_WX], c->stream));
+    if (gauge) RET(d2h(gauge, P.gauge + 8 * (size_t)J, 8, c->stream));
+    if (b) {
+        long long comp = ((long long)ch[CH_COMP_HI] << 32) | (unsigned int)ch[CH_COMP_LO];
+        for (int r = 0; r < ch[CH_H]; ++r)
+            RET(d2h(b + (size_t)r * ch[CH_W], P.comp_b + comp + (size_t)r * ch[CH_STRIDE], ch[CH_W], c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
     return DD_OK;
 }
 

@@ -100,6 +100,15 @@ __device__ long long block_exscan(long long x, long long* sh, long long* total) 
     return base + inc - x;
 }
 
+// Row stride of the box arrays in shared memory: a multiple of 4 floats (float4
+// access) whose quarter is odd, so that the rows touched by one warp fall in
+// different 16-byte bank groups.
+__host__ __device__ __forceinline__ int padw(int w) {
+    int s = (w + 3) & ~3;
+    if (((s >> 2) & 1) == 0) s += 4;
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // planning: union boxes and pool offsets (one CTA)
 __global__ void k_plan_half(int ncell, const int32_t* __restrict__ members, const int32_t* __restrict__ bhdr,
@@ -132,7 +141,7 @@ __global__ void k_plan_half(int ncell, const int32_t* __restrict__ members, cons
         long long area = (long long)h * stride;
         sa += area;
         so += area * xblk[XB_N * J + XB_NMEM];
-        ma = max(ma, (long long)h * w);
+        ma = max(ma, (long long)h * padw(w));
         mh = max(mh, (long long)h);
         mw = max(mw, (long long)w);
     }
@@ -186,6 +195,7 @@ struct HalfArgs {
     const double* nu;
     const double* m;
     double tol;
+    float omega;  // 1: plain Sinkhorn; (1, 2): fixed over-relaxation; < 0: adaptive
     int max_iter, fixed_iters;
     float trunc;
     int32_t* iters;
@@ -198,21 +208,20 @@ struct HalfArgs {
     int smaxA, smaxH, smaxW;  // shared-memory capacities
 };
 
-// shared-memory layout (floats unless noted)
+// shared-memory layout (floats unless noted); BS = padw(max box width)
 struct Smem {
-    float* lgnu;  // maxA
-    float* b;     // maxA
-    float* T;     // 4 * (2s) * maxW   (Y stage 1; C2B partial sums + moments)
-    float* R;     // maxH * (2s)
-    float* tab1;  // (2s) * maxH: axis-1 kernel k2 (sqrt(l1) ubar1 - vbar1 / sqrt(l1))^2
-    float* tab2;  // (2s) * maxW: axis-2 kernel
-    float* a;     // amax
-    float* an;    // amax
+    float* lgnu;  // maxH * BS: log2 nu_J (DD_NEG where nu_J = 0 and in the padding)
+    float* b;     // maxH * BS: Y dual b~ (DD_NEG where nu_J = 0 and in the padding)
+    float* T;     // 4 * (2s) * BS: Y stage 1; CompositeToBasic partial sums + moments
+    float* R;     // maxH * (2s): X stage 1
+    float* tab1;  // (2s) * maxH: axis-1 kernel (gauge-reduced)
+    float* tab2;  // (2s) * BS: axis-2 kernel (gauge-reduced, 0 in the padding)
+    float* a;     // 2 * amax: X dual, ping-pong
     float* lgm;   // amax
     double* mux;  // amax
     double* red;  // 32 * 16 + 16
     double* B1;   // maxH: min over u1 of the axis-1 kernel at v1 (FP64)
-    double* B2;   // maxW: min over u2 of the axis-2 kernel at v2
+    double* B2;   // BS: min over u2 of the axis-2 kernel at v2
     float* coef;  // 16
     int* ctl;     // 32
 };
@@ -220,6 +229,7 @@ struct Smem {
 __device__ Smem carve(char* base, const HalfArgs& A) {
     Smem S;
     const int s2 = 2 * A.s;
+    const int BS = padw(A.smaxW);
     double* d = reinterpret_cast<double*>(base);
     S.mux = d;
     d += A.amax;
@@ -228,23 +238,22 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.B1 = d;
     d += A.smaxH;
     S.B2 = d;
-    d += A.smaxW;
-    float* f = reinterpret_cast<float*>(d);
+    d += BS;
+    float* f = reinterpret_cast<float*>(((uintptr_t)d + 15) & ~(uintptr_t)15);  // float4 rows
     S.lgnu = f; f += A.smaxA;
     S.b = f; f += A.smaxA;
-    S.T = f; f += 4 * s2 * A.smaxW;
+    S.T = f; f += 4 * s2 * BS;
     S.R = f; f += A.smaxH * s2;
     S.tab1 = f; f += A.smaxH * s2;
-    S.tab2 = f; f += A.smaxW * s2;
-    S.a = f; f += A.amax;
-    S.an = f; f += A.amax;
+    S.tab2 = f; f += BS * s2;
+    S.a = f; f += 2 * A.amax;
     S.lgm = f; f += A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     return S;
 }
 
-// log2 sum_k 2^t_k for a line read through a functor, two passes
+// log2 sum_k 2^t_k for a line read through a functor, two passes (exact shift)
 template <typename F>
 __device__ __forceinline__ float lse2(int n, F term) {
     float m = DD_NEG;
@@ -254,10 +263,15 @@ __device__ __forceinline__ float lse2(int n, F term) {
     return m + lg2f(s);
 }
 
+// a sum s = sum_k 2^(t_k - m) taken with a guessed shift m is trusted when it
+// neither over- nor underflows: then no significant term was flushed to zero
+__device__ __forceinline__ bool shift_ok(float s) { return s >= 8.67e-19f && s <= 1.15e18f; }  // 2^-60 .. 2^60
+
 __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
     Smem S = carve(smem_raw, A);
     const int tid = threadIdx.x, NT = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5;
     const int s = A.s;
 
     while (true) {
@@ -274,6 +288,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         const long long slot0 = ch[CH_OUT_SLOT];
         const long long area = (long long)h * stride;
         const int nx = hx * wx, nA = h * w;
+        const int bs = padw(w), bq = bs >> 2;
         int32_t mem[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
@@ -295,23 +310,29 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
 
         // ---- 1. gather nu_J ---------------------------------------------------
         double gm[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int v = tid; v < nA; v += NT) {
-            const int v1 = v / w, v2 = v - v1 * w;
-            const int y1 = o1 + v1, y2 = o2 + v2;
-            float acc = 0.f;
+        for (int v = tid; v < h * bs; v += NT) {
+            const int v1 = v / bs, v2 = v - v1 * bs;
+            float lg = DD_NEG;
+            if (v2 < w) {
+                const int y1 = o1 + v1, y2 = o2 + v2;
+                float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (mem[k] < 0) continue;
-                const int32_t* bh = A.bhdr_in + BH_N * mem[k];
-                const int p1 = y1 - bh[BH_O1], p2 = y2 - bh[BH_O2];
-                if (p1 >= 0 && p1 < bh[BH_H] && p2 >= 0 && p2 < bh[BH_W])
-                    acc += A.pool_in[(long long)bh[BH_START] + (long long)p1 * bh[BH_STRIDE] + p2];
+                for (int k = 0; k < 4; ++k) {
+                    if (mem[k] < 0) continue;
+                    const int32_t* bh = A.bhdr_in + BH_N * mem[k];
+                    const int p1 = y1 - bh[BH_O1], p2 = y2 - bh[BH_O2];
+                    if (p1 >= 0 && p1 < bh[BH_H] && p2 >= 0 && p2 < bh[BH_W])
+                        acc += A.pool_in[(long long)bh[BH_START] + (long long)p1 * bh[BH_STRIDE] + p2];
+                }
+                A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
+                if (acc > 0.f) lg = lg2f(acc);
+                const double da = acc;
+                gm[0] += da; gm[1] += da * v1; gm[2] += da * v2; gm[3] += da * v1 * v1; gm[4] += da * v2 * v2;
             }
-            A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
-            S.lgnu[v] = acc > 0.f ? lg2f(acc) : DD_NEG;
-            const double da = acc;
-            gm[0] += da; gm[1] += da * v1; gm[2] += da * v2; gm[3] += da * v1 * v1; gm[4] += da * v2 * v2;
+            S.lgnu[v] = lg;
+            S.b[v] = DD_NEG;
         }
+        for (int q = tid; q < hx * bs; q += NT) S.T[q] = DD_NEG;
         for (int u = tid; u < nx; u += NT) {
             const int u1 = u / wx, u2 = u - u1 * wx;
             const double mux = A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
@@ -348,7 +369,11 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 S.tab1[u1 * h + v1] = (float)(A.k2d * (l1 * ub * ub - 2.0 * ub * vb + vb * vb / l1) - mn);
             }
         }
-        for (int v2 = tid; v2 < w; v2 += NT) {
+        for (int v2 = tid; v2 < bs; v2 += NT) {
+            if (v2 >= w) {
+                for (int u2 = 0; u2 < wx; ++u2) S.tab2[u2 * bs + v2] = 0.f;
+                continue;
+            }
             const double vb = v2 - (double)vc2;
             double mn = 1e300;
             for (int u2 = 0; u2 < wx; ++u2) {
@@ -358,10 +383,12 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             S.B2[v2] = mn;
             for (int u2 = 0; u2 < wx; ++u2) {
                 const double ub = u2 - (double)uc2;
-                S.tab2[u2 * w + v2] = (float)(A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2) - mn);
+                S.tab2[u2 * bs + v2] = (float)(A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2) - mn);
             }
         }
         // X side: log2 mu and the warm start
+        float* aC = S.a;
+        float* aN = S.a + A.amax;
         const float* ap = A.alpha + (long long)A.amax * J;
         const float* pg = A.gauge + 8 * J;
         const float pd1 = pg[0], pd2 = pg[1], pl1 = pg[2], pl2 = pg[3];
@@ -378,74 +405,229 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                      A.k2 * ((l1 - pl1) * ub1 * ub1 + (l2 - pl2) * ub2 * ub2);
             else
                 a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2) + A.k2 * ((l1 - 1.f) * ub1 * ub1 + (l2 - 1.f) * ub2 * ub2);
-            S.a[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
+            aC[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
+        }
+        {
+            // the duals are defined up to (a + C, b - C): start every solve with
+            // a mu-weighted mean of zero, so that no constant accumulates across
+            // warm starts and the FP32 values keep their resolution
+            double cm[1] = {0.0};
+            for (int u = tid; u < nx; u += NT)
+                if (aC[u] > 0.5f * DD_NEG) cm[0] += S.mux[u] * (double)aC[u];
+            block_sum_d<1>(cm, S.red);
+            const float shift = (float)(cm[0] / gm[5]);
+            for (int u = tid; u < nx; u += NT)
+                if (aC[u] > 0.5f * DD_NEG) aC[u] -= shift;
         }
         __syncthreads();
 
-        // ---- 2. Sinkhorn ----------------------------------------------------
+        // ---- 2. Sinkhorn (4 barriers per iteration) ----------------------------
+        // Every log-sum-exp is first taken with the previous iteration's value of
+        // the same line as the shift (one pass); lines whose sum over- or
+        // underflows, and all lines of the first iteration, use the exact max.
         const double tolm = A.tol * A.mJ[J];
         int it = 0;
         double err = 0.0, best = 1e300;
         int since = 0;
-        bool stalled = false;
+        bool stalled = false, first = true;
+        // over-relaxation of the X-update (same fixed point): a <- a + w (X(b) - a).
+        // Adaptive: plain for the first iterations, then w from the observed
+        // contraction r of the error, w = 2 / (1 + sqrt(1 - r)) (Young's rule).
+        float om = A.omega > 1.f ? A.omega : 1.f;
+        double err_prev = 0.0, err_mark = 0.0;
+        int om_start = 5;
+        // threads per line of the X-update stage 2 (a power of two, lanes adjacent)
+        int P2 = 1;
+        while (P2 * 2 * nx <= NT && P2 < 16) P2 *= 2;
+        const float4* b4 = reinterpret_cast<const float4*>(S.b);
+        const float4* t24 = reinterpret_cast<const float4*>(S.tab2);
+        const int nq = (w + 3) >> 2;  // float4 groups holding data per row
         while (true) {
             ++it;
-            // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1,u2) - k2 (u2 - v2 + e2)^2]
+            // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1, u2) - K2(u2, v2)]
             for (int q = tid; q < hx * w; q += NT) {
                 const int u1 = q / w, v2 = q - u1 * w;
-                const float* ar = S.a + u1 * wx;
+                const float* ar = aC + u1 * wx;
                 const float* tb = S.tab2 + v2;
-                S.T[q] = lse2(wx, [&](int u2) { return ar[u2] - tb[u2 * w]; });
-            }
-            __syncthreads();
-            // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - k2 (u1 - v1 + e1)^2]
-            for (int v = tid; v < nA; v += NT) {
-                const int v1 = v / w, v2 = v - v1 * w;
-                const float ln = S.lgnu[v];
-                float bv = DD_NEG;
-                if (ln > 0.5f * DD_NEG) {
-                    const float* tb = S.tab1 + v1;
-                    const float* Tc = S.T + v2;
-                    bv = ln - lse2(hx, [&](int u1) { return Tc[u1 * w] - tb[u1 * h]; });
+                float m = first ? 0.f : S.T[u1 * bs + v2];
+                float sacc = 0.f;
+                if (!first) {
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int u2 = 0; u2 < 16; u2 += 2) {
+                        if (u2 >= wx) break;
+                        s0 += ex2f(ar[u2] - tb[u2 * bs] - m);
+                        if (u2 + 1 < wx) s1 += ex2f(ar[u2 + 1] - tb[(u2 + 1) * bs] - m);
+                    }
+                    sacc = s0 + s1;
                 }
-                S.b[v] = bv;
+                if (first || !shift_ok(sacc)) {
+                    m = DD_NEG;
+                    for (int u2 = 0; u2 < wx; ++u2) m = fmaxf(m, ar[u2] - tb[u2 * bs]);
+                    sacc = 0.f;
+                    for (int u2 = 0; u2 < wx; ++u2) sacc += ex2f(ar[u2] - tb[u2 * bs] - m);
+                }
+                S.T[u1 * bs + v2] = m + lg2f(sacc);
             }
             __syncthreads();
-            // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - k2 (u2 - v2 + e2)^2]
+            // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - K1(u1, v1)],
+            // four adjacent v2 per thread (float4 rows of T, b, log2 nu_J)
+            for (int q = tid; q < h * nq; q += NT) {
+                const int v1 = q / nq, g4 = q - v1 * nq;
+                const float4 ln4 = reinterpret_cast<const float4*>(S.lgnu)[v1 * bq + g4];
+                const float4 bp4 = b4[v1 * bq + g4];
+                const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
+                float m[4], sa[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    m[k] = first ? 0.f : (ln[k] > 0.5f * DD_NEG ? ln[k] - bp[k] : 0.f);
+                    sa[k] = 0.f;
+                }
+                const float* tb = S.tab1 + v1;
+                if (!first) {
+#pragma unroll
+                    for (int u1 = 0; u1 < 16; ++u1) {
+                        if (u1 >= hx) break;
+                        const float4 T4 = reinterpret_cast<const float4*>(S.T + u1 * bs)[g4];
+                        const float kk = tb[u1 * h];
+                        sa[0] += ex2f(T4.x - kk - m[0]);
+                        sa[1] += ex2f(T4.y - kk - m[1]);
+                        sa[2] += ex2f(T4.z - kk - m[2]);
+                        sa[3] += ex2f(T4.w - kk - m[3]);
+                    }
+                }
+                float out[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int v2 = 4 * g4 + k;
+                    if (v2 >= w || !(ln[k] > 0.5f * DD_NEG)) { out[k] = DD_NEG; continue; }
+                    if (first || !shift_ok(sa[k])) {
+                        float mm = DD_NEG;
+                        for (int u1 = 0; u1 < hx; ++u1) mm = fmaxf(mm, S.T[u1 * bs + v2] - tb[u1 * h]);
+                        float ss = 0.f;
+                        for (int u1 = 0; u1 < hx; ++u1) ss += ex2f(S.T[u1 * bs + v2] - tb[u1 * h] - mm);
+                        m[k] = mm;
+                        sa[k] = ss;
+                    }
+                    out[k] = ln[k] - (m[k] + lg2f(sa[k]));
+                }
+                reinterpret_cast<float4*>(S.b)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
+            }
+            __syncthreads();
+            // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over v2
             for (int q = tid; q < h * wx; q += NT) {
                 const int v1 = q / wx, u2 = q - v1 * wx;
-                const float* br = S.b + v1 * w;
-                const float* tb = S.tab2 + u2 * w;
-                S.R[q] = lse2(w, [&](int v2) { return br[v2] - tb[v2]; });
+                const float4* br = b4 + v1 * bq;
+                const float4* tr = t24 + u2 * bq;
+                float m = first ? 0.f : S.R[q];
+                float sacc = 0.f;
+                if (!first) {
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                    int g = 0;
+                    for (; g + 2 <= nq; g += 2) {
+                        const float4 bb = br[g], tt = tr[g], bc = br[g + 1], tc = tr[g + 1];
+                        s0 += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m);
+                        s1 += ex2f(bb.z - tt.z - m) + ex2f(bb.w - tt.w - m);
+                        s2 += ex2f(bc.x - tc.x - m) + ex2f(bc.y - tc.y - m);
+                        s3 += ex2f(bc.z - tc.z - m) + ex2f(bc.w - tc.w - m);
+                    }
+                    if (g < nq) {
+                        const float4 bb = br[g], tt = tr[g];
+                        s0 += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m);
+                        s1 += ex2f(bb.z - tt.z - m) + ex2f(bb.w - tt.w - m);
+                    }
+                    sacc = (s0 + s1) + (s2 + s3);
+                }
+                if (first || !shift_ok(sacc)) {
+                    m = DD_NEG;
+                    for (int g = 0; g < nq; ++g) {
+                        const float4 bb = br[g], tt = tr[g];
+                        m = fmaxf(fmaxf(fmaxf(m, bb.x - tt.x), fmaxf(bb.y - tt.y, bb.z - tt.z)), bb.w - tt.w);
+                    }
+                    sacc = 0.f;
+                    for (int g = 0; g < nq; ++g) {
+                        const float4 bb = br[g], tt = tr[g];
+                        sacc += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m) + ex2f(bb.z - tt.z - m) +
+                                ex2f(bb.w - tt.w - m);
+                    }
+                }
+                S.R[q] = m + lg2f(sacc);
             }
             __syncthreads();
-            // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - k2 (u1 - v1 + e1)^2]
+            // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - K1(u1, v1)],
+            // P2 adjacent lanes per line, combined by warp shuffles; L1 X error
             double e_loc = 0.0;
-            for (int u = tid; u < nx; u += NT) {
-                const int u1 = u / wx, u2 = u - u1 * wx;
-                const float lg = S.lgm[u];
-                float an = DD_NEG;
-                if (lg > 0.5f * DD_NEG) {
-                    const float* tb = S.tab1 + u1 * h;
-                    const float* Rc = S.R + u2;
-                    an = lg - lse2(h, [&](int v1) { return Rc[v1 * wx] - tb[v1]; });
-                    e_loc += S.mux[u] * (double)fabsf(expm1f((S.a[u] - an) * kLn2));
+            for (int base = 0; base < nx * P2; base += NT) {
+                const int q = base + tid;
+                const bool act = q < nx * P2;
+                const int line = act ? q / P2 : 0, part = q - (q / P2) * P2;
+                const int u1 = line / wx, u2 = line - u1 * wx;
+                const float lg = act ? S.lgm[line] : DD_NEG;
+                const bool live = lg > 0.5f * DD_NEG;
+                const float* Rc = S.R + u2;
+                const float* tb = S.tab1 + u1 * h;
+                float m = (first || !live) ? 0.f : lg - aC[line];
+                float sacc = 0.f;
+                if (live && !first) {
+                    float s0 = 0.f, s1 = 0.f;
+                    int v1 = part;
+                    for (; v1 + P2 < h; v1 += 2 * P2) {
+                        s0 += ex2f(Rc[v1 * wx] - tb[v1] - m);
+                        s1 += ex2f(Rc[(v1 + P2) * wx] - tb[v1 + P2] - m);
+                    }
+                    if (v1 < h) s0 += ex2f(Rc[v1 * wx] - tb[v1] - m);
+                    sacc = s0 + s1;
                 }
-                S.an[u] = an;
+                for (int o = 1; o < P2; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                const bool bad = live && (first || !shift_ok(sacc));
+                if (__any_sync(0xffffffffu, bad)) {
+                    float mm = DD_NEG;
+                    if (live)
+                        for (int v1 = part; v1 < h; v1 += P2) mm = fmaxf(mm, Rc[v1 * wx] - tb[v1]);
+                    for (int o = 1; o < P2; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+                    float ss = 0.f;
+                    if (live)
+                        for (int v1 = part; v1 < h; v1 += P2) ss += ex2f(Rc[v1 * wx] - tb[v1] - mm);
+                    for (int o = 1; o < P2; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    if (bad) { m = mm; sacc = ss; }
+                }
+                if (act && part == 0) {
+                    const float an = live ? lg - (m + lg2f(sacc)) : DD_NEG;
+                    aN[line] = (live && om != 1.f) ? aC[line] + om * (an - aC[line]) : an;
+                    if (live) e_loc += S.mux[line] * (double)fabsf(expm1f((aC[line] - an) * kLn2));
+                }
             }
-            double ev[1] = {e_loc};
-            block_sum_d<1>(ev, S.red);
-            err = ev[0];
+            for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
+            if (lane == 0) S.red[wid] = e_loc;
+            __syncthreads();
+            err = 0.0;
+            for (int k = 0; k < (NT >> 5); ++k) err += S.red[k];
+            first = false;
             // stall: no 1% improvement for 64 iterations while already within
             // 50 tol (the FP32 rounding floor of this cell has been reached)
             if (err < 0.99 * best) { best = err; since = 0; } else ++since;
             stalled = A.fixed_iters <= 0 && since >= 64 && err <= 50.0 * tolm;
+            if (A.omega < 0.f) {
+                if (om > 1.f && err > 1.5 * err_prev) {  // diverging: back to plain steps
+                    om = 1.f;
+                    om_start = it + 5;
+                } else if (it == om_start) {
+                    err_mark = err;
+                } else if (it == om_start + 5 && err_mark > 0.0) {
+                    const double r = fmin(pow(err / err_mark, 0.2), 0.999);
+                    om = (float)fmin(1.85, fmax(1.0, 2.0 / (1.0 + sqrt(1.0 - r))));
+                }
+            }
+            err_prev = err;
             const bool done = (A.fixed_iters > 0) ? (it >= A.fixed_iters)
                                                   : (err <= tolm || it >= A.max_iter || stalled);
             if (done) break;
-            for (int u = tid; u < nx; u += NT) S.a[u] = S.an[u];
-            __syncthreads();
+            float* tmp = aC;
+            aC = aN;
+            aN = tmp;
         }
+        __syncthreads();  // every thread has read the error partials in S.red
         if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[stalled ? 3 : 0], 1);
 
         // ---- outputs of the solve: duals, objective --------------------------
@@ -456,13 +638,13 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         const double dx2 = (double)(c0 - o2) + (double)uc2 - (double)vc2;
         const double hd = 0.5 * A.k2d * (dx1 * dx1 + dx2 * dx2);
         for (int u = tid; u < nx; u += NT) {
-            apo[u] = S.a[u];
+            apo[u] = aC[u];
             const float lg = S.lgm[u];
             if (lg > 0.5f * DD_NEG) {
                 const int u1 = u / wx, u2 = u - u1 * wx;
-                const double r = S.mux[u] * exp2((double)(S.a[u] - S.an[u]));
+                const double r = S.mux[u] * exp2((double)(aC[u] - aN[u]));
                 const double ub1 = u1 - (double)uc1, ub2 = u2 - (double)uc2;
-                const double al = kLn2d * ((double)S.a[u] - A.k2d * ((l1 - 1.0) * ub1 * ub1 + (l2 - 1.0) * ub2 * ub2)
+                const double al = kLn2d * ((double)aC[u] - A.k2d * ((l1 - 1.0) * ub1 * ub1 + (l2 - 1.0) * ub2 * ub2)
                                            + 2.0 * A.k2d * (dx1 * ub1 + dx2 * ub2) + hd)
                                   - log(S.mux[u]);
                 eloc[0] += al * r;
@@ -470,11 +652,11 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         }
         for (int v = tid; v < nA; v += NT) {
             const int v1 = v / w, v2 = v - v1 * w;
-            A.comp_b[comp + (long long)v1 * stride + v2] = S.b[v];
-            if (S.lgnu[v] > 0.5f * DD_NEG) {
+            A.comp_b[comp + (long long)v1 * stride + v2] = S.b[v1 * bs + v2];
+            if (S.lgnu[v1 * bs + v2] > 0.5f * DD_NEG) {
                 const double nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
                 const double vb1 = v1 - (double)vc1, vb2 = v2 - (double)vc2;
-                const double be = kLn2d * ((double)S.b[v] + S.B1[v1] + S.B2[v2]
+                const double be = kLn2d * ((double)S.b[v1 * bs + v2] + S.B1[v1] + S.B2[v2]
                                            - A.k2d * ((1.0 / l1 - 1.0) * vb1 * vb1 + (1.0 / l2 - 1.0) * vb2 * vb2)
                                            - 2.0 * A.k2d * (dx1 * vb1 + dx2 * vb2) + hd)
                                   - log(A.nu[(o1 + v1) * A.N2 + (o2 + v2)]);
@@ -496,17 +678,17 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         //     M2 = mean of (x2 - y2)^2 under that partial distribution.
         const int ncg = wx / s, nrg = hx / s;
         float* T2 = S.T;
-        float* M2 = S.T + 2 * (2 * s) * A.smaxW;
+        float* M2 = S.T + 2 * (2 * s) * padw(A.smaxW);
         for (int q = tid; q < ncg * hx * w; q += NT) {
             const int cg = q / (hx * w), rem = q - cg * hx * w;
             const int u1 = rem / w, v2 = rem - u1 * w;
-            const float* ar = S.a + u1 * wx + cg * s;
-            const float* tb = S.tab2 + (cg * s) * w + v2;
-            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k * w]; });
+            const float* ar = aC + u1 * wx + cg * s;
+            const float* tb = S.tab2 + (cg * s) * bs + v2;
+            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k * bs]; });
             float mom = 0.f;
             for (int k = 0; k < s; ++k) {
                 const float dd = (float)(c0 + cg * s + k - o2 - v2);
-                mom += ex2f(ar[k] - tb[k * w] - lse) * dd * dd;
+                mom += ex2f(ar[k] - tb[k * bs] - lse) * dd * dd;
             }
             T2[q] = lse;
             M2[q] = mom;
@@ -714,10 +896,9 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
 }  // namespace
 
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
-    const int s2 = 2 * c->s;
-    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + (size_t)maxw);
-    size_t fl = 2 * (size_t)maxarea + 4 * (size_t)s2 * maxw + (size_t)maxh * s2 + (size_t)maxh * s2 + (size_t)maxw * s2 +
-                3 * (size_t)c->amax + 16 + 32;
+    const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
+    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS) + 16;
+    size_t fl = 2 * (size_t)maxarea + 4 * s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 3 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
 }
 
@@ -741,7 +922,7 @@ int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
     }
     HalfArgs A;
     A.N1 = c->N1; A.N2 = c->N2; A.s = c->s; A.ncell = P.ncell; A.amax = c->amax;
-    A.k2 = c->k2; A.k2d = c->k2; A.eps = c->eps; A.h2 = c->h * c->h;
+    A.k2 = c->k2; A.k2d = c->k2d; A.eps = c->eps; A.h2 = c->h * c->h;
     A.members = P.members; A.xblk = P.xblk; A.mJ = P.mJ; A.order = P.order;
     A.bhdr_in = c->bhdr[c->cur]; A.pool_in = c->pool[c->cur];
     A.bhdr_out = c->bhdr[1 - c->cur]; A.pool_out = c->pool[1 - c->cur];
@@ -750,6 +931,7 @@ int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
     A.warm = (c->opt.warm == DD_WARM_PREV && P.warm_valid) ? 1 : 0;
     A.lgmu = c->d_lgmu; A.mu = c->d_mu; A.nu = c->d_nu; A.m = c->d_m;
     A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
+    A.omega = (float)c->opt.omega;
     A.trunc = (float)c->opt.trunc;
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
     A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;

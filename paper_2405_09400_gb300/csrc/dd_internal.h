@@ -53,7 +53,8 @@ struct DevPart {
 struct dd_ctx {
     int N1 = 0, N2 = 0, s = 0, n1 = 0, n2 = 0, nb = 0, amax = 0;
     double h = 0, eps = 0;
-    float k2 = 0;  // h^2 / eps * log2(e): cost exponent per squared pixel, base 2
+    float k2 = 0;    // h^2 / eps * log2(e): cost exponent per squared pixel, base 2 (FP32 copy)
+    double k2d = 0;  // the same in FP64 (kernel tables, gauge conversions)
     dd_options opt{};
     cudaStream_t stream = nullptr;
     int dev = 0, nsm = 0;

@@ -15,8 +15,10 @@
 //    cell grid; it is strongly feasible, and the leaving arc is chosen by
 //    Cunningham's rule (last blocking arc from the apex), which rules out cycling;
 //  * entering arcs by block search over the reduced costs;
-//  * the tree is kept as parent pointers with doubly linked child lists; after a
-//    pivot the cut subtree is re-rooted and its depths / potentials updated.
+//  * the tree is kept as parent pointers with doubly linked child lists; the
+//    apex of a pivot cycle is found by marking the two upward walks; after a
+//    pivot the cut subtree is re-rooted, and the potentials of the smaller of
+//    the cut subtree and the rest are shifted (only differences matter).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -26,15 +28,23 @@
 
 namespace {
 
+int mcf_block = 0;  // entering-arc block size; 0 = sqrt(#arcs)
+
 struct NetworkSimplex {
     int nn = 0;  // nodes: sources 0..n-1, sinks n..2n-1
     int na = 0;  // arcs
     std::vector<int> tail, head;
     std::vector<int64_t> cost, flow;
-    std::vector<int> parent, parc, depth, first_child, next_sib, prev_sib;
+    std::vector<int> parent, parc, first_child, next_sib, prev_sib;
     std::vector<int64_t> pot;
+    std::vector<int64_t> stamp;  // last pivot that visited the node (apex search)
+    std::vector<int> pos;        // position of the node in its apex-search path
     std::vector<char> in_tree;
+    std::vector<int> pu, pv, path, arcs, s1, s2, l1, l2;
     int64_t pivots = 0;
+#ifdef MCF_STATS
+    int64_t st_refresh = 0, st_path = 0, st_scan = 0, st_degenerate = 0;
+#endif
 
     void add_child(int p, int c) {
         prev_sib[c] = -1;
@@ -52,31 +62,46 @@ struct NetworkSimplex {
     }
     int64_t rc(int a) const { return cost[a] + pot[tail[a]] - pot[head[a]]; }
 
-    // re-derive depth and potential of the subtree below r from its parent
-    void refresh_subtree(int r, std::vector<int>& stack) {
-        stack.clear();
-        stack.push_back(r);
-        while (!stack.empty()) {
-            int x = stack.back();
-            stack.pop_back();
+    // potentials of the whole tree from the root (node 0), tree arcs priced at 0
+    void price_tree() {
+        s1.clear();
+        pot[0] = 0;
+        for (int c = first_child[0]; c >= 0; c = next_sib[c]) s1.push_back(c);
+        while (!s1.empty()) {
+            int x = s1.back();
+            s1.pop_back();
             int p = parent[x], a = parc[x];
-            depth[x] = depth[p] + 1;
             pot[x] = (tail[a] == p) ? pot[p] + cost[a] : pot[p] - cost[a];
-            for (int c = first_child[x]; c >= 0; c = next_sib[c]) stack.push_back(c);
+            for (int c = first_child[x]; c >= 0; c = next_sib[c]) s1.push_back(c);
         }
     }
 
-    bool pivot(int a, std::vector<int>& pu, std::vector<int>& pv, std::vector<int>& stack) {
-        int u = tail[a], v = head[a];
-        // apex by depth
+    bool pivot(int a) {
+        const int u = tail[a], v = head[a];
+        const int64_t tag = pivots + 1;
+        // apex: walk up from u and v alternately, marking the nodes of each walk;
+        // the first node reached that the other walk already marked is the apex.
+        // pu / pv end up holding the nodes strictly below the apex on each side.
         pu.clear();
         pv.clear();
-        int x = u, y = v;
-        while (depth[x] > depth[y]) { pu.push_back(x); x = parent[x]; }
-        while (depth[y] > depth[x]) { pv.push_back(y); y = parent[y]; }
-        while (x != y) {
-            pu.push_back(x); x = parent[x];
-            pv.push_back(y); y = parent[y];
+        stamp[u] = tag; pos[u] = 0; pu.push_back(u);
+        stamp[v] = -tag; pos[v] = 0; pv.push_back(v);
+        int x = u, y = v, apex = -1;
+        while (apex < 0) {
+            bool moved = false;
+            if (parent[x] >= 0) {
+                moved = true;
+                x = parent[x];
+                if (stamp[x] == -tag) { apex = x; pv.resize(pos[x]); break; }
+                stamp[x] = tag; pos[x] = (int)pu.size(); pu.push_back(x);
+            }
+            if (parent[y] >= 0) {
+                moved = true;
+                y = parent[y];
+                if (stamp[y] == tag) { apex = y; pu.resize(pos[y]); break; }
+                stamp[y] = -tag; pos[y] = (int)pv.size(); pv.push_back(y);
+            }
+            if (!moved) return false;  // not a tree (cannot happen)
         }
         // backward arcs: on the u path (traversed apex -> u, downwards) arcs
         // pointing up; on the v path (traversed v -> apex, upwards) arcs pointing down.
@@ -90,6 +115,10 @@ struct NetworkSimplex {
             if (head[e] == z) theta = std::min(theta, flow[e]);
         }
         if (theta == INT64_MAX) return false;  // unbounded (cannot happen here)
+#ifdef MCF_STATS
+        st_path += pu.size() + pv.size();
+        if (theta == 0) ++st_degenerate;
+#endif
         // leaving arc: last blocking arc in the order apex->u, a, v->apex
         int leave_node = -1;
         bool on_v = false;
@@ -103,7 +132,6 @@ struct NetworkSimplex {
                 if (tail[e] == z && flow[e] == theta) { leave_node = z; break; }
             }
         }
-        // flow update
         if (theta > 0) {
             for (int z : pu) {
                 int e = parc[z];
@@ -115,20 +143,49 @@ struct NetworkSimplex {
             }
             flow[a] += theta;
         }
-        // tree update: cut subtree below leave_node, re-hang at the endpoint of a inside it
-        int q = leave_node;
-        int r = on_v ? v : u;
-        int o = on_v ? u : v;
+        // the subtree T_q below the leaving arc re-hangs at the endpoint r of a
+        // inside it; its potentials shift by delta relative to the rest. Only
+        // differences matter, so the smaller of T_q and the rest is shifted:
+        // the two are enumerated in lockstep until one is exhausted.
+        const int q = leave_node;
+        const int r = on_v ? v : u;
+        const int o = on_v ? u : v;
+        const int64_t delta = on_v ? rc(a) : -rc(a);
         in_tree[parc[q]] = 0;
         in_tree[a] = 1;
         remove_child(parent[q], q);
+        {
+            s1.clear(); s2.clear(); l1.clear(); l2.clear();
+            s1.push_back(q);
+            s2.push_back(0);
+            int done = 0;
+            while (!done) {
+                if (!s1.empty()) {
+                    int z = s1.back(); s1.pop_back(); l1.push_back(z);
+                    for (int c = first_child[z]; c >= 0; c = next_sib[c]) s1.push_back(c);
+                } else done = 1;
+                if (!done) {
+                    if (!s2.empty()) {
+                        int z = s2.back(); s2.pop_back(); l2.push_back(z);
+                        for (int c = first_child[z]; c >= 0; c = next_sib[c]) s2.push_back(c);
+                    } else done = 2;
+                }
+            }
+            if (done == 1) {
+                for (int z : l1) pot[z] += delta;
+            } else {
+                for (int z : l2) pot[z] -= delta;
+            }
+#ifdef MCF_STATS
+            st_refresh += l1.size() + l2.size();
+#endif
+        }
         // path r -> q, reversed
-        std::vector<int>& path = stack;
         path.clear();
         for (int z = r; z != q; z = parent[z]) path.push_back(z);
         path.push_back(q);
         for (size_t t = 0; t + 1 < path.size(); ++t) remove_child(path[t + 1], path[t]);
-        std::vector<int> arcs(path.size());
+        arcs.resize(path.size());
         for (size_t t = 0; t + 1 < path.size(); ++t) arcs[t] = parc[path[t]];
         for (size_t t = 0; t + 1 < path.size(); ++t) {
             int z0 = path[t], z1 = path[t + 1];
@@ -139,15 +196,12 @@ struct NetworkSimplex {
         parent[r] = o;
         parc[r] = a;
         add_child(o, r);
-        std::vector<int> st2;
-        refresh_subtree(r, st2);
         ++pivots;
         return true;
     }
 
     bool run() {
-        std::vector<int> pu, pv, stack;
-        const int block = std::max(16, (int)std::sqrt((double)na));
+        const int block = mcf_block > 0 ? mcf_block : std::max(16, (int)std::sqrt((double)na));
         int next = 0;
         while (true) {
             int best = -1;
@@ -159,6 +213,9 @@ struct NetworkSimplex {
                     int e = next;
                     next = (next + 1 == na) ? 0 : next + 1;
                     if (in_tree[e]) continue;
+#ifdef MCF_STATS
+                    ++st_scan;
+#endif
                     int64_t r = rc(e);
                     if (r < best_rc) { best_rc = r; best = e; }
                 }
@@ -166,7 +223,7 @@ struct NetworkSimplex {
                 if (best >= 0) break;
             }
             if (best < 0) return true;
-            if (!pivot(best, pu, pv, stack)) return false;
+            if (!pivot(best)) return false;
         }
     }
 };
@@ -226,7 +283,8 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
     const int nn = ns.nn;
     ns.parent.assign(nn, -1);
     ns.parc.assign(nn, -1);
-    ns.depth.assign(nn, 0);
+    ns.stamp.assign(nn, 0);
+    ns.pos.assign(nn, 0);
     ns.first_child.assign(nn, -1);
     ns.next_sib.assign(nn, -1);
     ns.prev_sib.assign(nn, -1);
@@ -299,12 +357,7 @@ int mcf_solve(McfSolver* S, const double* cbar, double* w, double* value, int32_
             if (a >= 0) ns.cost[a] = (int64_t)std::llround(cbar[5 * i + k] * cscale);
         }
     // re-price the current tree from its root (node 0 = s_0 never has a parent)
-    {
-        std::vector<int> st;
-        ns.pot[0] = 0;
-        ns.depth[0] = 0;
-        for (int c = ns.first_child[0]; c >= 0; c = ns.next_sib[c]) ns.refresh_subtree(c, st);
-    }
+    ns.price_tree();
     const int64_t piv0 = ns.pivots;
     if (!ns.run()) return DD_ERR_FLOW;
     double val = 0.0;

@@ -13,9 +13,10 @@ Tolerances (derived from the arithmetic; see the design notes):
   round at ~1.2e-5, and a pair of them enters each exponent. The library's own
   state is Y-exact up to FP32 storage (L1 Y error <= 1e-6) and X-exact per basic
   cell (rescaled to m_i);
-* flow update: edge costs computed from the same state agree to 1e-7 of the
-  largest |c_bar| (the GPU's moments are taken on the values before their final
-  FP32 rounding, relative 6e-8); the optimal
+* flow update: edge costs computed from the same state agree to 5e-7 of the
+  largest |c_bar|: both terms of c_bar (candidate cost and D_i / m_i, each up to
+  max|c_bar|) come from FP32-stored marginals summed in FP64 (relative ~2e-7,
+  and the GPU takes its moments before the final FP32 rounding); the optimal
   values of the library's network simplex and the oracle's LP to 1e-9 relative.
 """
 
@@ -192,7 +193,7 @@ def test_flow_update_matches_oracle_on_gpu_state(dd):
     ref = edge_costs(geom, mu, state, D, 1.0 / N)
     ok = ~np.isnan(ref)
     scale = np.abs(ref[ok]).max()
-    assert np.abs(cbar[ok] - ref[ok]).max() <= 1e-7 * scale
+    assert np.abs(cbar[ok] - ref[ok]).max() <= 5e-7 * scale
     _, val_ref, _ = min_cost_flow(nbr, cbar, m)
     assert f["value"] == pytest.approx(val_ref, rel=1e-9, abs=1e-18)
     assert f["value"] < 0
