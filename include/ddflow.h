@@ -226,6 +226,36 @@ int dd_debug_cell(dd_ctx* ctx, int part, int J, float* a, float* b, float* gauge
  * device and device to host. Any pointer may be NULL. */
 int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
 
+/*
+ * Allocation-free variant of the L1 Y-marginal error of dd_get_objective (the
+ * paper has no counterpart; this is a library facility). For callers that
+ * cannot allocate device memory: code running inside CUDA stream capture
+ * (cudaMalloc cannot be captured), real-time pipelines that reserve all device
+ * memory up front, hosts whose own allocator owns the GPU. It computes
+ *     *l1_out = sum_y | sum_i nu_i(y) - nu(y) |
+ * with scratch memory taken from a fixed __device__ array inside the library,
+ * never from cudaMalloc.
+ *  - All pointers are DEVICE pointers on the current device: hdr (nbasic x 4
+ *    int32 box headers o1, o2, h, w), data (float32 box contents packed in cell
+ *    order, each h x w row-major, no padding), nu (N1 * N2 float64), l1_out (one
+ *    float64, overwritten). Entries of a box outside the grid are ignored.
+ *  - Limits: N1 * N2 <= DD_STATIC_MAX_PIXELS and nbasic <= DD_STATIC_MAX_CELLS;
+ *    larger problems return DD_ERR_ARG without touching the GPU. The array
+ *    (about 8.5 MB) is held by every GPU that loads the library until exit.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other streams,
+ *    other host threads on the same device) race. Calls ordered on one stream are
+ *    safe; each call clears the accumulator it uses.
+ *  - Work is enqueued on `stream` (cudaStream_t as void*); the call returns
+ *    before it completes.
+ */
+#define DD_STATIC_MAX_PIXELS (1024 * 1024)
+#define DD_STATIC_MAX_CELLS 65536
+int dd_l1_y_error_static(int32_t N1, int32_t N2, int32_t nbasic, const int32_t* hdr, const float* data,
+                         const double* nu, double* l1_out, void* stream);
+
 /* Release every resource of the context (NULL is ignored). */
 void dd_destroy(dd_ctx* ctx);
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
-    "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_destroy",
+    "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
 ]
 
 
@@ -104,6 +104,7 @@ def load():
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
         "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
+        "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -299,6 +300,13 @@ def dd_debug_cell(ctx, part, J, amax):
                                 _ptr(geom, _i32p)), "dd_debug_cell")
     hx, wx = int(geom[2]), int(geom[3])
     return dict(a=a[:hx * wx].reshape(hx, wx), b=b.reshape(int(geom[6]), int(geom[7])), gauge=g, geom=geom)
+
+
+def dd_l1_y_error_static(N1, N2, nbasic, hdr_ptr, data_ptr, nu_ptr, out_ptr, stream=None):
+    """Allocation-free L1 Y error; all pointers are device addresses (ints)."""
+    return load().dd_l1_y_error_static(int(N1), int(N2), int(nbasic), C.c_void_p(hdr_ptr), C.c_void_p(data_ptr),
+                                       C.c_void_p(nu_ptr), C.c_void_p(out_ptr),
+                                       stream if stream is not None else current_stream())
 
 
 def dd_destroy(ctx):
