@@ -196,6 +196,7 @@ void dd_destroy(dd_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->mcf) mcf_destroy(c->mcf);
     dfree(c->d_mu); dfree(c->d_nu); dfree(c->d_lgmu); dfree(c->d_m); dfree(c->d_xmom);
+    dfree(c->d_lnmu); dfree(c->d_lnnu); dfree(c->d_lnnuf);
     dfree(c->d_nbr); dfree(c->d_rev);
     for (int p = 0; p < 2; ++p) {
         DevPart& P = c->part[p];
@@ -210,6 +211,9 @@ void dd_destroy(dd_ctx* c) {
     if (c->h_w) cudaFreeHost(c->h_w);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
 }
 
@@ -302,6 +306,19 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_mu, np)); TRY(h2d(c->d_mu, mu, np, c->stream));
         TRY(dmalloc(&c->d_nu, np)); TRY(h2d(c->d_nu, nu, np, c->stream));
         TRY(dmalloc(&c->d_lgmu, np)); TRY(h2d(c->d_lgmu, lgmu.data(), np, c->stream));
+        {
+            std::vector<double> lnm(np), lnn(np);
+            for (size_t k = 0; k < np; ++k) {
+                lnm[k] = mu[k] > 0 ? std::log(mu[k]) : -INFINITY;
+                lnn[k] = nu[k] > 0 ? std::log(nu[k]) : -INFINITY;
+            }
+            TRY(dmalloc(&c->d_lnmu, np)); TRY(h2d(c->d_lnmu, lnm.data(), np, c->stream));
+            TRY(dmalloc(&c->d_lnnu, np)); TRY(h2d(c->d_lnnu, lnn.data(), np, c->stream));
+            std::vector<float> lnnf(np);
+            for (size_t k = 0; k < np; ++k) lnnf[k] = nu[k] > 0 ? (float)lnn[k] : DD_NEG;
+            TRY(dmalloc(&c->d_lnnuf, np)); TRY(h2d(c->d_lnnuf, lnnf.data(), np, c->stream));
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        }
         TRY(dmalloc(&c->d_m, c->nb)); TRY(h2d(c->d_m, c->h_m.data(), c->nb, c->stream));
         TRY(dmalloc(&c->d_xmom, 3 * (size_t)c->nb)); TRY(h2d(c->d_xmom, xmom.data(), xmom.size(), c->stream));
         TRY(dmalloc(&c->d_nbr, 5 * (size_t)c->nb)); TRY(h2d(c->d_nbr, c->h_nbr.data(), c->h_nbr.size(), c->stream));
@@ -342,6 +359,12 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_red, 8));
         for (auto& e : c->ev)
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            rc = DD_ERR_CUDA;
+            goto fail;
+        }
         if (c->opt.init_kind == DD_INIT_PRODUCT) {
             // nu_i = m_i nu on the whole grid, truncated like every other state
             std::vector<int32_t> hdr(4 * (size_t)c->nb);
@@ -455,32 +478,75 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     }
     RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)outn));
     if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(&c->d_pre, &c->pre_cap, (size_t)outn));
-    {
-        // work queue order: longest expected solve first (box area x the cell's
-        // previous Sinkhorn iteration count), so that the slowest cells start at once
-        std::vector<int32_t> ch((size_t)CH_N * P.ncell), itp(P.ncell, 1);
-        RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
-        if (P.warm_valid) RET(d2h(itp.data(), P.iters, P.ncell, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        std::vector<double> key(P.ncell);
-        for (int J = 0; J < P.ncell; ++J)
-            key[J] = (double)ch[CH_N * J + CH_H] * ch[CH_N * J + CH_W] * std::max(1, itp[J]);
-        std::vector<int32_t> order(P.ncell);
-        for (int J = 0; J < P.ncell; ++J) order[J] = J;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return key[x] > key[y]; });
-        RET(h2d(P.order, order.data(), order.size(), c->stream));
+    // Work queue order: longest expected solve first (box area x the cell's
+    // previous Sinkhorn iteration count). Cells are split in two size classes,
+    // each launched with shared memory sized for its own largest box: the small
+    // class (most cells) fits many CTAs per SM, the large class runs concurrently
+    // on a second stream.
+    std::vector<int32_t> ch((size_t)CH_N * P.ncell), itp(P.ncell, 1);
+    RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
+    if (P.warm_valid) RET(d2h(itp.data(), P.iters, P.ncell, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> key(P.ncell);
+    std::vector<int32_t> big, small;
+    long long dims[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [class][area, h, w]
+    for (int J = 0; J < P.ncell; ++J) {
+        const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
+        const long long a = (long long)h * half_padw(w);
+        key[J] = (double)h * w * std::max(1, itp[J]);
+        const int cls = a <= kSmallArea && w <= kSmallW ? 1 : 0;
+        (cls ? small : big).push_back(J);
+        dims[cls][0] = std::max(dims[cls][0], a);
+        dims[cls][1] = std::max(dims[cls][1], (long long)h);
+        dims[cls][2] = std::max(dims[cls][2], (long long)w);
     }
-    const size_t smem = half_smem_bytes(c, c->h_tot[PT_MAXAREA], c->h_tot[PT_MAXH], c->h_tot[PT_MAXW]);
-    if (smem > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
-    const int threads = choose_threads(c, c->h_tot[PT_MAXAREA]);
-    int occ = half_occupancy(threads, smem);
-    if (occ < 1) occ = 1;
-    const int grid = std::max(1, std::min(P.ncell, c->nsm * occ));
+    auto by_key = [&](int32_t x, int32_t y) { return key[x] > key[y]; };
+    std::stable_sort(big.begin(), big.end(), by_key);
+    std::stable_sort(small.begin(), small.end(), by_key);
+    std::vector<int32_t> order(big);
+    order.insert(order.end(), small.begin(), small.end());
+    RET(h2d(P.order, order.data(), order.size(), c->stream));
+    size_t smem_c[2] = {0, 0};
+    for (int cls = 0; cls < 2; ++cls) {
+        smem_c[cls] = half_smem_bytes(c, dims[cls][0], dims[cls][1], dims[cls][2]);
+        if (smem_c[cls] > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+    }
+    const int thr_c[2] = {c->opt.threads > 0 ? choose_threads(c, 0) : 256,
+                          c->opt.threads > 0 ? choose_threads(c, 0) : 128};
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
-    RET(launch_half(c, part, threads, smem, grid));
-    c->n_launch += 1;
+    const bool has_big = !big.empty(), has_small = !small.empty();
+    if (has_big && has_small) {
+        CK(cudaEventRecord(c->ev_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    if (has_big) {
+        int occ = std::max(1, half_occupancy(thr_c[0], smem_c[0]));
+        int grid = std::max(1, std::min((int)big.size(), c->nsm * occ));
+        RET(launch_half(c, part, P.order, (int)big.size(), c->d_queue, dims[0], thr_c[0], smem_c[0], grid,
+                        has_small ? c->side : c->stream));
+        c->n_launch += 1;
+    }
+    if (has_small) {
+        int occ = std::max(1, half_occupancy(thr_c[1], smem_c[1]));
+        int grid = std::max(1, std::min((int)small.size(), c->nsm * occ));
+        RET(launch_half(c, part, P.order + big.size(), (int)small.size(), c->d_queue + 1, dims[1], thr_c[1],
+                        smem_c[1], grid, c->stream));
+        c->n_launch += 1;
+    }
+    if (has_big && has_small) {
+        CK(cudaEventRecord(c->ev_join, c->side));
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    }
+    {
+        const long long dall[3] = {std::max(dims[0][0], dims[1][0]), std::max(dims[0][1], dims[1][1]),
+                                   std::max(dims[0][2], dims[1][2])};
+        const size_t sm = c2b_smem_bytes(c, dall[1], dall[2]);
+        if (sm > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+        RET(launch_c2b(c, part, dall, sm));
+        c->n_launch += 1;
+    }
     CK(cudaEventRecord(c->ev[2], c->stream));
     c->cur = 1 - c->cur;
     P.warm_valid = true;
@@ -669,23 +735,20 @@ int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta,
         const double uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
         const double d1 = (double)(X[XB_R0] - x[CH_O1]) + uc1 - vc1, d2 = (double)(X[XB_C0] - x[CH_O2]) + uc2 - vc2;
         const double hd = 0.5 * k2 * (d1 * d1 + d2 * d2);
-        // per-row / per-column kernel minima the kernel subtracted from b
+        // per-row / per-column kernel minima the kernel subtracted from b:
+        // B(v) = k2 l (ubar* - t)^2 at the grid point nearest to t = vbar / l
         std::vector<double> B1(h), B2(w);
         for (int r = 0; r < h; ++r) {
-            double vb = r - vc1, mn = 1e300;
-            for (int u1 = 0; u1 < hx; ++u1) {
-                double ub = u1 - uc1;
-                mn = std::min(mn, k2 * (l1 * ub * ub - 2 * ub * vb + vb * vb / l1));
-            }
-            B1[r] = mn;
+            const double tt = (r - vc1) / l1;
+            const int us = std::min(hx - 1, std::max(0, (int)std::nearbyint(tt + uc1)));
+            const double w0 = 2.0 * ((us - uc1) - tt);
+            B1[r] = 0.25 * k2 * l1 * w0 * w0;
         }
         for (int q = 0; q < w; ++q) {
-            double vb = q - vc2, mn = 1e300;
-            for (int u2 = 0; u2 < wx; ++u2) {
-                double ub = u2 - uc2;
-                mn = std::min(mn, k2 * (l2 * ub * ub - 2 * ub * vb + vb * vb / l2));
-            }
-            B2[q] = mn;
+            const double tt = (q - vc2) / l2;
+            const int us = std::min(wx - 1, std::max(0, (int)std::nearbyint(tt + uc2)));
+            const double w0 = 2.0 * ((us - uc2) - tt);
+            B2[q] = 0.25 * k2 * l2 * w0 * w0;
         }
         if (alpha)
             for (int u1 = 0; u1 < hx; ++u1)

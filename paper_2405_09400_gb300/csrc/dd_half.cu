@@ -5,12 +5,14 @@
 //               boxes (BasicToComposite's output box, Eq. get-composite-cell-
 //               marginal), and prefix sums that place the composite marginal and
 //               the member outputs in their pools;
-//  k_half       a persistent kernel with a work queue; one CTA solves one
+//  k_sink       a persistent kernel with a work queue; one CTA solves one
 //               composite cell at a time, entirely in shared memory:
 //                 1. gather nu_J from the member boxes (BasicToComposite),
 //                 2. log-domain Sinkhorn (Section A.1, "Custom CUDA Sinkhorn")
 //                    with the separable per-axis log-sum-exp for the squared
 //                    cost, until the L1 X error <= tol * mu(X_J),
+//               and writes the duals, the objective and the error;
+//  k_c2b        one CTA per cell, from those duals:
 //                 3. CompositeToBasic by the partial log-sum-exp over each
 //                    basic cell (Section A.1, "Online reduction"), with
 //                    D_i = <c, pi_i> from the same partial sums,
@@ -35,6 +37,12 @@
 #include <cstdio>
 
 #include "dd_internal.h"
+
+#define RET_IF(x)                   \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != DD_OK) return r_; \
+    } while (0)
 
 namespace {
 
@@ -193,6 +201,9 @@ struct HalfArgs {
     const float* lgmu;
     const double* mu;
     const double* nu;
+    const double* lnmu;  // ln mu, ln nu (FP64, for the objective)
+    const double* lnnu;
+    const float* lnnuf;  // ln nu in FP32
     const double* m;
     double tol;
     float omega;  // 1: plain Sinkhorn; (1, 2): fixed over-relaxation; < 0: adaptive
@@ -218,6 +229,7 @@ struct Smem {
     float* tab2;  // (2s) * BS: axis-2 kernel (gauge-reduced, 0 in the padding)
     float* a;     // 2 * amax: X dual, ping-pong
     float* lgm;   // amax
+    float* muxf;  // amax: mu on the block (FP32 copy)
     double* mux;  // amax
     double* red;  // 32 * 16 + 16
     double* B1;   // maxH: min over u1 of the axis-1 kernel at v1 (FP64)
@@ -248,6 +260,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.tab2 = f; f += BS * s2;
     S.a = f; f += 2 * A.amax;
     S.lgm = f; f += A.amax;
+    S.muxf = f; f += A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     return S;
@@ -267,7 +280,8 @@ __device__ __forceinline__ float lse2(int n, F term) {
 // neither over- nor underflows: then no significant term was flushed to zero
 __device__ __forceinline__ bool shift_ok(float s) { return s >= 8.67e-19f && s <= 1.15e18f; }  // 2^-60 .. 2^60
 
-__global__ void __launch_bounds__(512) k_half(HalfArgs A) {
+template <int NTB>
+__global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
     Smem S = carve(smem_raw, A);
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -309,7 +323,9 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         }
 
         // ---- 1. gather nu_J ---------------------------------------------------
-        double gm[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // per-thread partial sums in FP32 (a few entries each), block sum in FP64;
+        // they only choose the change of gauge, which is exact for any value
+        float gf[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int v = tid; v < h * bs; v += NT) {
             const int v1 = v / bs, v2 = v - v1 * bs;
             float lg = DD_NEG;
@@ -326,8 +342,8 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 }
                 A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
                 if (acc > 0.f) lg = lg2f(acc);
-                const double da = acc;
-                gm[0] += da; gm[1] += da * v1; gm[2] += da * v2; gm[3] += da * v1 * v1; gm[4] += da * v2 * v2;
+                const float f1 = (float)v1, f2 = (float)v2;
+                gf[0] += acc; gf[1] += acc * f1; gf[2] += acc * f2; gf[3] += acc * f1 * f1; gf[4] += acc * f2 * f2;
             }
             S.lgnu[v] = lg;
             S.b[v] = DD_NEG;
@@ -335,9 +351,13 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         for (int q = tid; q < hx * bs; q += NT) S.T[q] = DD_NEG;
         for (int u = tid; u < nx; u += NT) {
             const int u1 = u / wx, u2 = u - u1 * wx;
-            const double mux = A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
-            gm[5] += mux; gm[6] += mux * u1; gm[7] += mux * u2; gm[8] += mux * u1 * u1; gm[9] += mux * u2 * u2;
+            const float mux = (float)A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
+            const float f1 = (float)u1, f2 = (float)u2;
+            gf[5] += mux; gf[6] += mux * f1; gf[7] += mux * f2; gf[8] += mux * f1 * f1; gf[9] += mux * f2 * f2;
         }
+        double gm[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) gm[k] = gf[k];
         block_sum_d<10>(gm, S.red);
         // Reparametrisation (exact for any choice): origins at the barycentres of
         // mu_J and nu_J, the linear part of the cost absorbed through d, and a
@@ -351,22 +371,23 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
         const float l1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
         const float l2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
         const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
-        // Kernel tables in FP64, rounded once. With
-        //   K_k(u, v) = k2 (l_k ubar^2 - 2 ubar vbar + vbar^2 / l_k)
-        // and B_k(v) = min_u K_k(u, v), the kernel used is K_k - B_k >= 0 and the
-        // Y dual is stored as b~ = b - B_1(v1) - B_2(v2) (another exact change of
-        // gauge); it removes the distance of v from the block from every value.
+        // Kernel tables. With t = vbar / l_k, the axis kernel is
+        //   K_k(u, v) = k2 l_k (ubar - t)^2,
+        // its minimum over the block's grid points is B_k(v) = k2 l_k (ubar* - t)^2
+        // at the grid point ubar* nearest to t, and the table holds
+        //   K_k - B_k = k2 l_k D (D + w0),  D = u - u* (integer), w0 = 2 (ubar* - t),
+        // w0 taken in FP64 per v and rounded once, so that the small values that
+        // matter keep full FP32 precision. The Y dual is stored as
+        // b~ = b - B_1(v1) - B_2(v2) (an exact change of gauge).
         for (int v1 = tid; v1 < h; v1 += NT) {
-            const double vb = v1 - (double)vc1;
-            double mn = 1e300;
+            const double tt = (v1 - (double)vc1) / (double)l1;
+            const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
+            const double w0 = 2.0 * ((us - (double)uc1) - tt);
+            S.B1[v1] = 0.25 * A.k2d * l1 * w0 * w0;
+            const float w0f = (float)w0, kl = (float)(A.k2d * l1);
             for (int u1 = 0; u1 < hx; ++u1) {
-                const double ub = u1 - (double)uc1;
-                mn = fmin(mn, A.k2d * (l1 * ub * ub - 2.0 * ub * vb + vb * vb / l1));
-            }
-            S.B1[v1] = mn;
-            for (int u1 = 0; u1 < hx; ++u1) {
-                const double ub = u1 - (double)uc1;
-                S.tab1[u1 * h + v1] = (float)(A.k2d * (l1 * ub * ub - 2.0 * ub * vb + vb * vb / l1) - mn);
+                const float D = (float)(u1 - us);
+                S.tab1[u1 * h + v1] = kl * D * (D + w0f);
             }
         }
         for (int v2 = tid; v2 < bs; v2 += NT) {
@@ -374,16 +395,14 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 for (int u2 = 0; u2 < wx; ++u2) S.tab2[u2 * bs + v2] = 0.f;
                 continue;
             }
-            const double vb = v2 - (double)vc2;
-            double mn = 1e300;
+            const double tt = (v2 - (double)vc2) / (double)l2;
+            const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
+            const double w0 = 2.0 * ((us - (double)uc2) - tt);
+            S.B2[v2] = 0.25 * A.k2d * l2 * w0 * w0;
+            const float w0f = (float)w0, kl = (float)(A.k2d * l2);
             for (int u2 = 0; u2 < wx; ++u2) {
-                const double ub = u2 - (double)uc2;
-                mn = fmin(mn, A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2));
-            }
-            S.B2[v2] = mn;
-            for (int u2 = 0; u2 < wx; ++u2) {
-                const double ub = u2 - (double)uc2;
-                S.tab2[u2 * bs + v2] = (float)(A.k2d * (l2 * ub * ub - 2.0 * ub * vb + vb * vb / l2) - mn);
+                const float D = (float)(u2 - us);
+                S.tab2[u2 * bs + v2] = kl * D * (D + w0f);
             }
         }
         // X side: log2 mu and the warm start
@@ -396,6 +415,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             const int u1 = u / wx, u2 = u - u1 * wx;
             const int x = (r0 + u1) * A.N2 + (c0 + u2);
             S.mux[u] = A.mu[x];
+            S.muxf[u] = (float)A.mu[x];
             const float lg = A.lgmu[x];
             S.lgm[u] = lg;
             const float ub1 = u1 - uc1, ub2 = u2 - uc2;
@@ -557,7 +577,7 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             __syncthreads();
             // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - K1(u1, v1)],
             // P2 adjacent lanes per line, combined by warp shuffles; L1 X error
-            double e_loc = 0.0;
+            float e_loc = 0.f;
             for (int base = 0; base < nx * P2; base += NT) {
                 const int q = base + tid;
                 const bool act = q < nx * P2;
@@ -595,11 +615,11 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
                 if (act && part == 0) {
                     const float an = live ? lg - (m + lg2f(sacc)) : DD_NEG;
                     aN[line] = (live && om != 1.f) ? aC[line] + om * (an - aC[line]) : an;
-                    if (live) e_loc += S.mux[line] * (double)fabsf(expm1f((aC[line] - an) * kLn2));
+                    if (live) e_loc += S.muxf[line] * fabsf(expm1f((aC[line] - an) * kLn2));
                 }
             }
             for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
-            if (lane == 0) S.red[wid] = e_loc;
+            if (lane == 0) S.red[wid] = (double)e_loc;
             __syncthreads();
             err = 0.0;
             for (int k = 0; k < (NT >> 5); ++k) err += S.red[k];
@@ -642,26 +662,39 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             const float lg = S.lgm[u];
             if (lg > 0.5f * DD_NEG) {
                 const int u1 = u / wx, u2 = u - u1 * wx;
-                const double r = S.mux[u] * exp2((double)(aC[u] - aN[u]));
+                const double r = S.mux[u] * (double)exp2f(aC[u] - aN[u]);
                 const double ub1 = u1 - (double)uc1, ub2 = u2 - (double)uc2;
                 const double al = kLn2d * ((double)aC[u] - A.k2d * ((l1 - 1.0) * ub1 * ub1 + (l2 - 1.0) * ub2 * ub2)
                                            + 2.0 * A.k2d * (dx1 * ub1 + dx2 * ub2) + hd)
-                                  - log(S.mux[u]);
+                                  - A.lnmu[(r0 + u1) * A.N2 + (c0 + u2)];
                 eloc[0] += al * r;
             }
         }
+        // Y side of the objective: per entry ln2 b~ nu_J - ln(nu) nu_J in FP32
+        // (per-thread partials), the separable gauge terms of b through row and
+        // column sums of nu_J with FP64 weights, and the constant hd |nu_J|.
+        float ef = 0.f;
         for (int v = tid; v < nA; v += NT) {
             const int v1 = v / w, v2 = v - v1 * w;
-            A.comp_b[comp + (long long)v1 * stride + v2] = S.b[v1 * bs + v2];
+            const float bv = S.b[v1 * bs + v2];
+            A.comp_b[comp + (long long)v1 * stride + v2] = bv;
             if (S.lgnu[v1 * bs + v2] > 0.5f * DD_NEG) {
-                const double nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
-                const double vb1 = v1 - (double)vc1, vb2 = v2 - (double)vc2;
-                const double be = kLn2d * ((double)S.b[v1 * bs + v2] + S.B1[v1] + S.B2[v2]
-                                           - A.k2d * ((1.0 / l1 - 1.0) * vb1 * vb1 + (1.0 / l2 - 1.0) * vb2 * vb2)
-                                           - 2.0 * A.k2d * (dx1 * vb1 + dx2 * vb2) + hd)
-                                  - log(A.nu[(o1 + v1) * A.N2 + (o2 + v2)]);
-                eloc[0] += be * nuJ;
+                const float nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
+                ef += nuJ * (kLn2 * bv - A.lnnuf[(o1 + v1) * A.N2 + (o2 + v2)]);
             }
+        }
+        eloc[0] += (double)ef;
+        for (int v1 = tid; v1 < h; v1 += NT) {  // rows: B1 and the axis-1 gauge terms
+            float rs = 0.f;
+            for (int v2 = 0; v2 < w; ++v2) rs += A.comp_nu[comp + (long long)v1 * stride + v2];
+            const double vb1 = v1 - (double)vc1;
+            eloc[0] += kLn2d * (S.B1[v1] - A.k2d * (1.0 / l1 - 1.0) * vb1 * vb1 - 2.0 * A.k2d * dx1 * vb1 + hd) * rs;
+        }
+        for (int v2 = tid; v2 < w; v2 += NT) {  // columns: B2 and the axis-2 gauge terms
+            float cs = 0.f;
+            for (int v1 = 0; v1 < h; ++v1) cs += A.comp_nu[comp + (long long)v1 * stride + v2];
+            const double vb2 = v2 - (double)vc2;
+            eloc[0] += kLn2d * (S.B2[v2] - A.k2d * (1.0 / l2 - 1.0) * vb2 * vb2 - 2.0 * A.k2d * dx2 * vb2) * cs;
         }
         block_sum_d<1>(eloc, S.red);
         if (tid == 0) {
@@ -673,224 +706,297 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
             A.Ecell[J] = A.eps * eloc[0];
         }
 
-        // ---- 3. CompositeToBasic with D_i -----------------------------------
-        // C1: per column group cg, T2(cg, u1, v2) = LSE over u2 in the group, and
-        //     M2 = mean of (x2 - y2)^2 under that partial distribution.
-        const int ncg = wx / s, nrg = hx / s;
-        float* T2 = S.T;
-        float* M2 = S.T + 2 * (2 * s) * padw(A.smaxW);
-        for (int q = tid; q < ncg * hx * w; q += NT) {
-            const int cg = q / (hx * w), rem = q - cg * hx * w;
-            const int u1 = rem / w, v2 = rem - u1 * w;
-            const float* ar = aC + u1 * wx + cg * s;
-            const float* tb = S.tab2 + (cg * s) * bs + v2;
-            const float lse = lse2(s, [&](int k) { return ar[k] - tb[k * bs]; });
-            float mom = 0.f;
-            for (int k = 0; k < s; ++k) {
-                const float dd = (float)(c0 + cg * s + k - o2 - v2);
-                mom += ex2f(ar[k] - tb[k * bs] - lse) * dd * dd;
-            }
-            T2[q] = lse;
-            M2[q] = mom;
+    }
+}
+
+// CompositeToBasic, D_i, balancing, truncation and compaction of one composite
+// cell per CTA, from the duals k_sink left in global memory (alpha, b~ not
+// needed: the member shares are ratios of partial sums over X).
+__global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int s = A.s;
+    const int J = blockIdx.x;
+    const int32_t* xb = A.xblk + XB_N * J;
+    const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
+    const int32_t* ch = A.chdr + CH_N * J;
+    const int o1 = ch[CH_O1], o2 = ch[CH_O2], h = ch[CH_H], w = ch[CH_W], stride = ch[CH_STRIDE];
+    const long long comp = ((long long)ch[CH_COMP_HI] << 32) | (unsigned int)ch[CH_COMP_LO];
+    const long long slot0 = ch[CH_OUT_SLOT];
+    const long long area = (long long)h * stride;
+    const int nx = hx * wx, nA = h * w;
+    const int bs = padw(w);
+    if (nA == 0) return;  // handled (empty outputs) by k_sink
+    int32_t mem[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
+    // shared memory
+    const int s2 = 2 * s, BS = padw(A.smaxW);
+    double* dsm = reinterpret_cast<double*>(smem_raw);
+    struct {
+        double* red;
+        float* T;
+        float* tab1;
+        float* tab2;
+        float* a;
+        float* coef;
+        int* ctl;
+    } S;
+    S.red = dsm;
+    float* f = reinterpret_cast<float*>(dsm + 32 * 16 + 16);
+    S.T = f; f += 4 * s2 * BS;
+    S.tab1 = f; f += A.smaxH * s2;
+    S.tab2 = f; f += BS * s2;
+    S.a = f; f += A.amax;
+    S.coef = f; f += 16;
+    S.ctl = reinterpret_cast<int*>(f);
+    // the change of gauge of this cell's solve, and its kernel tables
+    const float* gg = A.gauge + 8 * J;
+    const float l1 = gg[2], l2 = gg[3], uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
+    for (int v1 = tid; v1 < h; v1 += NT) {
+        const double tt = (v1 - (double)vc1) / (double)l1;
+        const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
+        const double w0 = 2.0 * ((us - (double)uc1) - tt);
+        const float w0f = (float)w0, kl = (float)(A.k2d * l1);
+        for (int u1 = 0; u1 < hx; ++u1) {
+            const float D = (float)(u1 - us);
+            S.tab1[u1 * h + v1] = kl * D * (D + w0f);
         }
-        __syncthreads();
-        // C2: each member's share of the column mass, as a ratio of partial sums
-        // with one common shift, so that sum_i nu_i(v) = nu_J(v) up to FP32
-        // rounding whatever the size of the log-domain values:
-        //   nu_i(v) = nu_J(v) * sum_{u in X_i} pi(u, v) / sum_u pi(u, v),
-        // and the mean squared displacement E_i(v) under pi(., v) restricted to X_i.
-        double accm[4] = {0, 0, 0, 0}, accd[4] = {0, 0, 0, 0};
-        for (int v = tid; v < nA; v += NT) {
-            const int v1 = v / w, v2 = v - v1 * w;
-            const float* tb = S.tab1 + v1;
-            const float nuv = A.comp_nu[comp + (long long)v1 * stride + v2];
-            float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};
-            if (nuv > 0.f) {
-                float mx = DD_NEG;
-                for (int cg = 0; cg < ncg; ++cg)
-                    for (int u1 = 0; u1 < hx; ++u1) mx = fmaxf(mx, T2[(cg * hx + u1) * w + v2] - tb[u1 * h]);
-                float den = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (k >= nmem) break;
-                    const int rg = k / ncg, cg = k - rg * ncg;
-                    const float* Tc = T2 + cg * hx * w + v2;
-                    const float* Mc = M2 + cg * hx * w + v2;
-                    float nk = 0.f, ek = 0.f;
-                    for (int kk = 0; kk < s; ++kk) {
-                        const int u1 = rg * s + kk;
-                        const float wt = ex2f(Tc[u1 * w] - tb[u1 * h] - mx);
-                        const float dd = (float)(r0 + u1 - o1 - v1);
-                        nk += wt;
-                        ek += wt * (dd * dd + Mc[u1 * w]);
-                    }
-                    num[k] = nk;
-                    ew[k] = nk > 0.f ? ek / nk : 0.f;
-                    den += nk;
-                }
-                const float sc = den > 0.f ? nuv / den : 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) num[k] *= sc;
-            }
+    }
+    for (int v2 = tid; v2 < w; v2 += NT) {
+        const double tt = (v2 - (double)vc2) / (double)l2;
+        const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
+        const double w0 = 2.0 * ((us - (double)uc2) - tt);
+        const float w0f = (float)w0, kl = (float)(A.k2d * l2);
+        for (int u2 = 0; u2 < wx; ++u2) {
+            const float D = (float)(u2 - us);
+            S.tab2[u2 * bs + v2] = kl * D * (D + w0f);
+        }
+    }
+    const float* ap = A.alpha + (long long)A.amax * J;
+    for (int u = tid; u < nx; u += NT) S.a[u] = ap[u];
+    float* aC = S.a;
+    __syncthreads();
+
+    // ---- 3. CompositeToBasic with D_i -----------------------------------
+    // C1: per column group cg, T2(cg, u1, v2) = LSE over u2 in the group, and
+    //     M2 = mean of (x2 - y2)^2 under that partial distribution.
+    const int ncg = wx / s, nrg = hx / s;
+    float* T2 = S.T;
+    float* M2 = S.T + 2 * (2 * s) * padw(A.smaxW);
+    for (int q = tid; q < ncg * hx * w; q += NT) {
+        const int cg = q / (hx * w), rem = q - cg * hx * w;
+        const int u1 = rem / w, v2 = rem - u1 * w;
+        const float* ar = aC + u1 * wx + cg * s;
+        const float* tb = S.tab2 + (cg * s) * bs + v2;
+        const float lse = lse2(s, [&](int k) { return ar[k] - tb[k * bs]; });
+        float mom = 0.f;
+        for (int k = 0; k < s; ++k) {
+            const float dd = (float)(c0 + cg * s + k - o2 - v2);
+            mom += ex2f(ar[k] - tb[k * bs] - lse) * dd * dd;
+        }
+        T2[q] = lse;
+        M2[q] = mom;
+    }
+    __syncthreads();
+    // C2: each member's share of the column mass, as a ratio of partial sums
+    // with one common shift, so that sum_i nu_i(v) = nu_J(v) up to FP32
+    // rounding whatever the size of the log-domain values:
+    //   nu_i(v) = nu_J(v) * sum_{u in X_i} pi(u, v) / sum_u pi(u, v),
+    // and the mean squared displacement E_i(v) under pi(., v) restricted to X_i.
+    float accm[4] = {0.f, 0.f, 0.f, 0.f}, accd[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int v = tid; v < nA; v += NT) {
+        const int v1 = v / w, v2 = v - v1 * w;
+        const float* tb = S.tab1 + v1;
+        const float nuv = A.comp_nu[comp + (long long)v1 * stride + v2];
+        float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};
+        if (nuv > 0.f) {
+            float mx = DD_NEG;
+            for (int cg = 0; cg < ncg; ++cg)
+                for (int u1 = 0; u1 < hx; ++u1) mx = fmaxf(mx, T2[(cg * hx + u1) * w + v2] - tb[u1 * h]);
+            float den = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k >= nmem) break;
-                A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = num[k];
-                accm[k] += num[k];
-                accd[k] += (double)num[k] * ew[k];
-            }
-        }
-        double red8[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { red8[k] = accm[k]; red8[4 + k] = accd[k]; }
-        block_sum_d<8>(red8, S.red);
-        (void)nrg;
-
-        // ---- 4. balancing coefficients (member order walk) -------------------
-        if (tid == 0) {
-            double mass[4], e[4];
-            for (int k = 0; k < 4; ++k) {
-                mass[k] = red8[k];
-                e[k] = (k < nmem) ? mass[k] - A.m[mem[k]] : 0.0;
-            }
-            double cf[4][4];
-            for (int j = 0; j < 4; ++j)
-                for (int k = 0; k < 4; ++k) cf[j][k] = (j == k) ? 1.0 : 0.0;
-            int pos[4], neg[4], np = 0, nn = 0;
-            for (int k = 0; k < nmem; ++k) {
-                if (e[k] > 0.0) pos[np++] = k;
-                else if (e[k] < 0.0) neg[nn++] = k;
-            }
-            int p = 0, q = 0;
-            double rp = np ? e[pos[0]] : 0.0, rq = nn ? -e[neg[0]] : 0.0;
-            while (p < np && q < nn) {
-                const int i = pos[p], j = neg[q];
-                const double d = fmin(rp, rq);
-                const double f = d / mass[i];
-                cf[i][i] -= f;
-                cf[j][i] += f;
-                rp -= d;
-                rq -= d;
-                if (rp <= 0.0) { ++p; rp = p < np ? e[pos[p]] : 0.0; }
-                if (rq <= 0.0) { ++q; rq = q < nn ? -e[neg[q]] : 0.0; }
-            }
-            for (int j = 0; j < 4; ++j)
-                for (int k = 0; k < 4; ++k) S.coef[4 * j + k] = (float)cf[j][k];
-            for (int k = 0; k < nmem; ++k) {
-                double* bm = A.bmom + BM_N * mem[k];
-                bm[BM_D] = A.h2 * red8[4 + k];
-                bm[BM_PREMASS] = mass[k];
-            }
-            for (int k = 0; k < 16; ++k) S.ctl[4 + k] = 0;
-            for (int k = 0; k < 4; ++k) {
-                S.ctl[4 + 4 * k + 0] = INT32_MAX;  // min row
-                S.ctl[4 + 4 * k + 1] = -1;         // max row
-                S.ctl[4 + 4 * k + 2] = INT32_MAX;  // min col
-                S.ctl[4 + 4 * k + 3] = -1;         // max col
-            }
-        }
-        __syncthreads();
-
-        // ---- 5. apply balancing, truncate, box and moments -------------------
-        const double bc1 = 0.5 * (h - 1), bc2 = 0.5 * (w - 1);
-        float cf[4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cf[j][k] = S.coef[4 * j + k];
-        int bb[4][4];
-        double mom[16];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            bb[k][0] = INT32_MAX; bb[k][1] = -1; bb[k][2] = INT32_MAX; bb[k][3] = -1;
-        }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) mom[k] = 0.0;
-        for (int v = tid; v < nA; v += NT) {
-            const int v1 = v / w, v2 = v - v1 * w;
-            const long long off = slot0 + (long long)v1 * stride + v2;
-            float vals[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) vals[k] = (k < nmem) ? A.pool_out[off + k * area] : 0.f;
-            if (A.pre) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nmem) A.pre[off + k * area] = vals[k];
-            }
-            const double y1 = (double)v1 - bc1, y2 = (double)v2 - bc2;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= nmem) break;
-                float nv = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) nv += cf[j][k] * vals[k];
-                if (!(nv >= A.trunc)) nv = 0.f;
-                A.pool_out[off + j * area] = nv;
-                if (nv > 0.f) {
-                    bb[j][0] = min(bb[j][0], v1); bb[j][1] = max(bb[j][1], v1);
-                    bb[j][2] = min(bb[j][2], v2); bb[j][3] = max(bb[j][3], v2);
-                    const double dv = nv;
-                    mom[4 * j + 0] += dv;
-                    mom[4 * j + 1] += dv * y1;
-                    mom[4 * j + 2] += dv * y2;
-                    mom[4 * j + 3] += dv * (y1 * y1 + y2 * y2);
+                const int rg = k / ncg, cg = k - rg * ncg;
+                const float* Tc = T2 + cg * hx * w + v2;
+                const float* Mc = M2 + cg * hx * w + v2;
+                float nk = 0.f, ek = 0.f;
+                for (int kk = 0; kk < s; ++kk) {
+                    const int u1 = rg * s + kk;
+                    const float wt = ex2f(Tc[u1 * w] - tb[u1 * h] - mx);
+                    const float dd = (float)(r0 + u1 - o1 - v1);
+                    nk += wt;
+                    ek += wt * (dd * dd + Mc[u1 * w]);
                 }
+                num[k] = nk;
+                ew[k] = nk > 0.f ? ek / nk : 0.f;
+                den += nk;
             }
+            const float sc = den > 0.f ? nuv / den : 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) num[k] *= sc;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (k >= nmem) break;
-            atomicMin(&S.ctl[4 + 4 * k + 0], bb[k][0]);
-            atomicMax(&S.ctl[4 + 4 * k + 1], bb[k][1]);
-            atomicMin(&S.ctl[4 + 4 * k + 2], bb[k][2]);
-            atomicMax(&S.ctl[4 + 4 * k + 3], bb[k][3]);
+            A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = num[k];
+            accm[k] += num[k];
+            accd[k] += num[k] * ew[k];
         }
-        block_sum_d<16>(mom, S.red);  // contains __syncthreads
-
-        // ---- compaction in place (dst index never exceeds src index) --------
-        // Each member is rescaled to its basic mass m_i after truncation, so that
-        // the removed entries do not leave later cell problems unbalanced.
-        for (int k = 0; k < nmem; ++k) {
-            const int rlo = S.ctl[4 + 4 * k + 0], rhi = S.ctl[4 + 4 * k + 1];
-            const int clo = S.ctl[4 + 4 * k + 2], chi = S.ctl[4 + 4 * k + 3];
-            const bool empty = rhi < 0;
-            const int hh = empty ? 0 : rhi - rlo + 1, ww = empty ? 0 : chi - clo + 1;
-            const int st = (ww + 3) & ~3;
-            const double msum = mom[4 * k + 0];
-            const float fsc = msum > 0.0 ? (float)(A.m[mem[k]] / msum) : 1.f;
-            float* sl = A.pool_out + slot0 + k * area;
-            const int n = hh * st;
-            for (int base = 0; base < n; base += NT) {
-                const int dI = base + tid;
-                float val = 0.f;
-                if (dI < n) {
-                    const int rr = dI / st, cc = dI - rr * st;
-                    if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
-                }
-                __syncthreads();
-                if (dI < n) sl[dI] = val;
-                __syncthreads();
-            }
-            if (tid == 0) {
-                const int i = mem[k];
-                int32_t* bo = A.bhdr_out + BH_N * i;
-                bo[BH_O1] = empty ? 0 : o1 + rlo;
-                bo[BH_O2] = empty ? 0 : o2 + clo;
-                bo[BH_H] = hh;
-                bo[BH_W] = ww;
-                bo[BH_STRIDE] = st;
-                bo[BH_START] = (int32_t)(slot0 + k * area);
-                double* bm = A.bmom + BM_N * i;
-                const double ms = mom[4 * k + 0];
-                const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
-                bm[BM_MASS] = ms > 0 ? A.m[i] : 0.0;
-                bm[BM_Y1] = o1 + bc1 + m1;
-                bm[BM_Y2] = o2 + bc2 + m2;
-                bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
-            }
-        }
-        __syncthreads();
     }
+    double red8[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { red8[k] = accm[k]; red8[4 + k] = accd[k]; }
+    block_sum_d<8>(red8, S.red);
+    (void)nrg;
+
+    // ---- 4. balancing coefficients (member order walk) -------------------
+    if (tid == 0) {
+        double mass[4], e[4];
+        for (int k = 0; k < 4; ++k) {
+            mass[k] = red8[k];
+            e[k] = (k < nmem) ? mass[k] - A.m[mem[k]] : 0.0;
+        }
+        double cf[4][4];
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < 4; ++k) cf[j][k] = (j == k) ? 1.0 : 0.0;
+        int pos[4], neg[4], np = 0, nn = 0;
+        for (int k = 0; k < nmem; ++k) {
+            if (e[k] > 0.0) pos[np++] = k;
+            else if (e[k] < 0.0) neg[nn++] = k;
+        }
+        int p = 0, q = 0;
+        double rp = np ? e[pos[0]] : 0.0, rq = nn ? -e[neg[0]] : 0.0;
+        while (p < np && q < nn) {
+            const int i = pos[p], j = neg[q];
+            const double d = fmin(rp, rq);
+            const double f = d / mass[i];
+            cf[i][i] -= f;
+            cf[j][i] += f;
+            rp -= d;
+            rq -= d;
+            if (rp <= 0.0) { ++p; rp = p < np ? e[pos[p]] : 0.0; }
+            if (rq <= 0.0) { ++q; rq = q < nn ? -e[neg[q]] : 0.0; }
+        }
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < 4; ++k) S.coef[4 * j + k] = (float)cf[j][k];
+        for (int k = 0; k < nmem; ++k) {
+            double* bm = A.bmom + BM_N * mem[k];
+            bm[BM_D] = A.h2 * red8[4 + k];
+            bm[BM_PREMASS] = mass[k];
+        }
+        for (int k = 0; k < 16; ++k) S.ctl[4 + k] = 0;
+        for (int k = 0; k < 4; ++k) {
+            S.ctl[4 + 4 * k + 0] = INT32_MAX;  // min row
+            S.ctl[4 + 4 * k + 1] = -1;         // max row
+            S.ctl[4 + 4 * k + 2] = INT32_MAX;  // min col
+            S.ctl[4 + 4 * k + 3] = -1;         // max col
+        }
+    }
+    __syncthreads();
+
+    // ---- 5. apply balancing, truncate, box and moments -------------------
+    const double bc1 = 0.5 * (h - 1), bc2 = 0.5 * (w - 1);
+    float cf[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cf[j][k] = S.coef[4 * j + k];
+    int bb[4][4];
+    float momf[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        bb[k][0] = INT32_MAX; bb[k][1] = -1; bb[k][2] = INT32_MAX; bb[k][3] = -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) momf[k] = 0.f;
+    for (int v = tid; v < nA; v += NT) {
+        const int v1 = v / w, v2 = v - v1 * w;
+        const long long off = slot0 + (long long)v1 * stride + v2;
+        float vals[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) vals[k] = (k < nmem) ? A.pool_out[off + k * area] : 0.f;
+        if (A.pre) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nmem) A.pre[off + k * area] = vals[k];
+        }
+        const float y1 = (float)(v1 - bc1), y2 = (float)(v2 - bc2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= nmem) break;
+            float nv = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nv += cf[j][k] * vals[k];
+            if (!(nv >= A.trunc)) nv = 0.f;
+            A.pool_out[off + j * area] = nv;
+            if (nv > 0.f) {
+                bb[j][0] = min(bb[j][0], v1); bb[j][1] = max(bb[j][1], v1);
+                bb[j][2] = min(bb[j][2], v2); bb[j][3] = max(bb[j][3], v2);
+                momf[4 * j + 0] += nv;
+                momf[4 * j + 1] += nv * y1;
+                momf[4 * j + 2] += nv * y2;
+                momf[4 * j + 3] += nv * (y1 * y1 + y2 * y2);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k >= nmem) break;
+        atomicMin(&S.ctl[4 + 4 * k + 0], bb[k][0]);
+        atomicMax(&S.ctl[4 + 4 * k + 1], bb[k][1]);
+        atomicMin(&S.ctl[4 + 4 * k + 2], bb[k][2]);
+        atomicMax(&S.ctl[4 + 4 * k + 3], bb[k][3]);
+    }
+    double mom[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) mom[k] = momf[k];
+    block_sum_d<16>(mom, S.red);  // contains __syncthreads
+
+    // ---- compaction in place (dst index never exceeds src index) --------
+    // Each member is rescaled to its basic mass m_i after truncation, so that
+    // the removed entries do not leave later cell problems unbalanced.
+    for (int k = 0; k < nmem; ++k) {
+        const int rlo = S.ctl[4 + 4 * k + 0], rhi = S.ctl[4 + 4 * k + 1];
+        const int clo = S.ctl[4 + 4 * k + 2], chi = S.ctl[4 + 4 * k + 3];
+        const bool empty = rhi < 0;
+        const int hh = empty ? 0 : rhi - rlo + 1, ww = empty ? 0 : chi - clo + 1;
+        const int st = (ww + 3) & ~3;
+        const double msum = mom[4 * k + 0];
+        const float fsc = msum > 0.0 ? (float)(A.m[mem[k]] / msum) : 1.f;
+        float* sl = A.pool_out + slot0 + k * area;
+        const int n = hh * st;
+        for (int base = 0; base < n; base += NT) {
+            const int dI = base + tid;
+            float val = 0.f;
+            if (dI < n) {
+                const int rr = dI / st, cc = dI - rr * st;
+                if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
+            }
+            __syncthreads();
+            if (dI < n) sl[dI] = val;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int i = mem[k];
+            int32_t* bo = A.bhdr_out + BH_N * i;
+            bo[BH_O1] = empty ? 0 : o1 + rlo;
+            bo[BH_O2] = empty ? 0 : o2 + clo;
+            bo[BH_H] = hh;
+            bo[BH_W] = ww;
+            bo[BH_STRIDE] = st;
+            bo[BH_START] = (int32_t)(slot0 + k * area);
+            double* bm = A.bmom + BM_N * i;
+            const double ms = mom[4 * k + 0];
+            const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
+            bm[BM_MASS] = ms > 0 ? A.m[i] : 0.0;
+            bm[BM_Y1] = o1 + bc1 + m1;
+            bm[BM_Y2] = o2 + bc2 + m2;
+            bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
+        }
+    }
+    
 }
 
 }  // namespace
@@ -898,8 +1004,14 @@ __global__ void __launch_bounds__(512) k_half(HalfArgs A) {
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
     size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS) + 16;
-    size_t fl = 2 * (size_t)maxarea + 4 * s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 3 * (size_t)c->amax + 16 + 32;
+    size_t fl = 2 * (size_t)maxarea + 4 * s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 4 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
+}
+
+size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw) {
+    const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
+    size_t fl = 4 * s2 * BS + (size_t)maxh * s2 + BS * s2 + (size_t)c->amax + 16 + 32;
+    return sizeof(double) * (32 * 16 + 16) + sizeof(float) * fl;
 }
 
 int half_kernel_max_smem() { return 227 * 1024; }
@@ -910,16 +1022,25 @@ int launch_plan_half(dd_ctx* c, int part) {
     return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
 }
 
-static bool g_attr_set = false;
+int half_padw(int w) { return padw(w); }
 
-int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
+namespace {
+bool g_attr_set = false;
+
+int set_attrs() {
+    if (g_attr_set) return DD_OK;
+    const int mx = half_kernel_max_smem();
+    if (cudaFuncSetAttribute(k_sink<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_c2b, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+        return DD_ERR_CUDA;
+    g_attr_set = true;
+    return DD_OK;
+}
+
+HalfArgs make_args(dd_ctx* c, int part) {
     DevPart& P = c->part[part];
-    if (!g_attr_set) {
-        if (cudaFuncSetAttribute(k_half, cudaFuncAttributeMaxDynamicSharedMemorySize, half_kernel_max_smem()) !=
-            cudaSuccess)
-            return DD_ERR_CUDA;
-        g_attr_set = true;
-    }
     HalfArgs A;
     A.N1 = c->N1; A.N2 = c->N2; A.s = c->s; A.ncell = P.ncell; A.amax = c->amax;
     A.k2 = c->k2; A.k2d = c->k2d; A.eps = c->eps; A.h2 = c->h * c->h;
@@ -930,27 +1051,54 @@ int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid) {
     A.alpha = P.alpha; A.gauge = P.gauge;
     A.warm = (c->opt.warm == DD_WARM_PREV && P.warm_valid) ? 1 : 0;
     A.lgmu = c->d_lgmu; A.mu = c->d_mu; A.nu = c->d_nu; A.m = c->d_m;
+    A.lnmu = c->d_lnmu; A.lnnu = c->d_lnnu; A.lnnuf = c->d_lnnuf;
     A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
     A.omega = (float)c->opt.omega;
     A.trunc = (float)c->opt.trunc;
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
     A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;
     A.queue = c->d_queue; A.status = c->d_status;
-    A.smaxA = (int)c->h_tot[PT_MAXAREA];
-    A.smaxH = (int)c->h_tot[PT_MAXH];
-    A.smaxW = (int)c->h_tot[PT_MAXW];
-    k_half<<<grid, threads, smem, c->stream>>>(A);
+    return A;
+}
+}  // namespace
+
+int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 256 ? 256 : 512); }
+
+int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
+                int threads, size_t smem, int grid, cudaStream_t stream) {
+    RET_IF(set_attrs());
+    HalfArgs A = make_args(c, part);
+    A.ncell = ncell;
+    A.order = order;
+    A.queue = queue;
+    A.smaxA = (int)dims[0];
+    A.smaxH = (int)dims[1];
+    A.smaxW = (int)dims[2];
+    switch (half_threads(threads)) {
+        case 128: k_sink<128><<<grid, 128, smem, stream>>>(A); break;
+        case 256: k_sink<256><<<grid, 256, smem, stream>>>(A); break;
+        default: k_sink<512><<<grid, 512, smem, stream>>>(A); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+}
+
+int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem) {
+    RET_IF(set_attrs());
+    HalfArgs A = make_args(c, part);
+    A.smaxA = (int)dims[0];
+    A.smaxH = (int)dims[1];
+    A.smaxW = (int)dims[2];
+    k_c2b<<<c->part[part].ncell, 128, smem, c->stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
 }
 
 int half_occupancy(int threads, size_t smem) {
+    if (set_attrs() != DD_OK) return 0;
     int nb = 0;
-    if (!g_attr_set) {
-        if (cudaFuncSetAttribute(k_half, cudaFuncAttributeMaxDynamicSharedMemorySize, half_kernel_max_smem()) !=
-            cudaSuccess)
-            return 0;
-        g_attr_set = true;
+    switch (half_threads(threads)) {
+        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<128>, 128, smem); break;
+        case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<256>, 256, smem); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<512>, 512, smem); break;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_half, threads, smem);
     return nb;
 }

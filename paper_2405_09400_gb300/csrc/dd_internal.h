@@ -63,6 +63,9 @@ struct dd_ctx {
     double* d_mu = nullptr;
     double* d_nu = nullptr;
     float* d_lgmu = nullptr;   // log2 mu (DD_NEG where 0)
+    double* d_lnmu = nullptr;  // ln mu, ln nu (FP64; -inf where 0)
+    double* d_lnnu = nullptr;
+    float* d_lnnuf = nullptr;  // ln nu in FP32 (DD_NEG where 0)
     double* d_m = nullptr;     // basic masses
     double* d_xmom = nullptr;  // per basic cell: x1bar, x2bar, var (pixels)
     int32_t* d_nbr = nullptr;  // nb x 5
@@ -104,6 +107,8 @@ struct dd_ctx {
     double* d_red = nullptr;
 
     cudaEvent_t ev[8] = {};
+    cudaStream_t side = nullptr;  // second stream: the large-box class of cells
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
 
@@ -114,9 +119,16 @@ struct dd_ctx {
 
 // kernels / launchers (dd_half.cu)
 int launch_plan_half(dd_ctx* c, int part);
-int launch_half(dd_ctx* c, int part, int threads, size_t smem, int grid);
+// cells whose padded box area / width exceed these run in the large-box launch
+constexpr long long kSmallArea = 1536;
+constexpr int kSmallW = 64;
+int half_padw(int w);
+int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
+                int threads, size_t smem, int grid, cudaStream_t stream);
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
 int half_kernel_max_smem();
+size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
+int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem);
 int half_occupancy(int threads, size_t smem);
 // dd_flow.cu
 int launch_cbar(dd_ctx* c);
