@@ -115,6 +115,10 @@ void dd_default_options(dd_options* opt);
 /* Human-readable name of a status code (static string). */
 const char* dd_strerror(int status);
 
+/* The CUDA call and error message behind the last DD_ERR_CUDA (static string,
+ * shared by all contexts; empty if none). */
+const char* dd_last_error(void);
+
 /*
  * Create a context. mu, nu: N1*N2 float64, >= 0, each summing to 1 within
  * 1e-12. eps > 0. cell_size must divide N1 and N2, give an even number of basic

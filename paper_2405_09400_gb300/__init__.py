@@ -28,7 +28,7 @@ DD_WARM_PREV, DD_WARM_COLD = 0, 1
 DD_FLAG_KEEP_PREBALANCE = 1
 
 EXPORTS = [
-    "dd_default_options", "dd_strerror", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
+    "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
@@ -66,7 +66,10 @@ class dd_flow_stats(C.Structure):
 class DDError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        msg = f"{where}: {strerror(code)} ({code})"
+        if code == DD_ERR_CUDA:
+            msg += " [" + load().dd_last_error().decode(errors="replace") + "]"
+        super().__init__(msg)
 
 
 _lib = None
@@ -86,6 +89,7 @@ def load():
     sig = {
         "dd_default_options": (None, [P(dd_options)]),
         "dd_strerror": (C.c_char_p, [C.c_int]),
+        "dd_last_error": (C.c_char_p, []),
         "dd_init": (C.c_int, [_f64p, _f64p, P(dd_grid), C.c_double, C.c_int, P(dd_options), vp, P(vp)]),
         "dd_set_plan": (C.c_int, [vp, _i32p, _f64p, C.c_size_t]),
         "dd_iterate": (C.c_int, [vp, C.c_int, P(dd_stats)]),

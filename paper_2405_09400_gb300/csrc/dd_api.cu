@@ -7,21 +7,30 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "dd_internal.h"
 
-#define CK(x)                                   \
-    do {                                        \
-        if ((x) != cudaSuccess) return DD_ERR_CUDA; \
+#define CK(x)                                                       \
+    do {                                                            \
+        cudaError_t e_ = (x);                                       \
+        if (e_ != cudaSuccess) return dd_record_cuda_error(e_, #x); \
     } while (0)
 #define RET(x)                         \
     do {                               \
         int r_ = (x);                  \
         if (r_ != DD_OK) return r_;    \
     } while (0)
+
+static char g_last_error[256] = "";
+
+int dd_record_cuda_error(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return DD_ERR_CUDA;
+}
 
 namespace {
 
@@ -175,6 +184,8 @@ void dd_default_options(dd_options* o) {
     o->omega = 1.0;
 }
 
+const char* dd_last_error(void) { return g_last_error; }
+
 const char* dd_strerror(int s) {
     switch (s) {
         case DD_OK: return "ok";
@@ -205,6 +216,7 @@ void dd_destroy(dd_ctx* c) {
         dfree(c->pool[p]); dfree(c->bhdr[p]);
     }
     dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
+    dfree(c->d_gscr); dfree(c->d_goff);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
     if (c->h_tot) cudaFreeHost(c->h_tot);
     if (c->h_cbar) cudaFreeHost(c->h_cbar);
@@ -225,13 +237,19 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     if (N1 <= 0 || N2 <= 0 || !(grid->h > 0) || !(eps > 0) || s <= 0 || N1 % s || N2 % s) return DD_ERR_ARG;
     if ((N1 / s) % 2 || (N2 / s) % 2 || 2 * s > 16) return DD_ERR_ARG;
     const size_t np = (size_t)N1 * N2;
-    double smu = 0, snu = 0;
+    // compensated (Neumaier) sums: a plain running sum over a megapixel grid is
+    // off by ~1e-11 and would reject correctly normalised measures
+    double smu = 0, snu = 0, cmu = 0, cnu = 0;
     for (size_t k = 0; k < np; ++k) {
         if (!(mu[k] >= 0) || !(nu[k] >= 0) || !std::isfinite(mu[k]) || !std::isfinite(nu[k])) return DD_ERR_ARG;
-        smu += mu[k];
-        snu += nu[k];
+        double t = smu + mu[k];
+        cmu += std::fabs(smu) >= mu[k] ? (smu - t) + mu[k] : (mu[k] - t) + smu;
+        smu = t;
+        t = snu + nu[k];
+        cnu += std::fabs(snu) >= nu[k] ? (snu - t) + nu[k] : (nu[k] - t) + snu;
+        snu = t;
     }
-    if (std::fabs(smu - 1.0) > 1e-12 || std::fabs(snu - 1.0) > 1e-12) return DD_ERR_ARG;
+    if (std::fabs(smu + cmu - 1.0) > 1e-12 || std::fabs(snu + cnu - 1.0) > 1e-12) return DD_ERR_ARG;
     dd_ctx* c = new (std::nothrow) dd_ctx();
     if (!c) return DD_ERR_OOM;
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
@@ -452,6 +470,7 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
         for (int i = 0; i < c->nb; ++i) ent += (int64_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
         st->stored_entries = ent;
     }
+    if (status[2] > 0) return DD_ERR_POOL;  // a kernel found its shared memory too small and skipped
     return status[0] > 0 ? DD_ERR_MAXITER : DD_OK;
 }
 
@@ -488,60 +507,88 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     if (P.warm_valid) RET(d2h(itp.data(), P.iters, P.ncell, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     std::vector<double> key(P.ncell);
-    std::vector<int32_t> big, small;
-    long long dims[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [class][area, h, w]
+    // classes: 0 large boxes (second stream), 1 small boxes, 2 boxes beyond shared
+    // memory (their two box arrays in global scratch, also on the second stream)
+    std::vector<int32_t> cls_cells[3];
+    long long dims[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [class][area, h, w]
+    std::vector<long long> goff(P.ncell, -1);
+    long long gtot = 0;
+    // largest box area a shared-memory launch can hold next to the tables of the
+    // tallest and widest boxes of this half-iteration
+    long long hmax = 1, wmax = 1;
+    for (int J = 0; J < P.ncell; ++J) {
+        hmax = std::max(hmax, (long long)ch[CH_N * J + CH_H]);
+        wmax = std::max(wmax, (long long)ch[CH_N * J + CH_W]);
+    }
+    const long long base = (long long)half_smem_bytes(c, 0, hmax, wmax);
+    const long long a_cap = std::max(0LL, ((long long)half_kernel_max_smem() - base) / 8);
     for (int J = 0; J < P.ncell; ++J) {
         const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
         const long long a = (long long)h * half_padw(w);
         key[J] = (double)h * w * std::max(1, itp[J]);
-        const int cls = a <= kSmallArea && w <= kSmallW ? 1 : 0;
-        (cls ? small : big).push_back(J);
+        int cls = a <= kSmallArea && w <= kSmallW ? 1 : 0;
+        if (cls == 0 && a > a_cap) {
+            cls = 2;
+            goff[J] = gtot;
+            gtot += 2 * a;
+        }
+        cls_cells[cls].push_back(J);
         dims[cls][0] = std::max(dims[cls][0], a);
         dims[cls][1] = std::max(dims[cls][1], (long long)h);
         dims[cls][2] = std::max(dims[cls][2], (long long)w);
     }
     auto by_key = [&](int32_t x, int32_t y) { return key[x] > key[y]; };
-    std::stable_sort(big.begin(), big.end(), by_key);
-    std::stable_sort(small.begin(), small.end(), by_key);
-    std::vector<int32_t> order(big);
-    order.insert(order.end(), small.begin(), small.end());
-    RET(h2d(P.order, order.data(), order.size(), c->stream));
-    size_t smem_c[2] = {0, 0};
-    for (int cls = 0; cls < 2; ++cls) {
-        smem_c[cls] = half_smem_bytes(c, dims[cls][0], dims[cls][1], dims[cls][2]);
-        if (smem_c[cls] > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+    std::vector<int32_t> order;
+    size_t cls_off[3];
+    for (int k = 0; k < 3; ++k) {
+        std::stable_sort(cls_cells[k].begin(), cls_cells[k].end(), by_key);
+        cls_off[k] = order.size();
+        order.insert(order.end(), cls_cells[k].begin(), cls_cells[k].end());
     }
-    const int thr_c[2] = {c->opt.threads > 0 ? choose_threads(c, 0) : 256,
-                          c->opt.threads > 0 ? choose_threads(c, 0) : 128};
+    RET(h2d(P.order, order.data(), order.size(), c->stream));
+    if (!cls_cells[2].empty()) {
+        RET(ensure_floats(&c->d_gscr, &c->gscr_cap, (size_t)gtot));
+        if (!c->d_goff) RET(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        RET(h2d(c->d_goff, goff.data(), goff.size(), c->stream));
+    }
+    size_t smem_c[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        if (cls_cells[k].empty()) continue;
+        smem_c[k] = half_smem_bytes(c, k == 2 ? 0 : dims[k][0], dims[k][1], dims[k][2]);
+        if (smem_c[k] > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+    }
+    const int thr_c[3] = {c->opt.threads > 0 ? choose_threads(c, 0) : 256,
+                          c->opt.threads > 0 ? choose_threads(c, 0) : 128,
+                          c->opt.threads > 0 ? choose_threads(c, 0) : 256};
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
-    const bool has_big = !big.empty(), has_small = !small.empty();
-    if (has_big && has_small) {
+    const bool side_used = !cls_cells[1].empty() && (!cls_cells[0].empty() || !cls_cells[2].empty());
+    if (side_used) {
         CK(cudaEventRecord(c->ev_fork, c->stream));
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     }
-    if (has_big) {
-        int occ = std::max(1, half_occupancy(thr_c[0], smem_c[0]));
-        int grid = std::max(1, std::min((int)big.size(), c->nsm * occ));
-        RET(launch_half(c, part, P.order, (int)big.size(), c->d_queue, dims[0], thr_c[0], smem_c[0], grid,
-                        has_small ? c->side : c->stream));
+    for (int k : {2, 0, 1}) {
+        if (cls_cells[k].empty()) continue;
+        const int n = (int)cls_cells[k].size();
+        int occ = std::max(1, half_occupancy(thr_c[k], smem_c[k]));
+        int grid = std::max(1, std::min(n, c->nsm * occ));
+        cudaStream_t st = (k != 1 && side_used) ? c->side : c->stream;
+        // the global-scratch class keeps no box array in shared memory: its carve
+        // must see area 0, as its shared-memory size was computed with area 0
+        const long long kd[3] = {k == 2 ? 0 : dims[k][0], dims[k][1], dims[k][2]};
+        RET(launch_half(c, part, P.order + cls_off[k], n, c->d_queue + k, kd, thr_c[k], smem_c[k], grid, st,
+                        k == 2));
         c->n_launch += 1;
     }
-    if (has_small) {
-        int occ = std::max(1, half_occupancy(thr_c[1], smem_c[1]));
-        int grid = std::max(1, std::min((int)small.size(), c->nsm * occ));
-        RET(launch_half(c, part, P.order + big.size(), (int)small.size(), c->d_queue + 1, dims[1], thr_c[1],
-                        smem_c[1], grid, c->stream));
-        c->n_launch += 1;
-    }
-    if (has_big && has_small) {
+    if (side_used) {
         CK(cudaEventRecord(c->ev_join, c->side));
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
     {
-        const long long dall[3] = {std::max(dims[0][0], dims[1][0]), std::max(dims[0][1], dims[1][1]),
-                                   std::max(dims[0][2], dims[1][2])};
+        const long long dall[3] = {std::max({dims[0][0], dims[1][0], dims[2][0]}),
+                                   std::max({dims[0][1], dims[1][1], dims[2][1]}),
+                                   std::max({dims[0][2], dims[1][2], dims[2][2]})};
         const size_t sm = c2b_smem_bytes(c, dall[1], dall[2]);
         if (sm > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
         RET(launch_c2b(c, part, dall, sm));

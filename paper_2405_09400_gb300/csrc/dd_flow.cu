@@ -232,20 +232,20 @@ __global__ void k_l1y(long long n, const double* __restrict__ acc, const double*
 int launch_cbar(dd_ctx* c) {
     k_cbar<<<(c->nb + 255) / 256, 256, 0, c->stream>>>(c->nb, c->d_nbr, c->d_xmom, c->d_bmom, c->d_m,
                                                        c->h * c->h, c->d_cbar);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int launch_plan_exchange(dd_ctx* c) {
     k_plan_exchange<<<1, 1024, 0, c->stream>>>(c->nb, c->d_nbr, c->d_rev, c->d_w, c->bhdr[c->cur], c->d_xhdr,
                                                c->d_tot);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int launch_exchange(dd_ctx* c) {
     k_exchange<<<c->nb, 128, 0, c->stream>>>(c->nb, c->d_nbr, c->d_rev, c->d_w, c->d_m, c->bhdr[c->cur],
                                              c->pool[c->cur], c->d_xhdr, c->bhdr[1 - c->cur], c->pool[1 - c->cur],
                                              c->d_bmom, (float)c->opt.trunc);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int launch_l1y(dd_ctx* c, double* out_dev) {
@@ -254,5 +254,5 @@ int launch_l1y(dd_ctx* c, double* out_dev) {
     if (cudaMemsetAsync(out_dev, 0, sizeof(double), c->stream) != cudaSuccess) return DD_ERR_CUDA;
     k_scatter_y<<<c->nb, 128, 0, c->stream>>>(c->nb, c->N2, c->bhdr[c->cur], c->pool[c->cur], c->d_yacc);
     k_l1y<<<c->nsm * 2, 256, 0, c->stream>>>(n, c->d_yacc, c->d_nu, out_dev);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }

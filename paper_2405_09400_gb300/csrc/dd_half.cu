@@ -58,6 +58,12 @@ __device__ __forceinline__ float lg2f(float x) {
 }
 
 constexpr float kLn2 = 0.69314718055994530942f;
+
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
 constexpr double kLn2d = 0.69314718055994530942;
 
 // ---------------------------------------------------------------------------
@@ -216,6 +222,8 @@ struct HalfArgs {
     float* pre;  // optional prebalance copy (same layout as pool_out)
     int* queue;
     int* status;
+    float* gscratch;        // box arrays of cells too large for shared memory
+    const long long* goff;  // per cell: offset in gscratch, or -1 (shared memory)
     int smaxA, smaxH, smaxW;  // shared-memory capacities
 };
 
@@ -223,7 +231,7 @@ struct HalfArgs {
 struct Smem {
     float* lgnu;  // maxH * BS: log2 nu_J (DD_NEG where nu_J = 0 and in the padding)
     float* b;     // maxH * BS: Y dual b~ (DD_NEG where nu_J = 0 and in the padding)
-    float* T;     // 4 * (2s) * BS: Y stage 1; CompositeToBasic partial sums + moments
+    float* T;     // (2s) * BS: Y-update stage 1
     float* R;     // maxH * (2s): X stage 1
     float* tab1;  // (2s) * maxH: axis-1 kernel (gauge-reduced)
     float* tab2;  // (2s) * BS: axis-2 kernel (gauge-reduced, 0 in the padding)
@@ -236,6 +244,7 @@ struct Smem {
     double* B2;   // BS: min over u2 of the axis-2 kernel at v2
     float* coef;  // 16
     int* ctl;     // 32
+    long long end;  // bytes used
 };
 
 __device__ Smem carve(char* base, const HalfArgs& A) {
@@ -254,7 +263,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     float* f = reinterpret_cast<float*>(((uintptr_t)d + 15) & ~(uintptr_t)15);  // float4 rows
     S.lgnu = f; f += A.smaxA;
     S.b = f; f += A.smaxA;
-    S.T = f; f += 4 * s2 * BS;
+    S.T = f; f += s2 * BS;
     S.R = f; f += A.smaxH * s2;
     S.tab1 = f; f += A.smaxH * s2;
     S.tab2 = f; f += BS * s2;
@@ -263,6 +272,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.muxf = f; f += A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
+    S.end = reinterpret_cast<char*>(f + 32) - base;
     return S;
 }
 
@@ -281,9 +291,13 @@ __device__ __forceinline__ float lse2(int n, F term) {
 __device__ __forceinline__ bool shift_ok(float s) { return s >= 8.67e-19f && s <= 1.15e18f; }  // 2^-60 .. 2^60
 
 template <int NTB>
-__global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
+__global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
     Smem S = carve(smem_raw, A);
+    if (S.end > (long long)dyn_smem_bytes()) {  // host and kernel disagree on the layout
+        if (threadIdx.x == 0) atomicAdd(&A.status[2], 1);
+        return;
+    }
     const int tid = threadIdx.x, NT = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
     const int s = A.s;
@@ -303,6 +317,11 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
         const long long area = (long long)h * stride;
         const int nx = hx * wx, nA = h * w;
         const int bs = padw(w), bq = bs >> 2;
+        // log2 nu_J and b~ live in shared memory, or for boxes too large for it
+        // in a global scratch slot of the cell (L2-resident)
+        const long long go = A.goff ? A.goff[J] : -1;
+        float* const lgnu_p = go >= 0 ? A.gscratch + go : S.lgnu;
+        float* const b_p = go >= 0 ? A.gscratch + go + (long long)h * bs : S.b;
         int32_t mem[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
@@ -345,8 +364,8 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
                 const float f1 = (float)v1, f2 = (float)v2;
                 gf[0] += acc; gf[1] += acc * f1; gf[2] += acc * f2; gf[3] += acc * f1 * f1; gf[4] += acc * f2 * f2;
             }
-            S.lgnu[v] = lg;
-            S.b[v] = DD_NEG;
+            lgnu_p[v] = lg;
+            b_p[v] = DD_NEG;
         }
         for (int q = tid; q < hx * bs; q += NT) S.T[q] = DD_NEG;
         for (int u = tid; u < nx; u += NT) {
@@ -459,7 +478,7 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
         // threads per line of the X-update stage 2 (a power of two, lanes adjacent)
         int P2 = 1;
         while (P2 * 2 * nx <= NT && P2 < 16) P2 *= 2;
-        const float4* b4 = reinterpret_cast<const float4*>(S.b);
+        const float4* b4 = reinterpret_cast<const float4*>(b_p);
         const float4* t24 = reinterpret_cast<const float4*>(S.tab2);
         const int nq = (w + 3) >> 2;  // float4 groups holding data per row
         while (true) {
@@ -494,7 +513,7 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
             // four adjacent v2 per thread (float4 rows of T, b, log2 nu_J)
             for (int q = tid; q < h * nq; q += NT) {
                 const int v1 = q / nq, g4 = q - v1 * nq;
-                const float4 ln4 = reinterpret_cast<const float4*>(S.lgnu)[v1 * bq + g4];
+                const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
                 const float4 bp4 = b4[v1 * bq + g4];
                 const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
                 const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
@@ -532,7 +551,7 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
                     }
                     out[k] = ln[k] - (m[k] + lg2f(sa[k]));
                 }
-                reinterpret_cast<float4*>(S.b)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
+                reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
             }
             __syncthreads();
             // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over v2
@@ -676,9 +695,9 @@ __global__ void __launch_bounds__(NTB, 1024 / NTB) k_sink(HalfArgs A) {
         float ef = 0.f;
         for (int v = tid; v < nA; v += NT) {
             const int v1 = v / w, v2 = v - v1 * w;
-            const float bv = S.b[v1 * bs + v2];
+            const float bv = b_p[v1 * bs + v2];
             A.comp_b[comp + (long long)v1 * stride + v2] = bv;
-            if (S.lgnu[v1 * bs + v2] > 0.5f * DD_NEG) {
+            if (lgnu_p[v1 * bs + v2] > 0.5f * DD_NEG) {
                 const float nuJ = A.comp_nu[comp + (long long)v1 * stride + v2];
                 ef += nuJ * (kLn2 * bv - A.lnnuf[(o1 + v1) * A.N2 + (o2 + v2)]);
             }
@@ -750,6 +769,10 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     S.a = f; f += A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
+    if (reinterpret_cast<char*>(f + 32) - smem_raw > (long long)dyn_smem_bytes()) {
+        if (tid == 0) atomicAdd(&A.status[2], 1);
+        return;
+    }
     // the change of gauge of this cell's solve, and its kernel tables
     const float* gg = A.gauge + 8 * J;
     const float l1 = gg[2], l2 = gg[3], uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
@@ -1004,7 +1027,7 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
     size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS) + 16;
-    size_t fl = 2 * (size_t)maxarea + 4 * s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 4 * (size_t)c->amax + 16 + 32;
+    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 4 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
 }
 
@@ -1019,7 +1042,7 @@ int half_kernel_max_smem() { return 227 * 1024; }
 int launch_plan_half(dd_ctx* c, int part) {
     DevPart& P = c->part[part];
     k_plan_half<<<1, 1024, 0, c->stream>>>(P.ncell, P.members, c->bhdr[c->cur], P.chdr, P.xblk, c->d_tot);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int half_padw(int w) { return padw(w); }
@@ -1058,6 +1081,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
     A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;
     A.queue = c->d_queue; A.status = c->d_status;
+    A.gscratch = nullptr; A.goff = nullptr;
     return A;
 }
 }  // namespace
@@ -1065,9 +1089,13 @@ HalfArgs make_args(dd_ctx* c, int part) {
 int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 256 ? 256 : 512); }
 
 int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
-                int threads, size_t smem, int grid, cudaStream_t stream) {
+                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes) {
     RET_IF(set_attrs());
     HalfArgs A = make_args(c, part);
+    if (global_boxes) {
+        A.gscratch = c->d_gscr;
+        A.goff = c->d_goff;
+    }
     A.ncell = ncell;
     A.order = order;
     A.queue = queue;
@@ -1079,7 +1107,7 @@ int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue
         case 256: k_sink<256><<<grid, 256, smem, stream>>>(A); break;
         default: k_sink<512><<<grid, 512, smem, stream>>>(A); break;
     }
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem) {
@@ -1089,7 +1117,7 @@ int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem) {
     A.smaxH = (int)dims[1];
     A.smaxW = (int)dims[2];
     k_c2b<<<c->part[part].ncell, 128, smem, c->stream>>>(A);
-    return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 int half_occupancy(int threads, size_t smem) {

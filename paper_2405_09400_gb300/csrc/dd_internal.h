@@ -91,6 +91,10 @@ struct dd_ctx {
     // prebalance copy
     float* d_pre = nullptr;
     size_t pre_cap = 0;
+    // global scratch for cells whose boxes exceed shared memory
+    float* d_gscr = nullptr;
+    size_t gscr_cap = 0;
+    long long* d_goff = nullptr;
     int32_t* d_prehdr = nullptr;
 
     // flow
@@ -117,6 +121,13 @@ struct dd_ctx {
     int graph_cur = -1;
 };
 
+// last CUDA error, kept for dd_last_error()
+int dd_record_cuda_error(cudaError_t e, const char* where);
+inline int launch_status(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DD_OK : dd_record_cuda_error(e, where);
+}
+
 // kernels / launchers (dd_half.cu)
 int launch_plan_half(dd_ctx* c, int part);
 // cells whose padded box area / width exceed these run in the large-box launch
@@ -124,7 +135,7 @@ constexpr long long kSmallArea = 1536;
 constexpr int kSmallW = 64;
 int half_padw(int w);
 int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
-                int threads, size_t smem, int grid, cudaStream_t stream);
+                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes = false);
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
 int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
