@@ -20,6 +20,10 @@ It follows the paper step by step, in float64, with plain numpy/scipy:
 * ``hybrid``    the hybrid schedule of Alg. 3 and the objective / marginal errors.
 * ``dense``     a full-plan version for tiny grids (global Sinkhorn, Alg. 1 and
   Def. 3.4 on the explicit plan), used to pin the box version.
+* ``warmstart`` (not in the paper) the inputs and training targets of the
+  learned Sinkhorn initialisation of a composite cell.
+* ``mlp``       (not in the paper) the warm-start network, its loss and its
+  gradient by backpropagation.
 
 Readings of the paper where it is silent or ambiguous are listed in the
 module docstrings where they apply.
