@@ -55,9 +55,20 @@ extern "C" {
 #define DD_WARM_PREV 0 /* alpha_init = alpha of the previous solve on the same
                           partition (Alg. 4 input), zero on the first solve        */
 #define DD_WARM_COLD 1 /* alpha_init = 0 for every solve                          */
+#define DD_WARM_AFFINE 2 /* alpha_init = the cell's affine dual: the exact dual
+                            when nu_J is mu_J translated and stretched per axis
+                            (barycentres and variances of the two marginals);
+                            not in the paper                                     */
+#define DD_WARM_MLP 3  /* alpha_init = affine dual + the learned correction of
+                          dd_set_warmstart_weights (cells with a full 8 x 8
+                          block; the others use the affine dual); not in the
+                          paper, requires cell_size 4                            */
 
 #define DD_FLAG_KEEP_PREBALANCE 1 /* keep the pre-balance basic marginals of the
                                      last half-iteration for dd_get_prebalance     */
+#define DD_FLAG_COLLECT 2 /* compute the warm-start network's inputs before, and
+                             its training targets after, every cell solve, for
+                             dd_collect_cells (requires cell_size 4)              */
 
 typedef struct dd_grid {
     int32_t N1, N2; /* pixels per axis                                          */
@@ -259,6 +270,74 @@ int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t*
 #define DD_STATIC_MAX_CELLS 65536
 int dd_l1_y_error_static(int32_t N1, int32_t N2, int32_t nbasic, const int32_t* hdr, const float* data,
                          const double* nu, double* l1_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper). A multilayer perceptron maps features
+ * of a composite-cell problem to a correction r of the cell's affine dual; the
+ * solver starts from alpha_init = affine dual + r (DD_WARM_MLP). The
+ * converged Sinkhorn error judges it: a poor prediction costs iterations, never
+ * accuracy (every solve still runs to tol).
+ *
+ * Network: DD_MLP_NIN -> DD_MLP_NHID -> DD_MLP_NHID -> DD_MLP_NHID ->
+ * DD_MLP_NOUT, SiLU on the hidden layers, linear output; BF16 weights and
+ * activations, FP32 accumulation (tensor cores). Parameters are one flat float
+ * vector of DD_MLP_NPARAMS: W_1 (NHID x NIN, row-major, row n = the weights into
+ * output n), b_1, W_2, b_2, W_3, b_3, W_4 (NOUT x NHID), b_4.
+ *
+ * Inputs (per cell, BF16): mu on the 8 x 8 block / its mean - 1 (64), nu_J
+ * resampled to 16 x 16 by exact area overlap / its mean - 1 (256), and 16
+ * scalars of the cell's change of gauge. Outputs: r on the block (64, base-2
+ * units, mu-weighted mean zero) and an auxiliary Y-side log dual on 16 x 16
+ * sample pixels of the box (256, trained, not used by the solver).
+ * ---------------------------------------------------------------------- */
+#define DD_MLP_NIN 336
+#define DD_MLP_NHID 256
+#define DD_MLP_NOUT 320
+#define DD_MLP_NPARAMS 300096
+
+typedef struct dd_mlp dd_mlp;
+
+/* A network (parameters zero) with buffers for batches of up to max_batch
+ * rows; its work is ordered on `stream`. Errors: DD_ERR_ARG, DD_ERR_OOM. */
+int dd_mlp_create(int32_t max_batch, void* stream, dd_mlp** out);
+
+/* Parameters from / to HOST memory (n = DD_MLP_NPARAMS floats). Setting them
+ * resets the optimiser state. Both synchronise the network's stream. */
+int dd_mlp_set_params(dd_mlp* m, const float* params, int64_t n);
+int dd_mlp_get_params(dd_mlp* m, float* params, int64_t n);
+
+/* Forward pass of M <= max_batch rows: x_dev (M x NIN BF16, DEVICE) -> y_dev
+ * (M x NOUT float, DEVICE). Asynchronous. */
+int dd_mlp_forward(dd_mlp* m, const uint16_t* x_dev, int32_t M, float* y_dev);
+
+/* Loss L = (1/M) sum_rows sum_j w_j (y_j - t_j)^2 of M rows and its gradient:
+ * x_dev (M x NIN BF16), t_dev (M x NOUT float), w_dev (NOUT float), all DEVICE;
+ * *loss (may be NULL) and grad_host (DD_MLP_NPARAMS floats, HOST, may be NULL).
+ * Synchronises. */
+int dd_mlp_loss_grad(dd_mlp* m, const uint16_t* x_dev, const float* t_dev, const float* w_dev, int32_t M,
+                     double* loss, float* grad_host);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8, learning rate lr) on the batch of
+ * rows idx_dev[0..B) (DEVICE int32) of the data set x_all (rows x NIN BF16) /
+ * t_all (rows x NOUT float), loss weights w_dev; all DEVICE. If loss is not NULL
+ * it receives the batch loss before the step (and the call synchronises);
+ * otherwise the step is only enqueued. */
+int dd_mlp_train_step(dd_mlp* m, const uint16_t* x_all, const float* t_all, const int32_t* idx_dev, int32_t B,
+                      const float* w_dev, float lr, double* loss);
+
+void dd_mlp_destroy(dd_mlp* m);
+
+/* Give the context the warm-start network's parameters (HOST, DD_MLP_NPARAMS
+ * floats; weights are used in BF16, biases in FP32). Needed before dd_iterate
+ * with DD_WARM_MLP (DD_ERR_STATE otherwise). Requires cell_size 4. */
+int dd_set_warmstart_weights(dd_ctx* ctx, const float* params, int64_t n);
+
+/* With DD_FLAG_COLLECT: the network inputs (rows x NIN BF16) and targets (rows x
+ * NOUT float) of the last half-iteration on `part`, one row per composite cell
+ * with a full 8 x 8 block, in cell order, into DEVICE buffers of max_rows rows.
+ * *rows receives the row count; with feat_dev NULL only the count is stored.
+ * DD_ERR_STATE if the last half-iteration was not on `part`. */
+int dd_collect_cells(dd_ctx* ctx, int part, uint16_t* feat_dev, float* targ_dev, int32_t max_rows, int32_t* rows);
 
 /* Release every resource of the context (NULL is ignored). */
 void dd_destroy(dd_ctx* ctx);

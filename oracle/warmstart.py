@@ -15,26 +15,32 @@ coordinates v of nu_J,
 With ub = u - uc and vb = v - vc the cell's cost in that gauge is
   K(u, v) = k2 sum_k l_k (ub_k - vb_k / l_k)^2.
 
+Affine dual. With S and T the 2 x 2 covariances of mu_J and nu_J (pixels), the
+map x -> m_nu + A (x - m_mu) with the symmetric positive semidefinite
+  A = S^(-1/2) (S^(1/2) T S^(1/2))^(1/2) S^(-1/2)
+is the optimal (unregularised) transport between Gaussians of those moments,
+and its Kantorovich dual for the cost |x - y|^2 is, in base-2 units,
+  base(u) = k2 (ub' (I - A) ub + 2 d.ub).
+(When det S <= 1e-6 the per-axis map A = diag(l) stands in.)
+
 Features (336 values):
-  [0, 64)     mu_J on the 8 x 8 block, divided by its mean, minus 1;
+  [0, 64)     log2(mu_J / its mean) / 4 on the 8 x 8 block;
   [64, 320)   nu_J resampled to 16 x 16 by exact area overlap (output row i
               covers [i h / 16, (i + 1) h / 16) of the box rows, likewise the
-              columns), divided by its mean, minus 1;
+              columns): log2(value / mean + 1/256) / 4;
   [320, 336)  h/32, w/32, d_1/8, d_2/8, log2 l_1, log2 l_2, (uc_1 - 3.5)/4,
               (uc_2 - 3.5)/4, (vc_1 + 0.5)/h - 0.5, (vc_2 + 0.5)/w - 0.5, log2 k2,
-              sqrt(Var_mu,1)/4, sqrt(Var_mu,2)/4, sqrt(Var_nu,1)/16,
-              sqrt(Var_nu,2)/16, 0.
+              sqrt(S_11)/4, sqrt(S_22)/4, sqrt(T_11)/16, sqrt(T_22)/16,
+              T_12 / sqrt(T_11 T_22) (0 if either is 0).
 
 Targets (320 values), from the converged dual alpha of the cell:
-  [0, 64)     r(u) = alpha(u) / (eps ln 2) - 2 k2 d.ub - k2 sum_k (1 - l_k) ub_k^2,
-              shifted to a mu-weighted mean of zero (duals are defined up to a
-              constant). The subtracted part is the exact dual of the cell
-              when nu_J is mu_J translated by -d and stretched by l (unregularised
-              transport); r is what remains. The solver starts from
-              alpha_init = eps ln 2 (2 k2 d.ub + k2 sum (1 - l_k) ub_k^2 + r_pred).
+  [0, 64)     r(u) = alpha(u) / (eps ln 2) - base(u), shifted to a mu-weighted
+              mean of zero (duals are defined up to a constant). The solver
+              starts from alpha_init = eps ln 2 (base + r_pred).
   [64, 320)   an auxiliary output, trained but not used by the solver: the
-              Y-side log dual in the same gauge,
-                G(v) = -log2 sum_u 2^(log2 mu(u) + r(u) - K(u, v)),
+              Y-side log dual of the cell's dual a(u) = log2 mu(u) + q(u) + r(u)
+              in the gauge, q(u) = k2 ub' (diag(l) - A) ub,
+                G(v) = -log2 sum_u 2^(a(u) - K(u, v)),
               at the 16 x 16 box pixels v_p = (((2i + 1) h) div 32,
               ((2j + 1) w) div 32), shifted to a plain mean of zero.
 """
@@ -42,6 +48,7 @@ Targets (320 values), from the converged dual alpha of the cell:
 from __future__ import annotations
 
 import numpy as np
+from scipy.linalg import sqrtm
 
 LN2 = np.log(2.0)
 NF, NT = 336, 320
@@ -60,7 +67,7 @@ def block_of(geom, members):
 
 
 def cell_gauge(mu_blk, r0, c0, nu_arr, o1, o2):
-    """uc, vc, variances, l, d of the change of gauge (module docstring)."""
+    """uc, vc, variances, covariances S and T, l, d and the map A (module docstring)."""
     hx, wx = mu_blk.shape
     h, w = nu_arr.shape
     mx = mu_blk.sum()
@@ -73,9 +80,20 @@ def cell_gauge(mu_blk, r0, c0, nu_arr, o1, o2):
     vc = np.array([(nu_arr * v1).sum() / my, (nu_arr * v2).sum() / my])
     vu = np.maximum(np.array([(mu_blk * u1 * u1).sum() / mx, (mu_blk * u2 * u2).sum() / mx]) - uc * uc, 0.0)
     vv = np.maximum(np.array([(nu_arr * v1 * v1).sum() / my, (nu_arr * v2 * v2).sum() / my]) - vc * vc, 0.0)
+    cu = (mu_blk * u1 * u2).sum() / mx - uc[0] * uc[1]
+    cv = (nu_arr * v1 * v2).sum() / my - vc[0] * vc[1]
     lam = np.where(vu > 1e-3, np.clip(np.sqrt(vv / np.where(vu > 0, vu, 1.0)), 0.125, 8.0), 1.0)
     d = np.array([r0 - o1, c0 - o2], dtype=np.float64) + uc - vc
-    return dict(uc=uc, vc=vc, vu=vu, vv=vv, l=lam, d=d)
+    S = np.array([[vu[0], cu], [cu, vu[1]]])
+    T = np.array([[vv[0], cv], [cv, vv[1]]])
+    if np.linalg.det(S) > 1e-6:
+        Sh = np.real(sqrtm(S))
+        Shi = np.linalg.inv(Sh)
+        A = Shi @ np.real(sqrtm(Sh @ T @ Sh)) @ Shi
+        A = 0.5 * (A + A.T)
+    else:
+        A = np.diag(lam)
+    return dict(uc=uc, vc=vc, vu=vu, vv=vv, S=S, T=T, l=lam, d=d, A=A)
 
 
 def overlap_matrix(n: int, m: int = 16) -> np.ndarray:
@@ -97,13 +115,15 @@ def cell_features(mu_blk, r0, c0, nu_arr, o1, o2, k2) -> np.ndarray:
     g = cell_gauge(mu_blk, r0, c0, nu_arr, o1, o2)
     h, w = nu_arr.shape
     f = np.zeros(NF)
-    f[:64] = (mu_blk / mu_blk.mean()).reshape(-1) - 1.0
+    f[:64] = np.log2(mu_blk / mu_blk.mean()).reshape(-1) / 4
     rs = resample16(nu_arr)
-    f[64:320] = (rs / rs.mean()).reshape(-1) - 1.0
+    f[64:320] = np.log2(rs / rs.mean() + 1.0 / 256).reshape(-1) / 4
+    T = g["T"]
+    rho = T[0, 1] / np.sqrt(T[0, 0] * T[1, 1]) if T[0, 0] > 0 and T[1, 1] > 0 else 0.0
     f[320:336] = [h / 32, w / 32, g["d"][0] / 8, g["d"][1] / 8, np.log2(g["l"][0]), np.log2(g["l"][1]),
                   (g["uc"][0] - 3.5) / 4, (g["uc"][1] - 3.5) / 4, (g["vc"][0] + 0.5) / h - 0.5,
                   (g["vc"][1] + 0.5) / w - 0.5, np.log2(k2), np.sqrt(g["vu"][0]) / 4, np.sqrt(g["vu"][1]) / 4,
-                  np.sqrt(g["vv"][0]) / 16, np.sqrt(g["vv"][1]) / 16, 0.0]
+                  np.sqrt(g["vv"][0]) / 16, np.sqrt(g["vv"][1]) / 16, rho]
     return f
 
 
@@ -113,12 +133,20 @@ def _ub(g, hx, wx):
     return ub1, ub2
 
 
-def alpha_target(alpha_blk, mu_blk, eps, k2, g) -> np.ndarray:
-    """r on the block (row-major, 64 values), mu-weighted mean zero."""
+def _quad(M, ub1, ub2):
+    return M[0, 0] * ub1 ** 2 + 2 * M[0, 1] * ub1 * ub2 + M[1, 1] * ub2 ** 2
+
+
+def affine_dual(mu_blk, k2, g) -> np.ndarray:
+    """base(u) = k2 (ub' (I - A) ub + 2 d.ub) on the block."""
     hx, wx = mu_blk.shape
     ub1, ub2 = _ub(g, hx, wx)
-    r = (alpha_blk / (eps * LN2) - 2.0 * k2 * (g["d"][0] * ub1 + g["d"][1] * ub2)
-         - k2 * ((1.0 - g["l"][0]) * ub1 ** 2 + (1.0 - g["l"][1]) * ub2 ** 2))
+    return k2 * (_quad(np.eye(2) - g["A"], ub1, ub2) + 2.0 * (g["d"][0] * ub1 + g["d"][1] * ub2))
+
+
+def alpha_target(alpha_blk, mu_blk, eps, k2, g) -> np.ndarray:
+    """r on the block (row-major, 64 values), mu-weighted mean zero."""
+    r = alpha_blk / (eps * LN2) - affine_dual(mu_blk, k2, g)
     r = r - (mu_blk * r).sum() / mu_blk.sum()
     return r.reshape(-1)
 
@@ -127,10 +155,7 @@ def alpha_from_prediction(r_pred, mu_blk, eps, k2, g) -> np.ndarray:
     """The warm start the solver builds from a predicted r (inverse of alpha_target
     up to the free constant)."""
     hx, wx = mu_blk.shape
-    ub1, ub2 = _ub(g, hx, wx)
-    base = 2.0 * k2 * (g["d"][0] * ub1 + g["d"][1] * ub2) + k2 * ((1.0 - g["l"][0]) * ub1 ** 2
-                                                                  + (1.0 - g["l"][1]) * ub2 ** 2)
-    return eps * LN2 * (base + np.asarray(r_pred).reshape(hx, wx))
+    return eps * LN2 * (affine_dual(mu_blk, k2, g) + np.asarray(r_pred).reshape(hx, wx))
 
 
 def sample_pixels(h, w):
@@ -142,7 +167,8 @@ def beta_aux_target(r, mu_blk, h, w, k2, g) -> np.ndarray:
     """G at the 16 x 16 sample pixels (row-major, 256 values), plain mean zero."""
     hx, wx = mu_blk.shape
     ub1, ub2 = _ub(g, hx, wx)
-    a = (np.log2(mu_blk) + np.asarray(r).reshape(hx, wx)).reshape(-1)
+    q = k2 * _quad(np.diag(g["l"]) - g["A"], ub1, ub2)
+    a = (np.log2(mu_blk) + q + np.asarray(r).reshape(hx, wx)).reshape(-1)
     p1, p2 = sample_pixels(h, w)
     out = np.zeros((16, 16))
     for i in range(16):

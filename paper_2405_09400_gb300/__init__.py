@@ -24,14 +24,17 @@ LIB_PATH = os.path.join(_PKG, "lib", "libddflow.so")
 DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_MAXITER = 0, -1, -2, -3, -4
 DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
-DD_WARM_PREV, DD_WARM_COLD = 0, 1
-DD_FLAG_KEEP_PREBALANCE = 1
+DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
+DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT = 1, 2
+DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 
 EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
+    "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
+    "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells",
 ]
 
 
@@ -110,6 +113,15 @@ def load():
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
+        "dd_mlp_create": (C.c_int, [C.c_int32, vp, P(vp)]),
+        "dd_mlp_set_params": (C.c_int, [vp, P(C.c_float), C.c_int64]),
+        "dd_mlp_get_params": (C.c_int, [vp, P(C.c_float), C.c_int64]),
+        "dd_mlp_forward": (C.c_int, [vp, vp, C.c_int32, vp]),
+        "dd_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, C.c_int32, _f64p, P(C.c_float)]),
+        "dd_mlp_train_step": (C.c_int, [vp, vp, vp, vp, C.c_int32, vp, C.c_float, _f64p]),
+        "dd_mlp_destroy": (None, [vp]),
+        "dd_set_warmstart_weights": (C.c_int, [vp, P(C.c_float), C.c_int64]),
+        "dd_collect_cells": (C.c_int, [vp, C.c_int, vp, vp, C.c_int32, _i32p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -318,6 +330,90 @@ def dd_destroy(ctx):
         load().dd_destroy(ctx)
 
 
+def _dptr(t):
+    """Device address of a CUDA tensor (None stays None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _params32(params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != DD_MLP_NPARAMS:
+        raise ValueError(f"expected {DD_MLP_NPARAMS} parameters, got {p.size}")
+    return p
+
+
+def dd_set_warmstart_weights(ctx, params):
+    p = _params32(params)
+    _check(load().dd_set_warmstart_weights(ctx, _ptr(p, P(C.c_float)), p.size), "dd_set_warmstart_weights")
+
+
+def dd_collect_cells(ctx, part):
+    """Network inputs (rows x NIN, torch.bfloat16) and targets (rows x NOUT,
+    torch.float32) of the last half-iteration on `part`, on the device."""
+    import torch
+
+    rows = C.c_int32()
+    lib = load()
+    _check(lib.dd_collect_cells(ctx, int(part), None, None, 0, C.byref(rows)), "dd_collect_cells")
+    n = rows.value
+    feat = torch.empty((n, DD_MLP_NIN), dtype=torch.bfloat16, device="cuda")
+    targ = torch.empty((n, DD_MLP_NOUT), dtype=torch.float32, device="cuda")
+    if n:
+        _check(lib.dd_collect_cells(ctx, int(part), _dptr(feat), _dptr(targ), n, C.byref(rows)), "dd_collect_cells")
+    return feat, targ
+
+
+class MLP:
+    """The warm-start network on the GPU (dd_mlp_*): parameters, forward pass,
+    loss gradient and Adam steps. Tensors are torch CUDA tensors."""
+
+    def __init__(self, max_batch, stream=None):
+        self.max_batch = int(max_batch)
+        self.h = C.c_void_p()
+        _check(load().dd_mlp_create(self.max_batch, stream if stream is not None else current_stream(),
+                                    C.byref(self.h)), "dd_mlp_create")
+
+    def set_params(self, params):
+        p = _params32(params)
+        _check(load().dd_mlp_set_params(self.h, _ptr(p, P(C.c_float)), p.size), "dd_mlp_set_params")
+
+    def get_params(self):
+        p = np.zeros(DD_MLP_NPARAMS, dtype=np.float32)
+        _check(load().dd_mlp_get_params(self.h, _ptr(p, P(C.c_float)), p.size), "dd_mlp_get_params")
+        return p
+
+    def forward(self, x):
+        import torch
+
+        y = torch.empty((x.shape[0], DD_MLP_NOUT), dtype=torch.float32, device=x.device)
+        _check(load().dd_mlp_forward(self.h, _dptr(x), int(x.shape[0]), _dptr(y)), "dd_mlp_forward")
+        return y
+
+    def loss_grad(self, x, t, w):
+        loss = C.c_double()
+        g = np.zeros(DD_MLP_NPARAMS, dtype=np.float32)
+        _check(load().dd_mlp_loss_grad(self.h, _dptr(x), _dptr(t), _dptr(w), int(x.shape[0]), C.byref(loss),
+                                       _ptr(g, P(C.c_float))), "dd_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x_all, t_all, idx, w, lr, want_loss=False):
+        loss = C.c_double()
+        _check(load().dd_mlp_train_step(self.h, _dptr(x_all), _dptr(t_all), _dptr(idx), int(idx.shape[0]), _dptr(w),
+                                        float(lr), C.byref(loss) if want_loss else None), "dd_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if self.h:
+            load().dd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- convenience wrapper -----------------------------------------------------
 def boxes_to_arrays(boxes):
     """[(o1, o2, array), ...] -> (hdr (n, 4) int32, packed float64 data)."""
@@ -338,7 +434,7 @@ def arrays_to_boxes(hdr, data):
 class DomDec:
     """One library context: DD half-iterations and flow updates on a grid problem."""
 
-    def __init__(self, mu, nu, eps, cell_size, boxes=None, h=None, stream=None, **opts):
+    def __init__(self, mu, nu, eps, cell_size, boxes=None, h=None, stream=None, weights=None, **opts):
         mu = np.asarray(mu, dtype=np.float64)
         self.shape = mu.shape
         self.s = int(cell_size)
@@ -351,6 +447,8 @@ class DomDec:
         self.ncell = [len(dd_get_partition(self.ctx, p)) for p in (0, 1)]
         if boxes is not None:
             self.set_plan(boxes)
+        if weights is not None:
+            self.set_warmstart_weights(weights)
 
     def set_plan(self, boxes):
         hdr, data = boxes if isinstance(boxes, tuple) else boxes_to_arrays(boxes)
@@ -398,6 +496,12 @@ class DomDec:
 
     def counters(self):
         return dd_get_counters(self.ctx)
+
+    def set_warmstart_weights(self, params):
+        dd_set_warmstart_weights(self.ctx, params)
+
+    def collect(self, part):
+        return dd_collect_cells(self.ctx, part)
 
     def close(self):
         if self.ctx:

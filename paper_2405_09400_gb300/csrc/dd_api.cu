@@ -166,6 +166,30 @@ int choose_threads(dd_ctx* c, long long maxarea) {
     return maxarea <= 1024 ? 128 : 256;
 }
 
+// per-cell buffers of the learned warm start, and the list of cells with a full
+// 8 x 8 X block per partition (the rows dd_collect_cells returns)
+int ensure_learned_buffers(dd_ctx* c) {
+    if (c->d_feat) return DD_OK;
+    const size_t mc = (size_t)std::max(c->part[0].ncell, c->part[1].ncell);
+    RET(dmalloc(&c->d_feat, mc * DD_MLP_NIN));
+    RET(dmalloc(&c->d_pred, mc * DD_MLP_NOUT));
+    RET(dmalloc(&c->d_targ, mc * DD_MLP_NOUT));
+    CK(cudaMemsetAsync(c->d_feat, 0, mc * DD_MLP_NIN * sizeof(uint16_t), c->stream));
+    CK(cudaMemsetAsync(c->d_pred, 0, mc * DD_MLP_NOUT * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_targ, 0, mc * DD_MLP_NOUT * sizeof(float), c->stream));
+    for (int p = 0; p < 2; ++p) {
+        const DevPart& P = c->part[p];
+        std::vector<int32_t> full;
+        for (int J = 0; J < P.ncell; ++J)
+            if (P.h_xblk[XB_N * J + XB_HX] * P.h_xblk[XB_N * J + XB_WX] == 64) full.push_back(J);
+        c->n_full[p] = (int)full.size();
+        RET(dmalloc(&c->d_full[p], std::max<size_t>(1, full.size())));
+        if (!full.empty()) RET(h2d(c->d_full[p], full.data(), full.size(), c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -217,6 +241,8 @@ void dd_destroy(dd_ctx* c) {
     }
     dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
     dfree(c->d_gscr); dfree(c->d_goff);
+    dfree(c->d_feat); dfree(c->d_pred); dfree(c->d_targ); dfree(c->d_full[0]); dfree(c->d_full[1]);
+    if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
     if (c->h_tot) cudaFreeHost(c->h_tot);
     if (c->h_cbar) cudaFreeHost(c->h_cbar);
@@ -253,8 +279,10 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     dd_ctx* c = new (std::nothrow) dd_ctx();
     if (!c) return DD_ERR_OOM;
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
+    const bool learned = c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT);
     if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
-        (c->opt.omega >= 0.0 && c->opt.omega < 1.0)) {
+        (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
+        (learned && s != 4)) {
         delete c;
         return DD_ERR_ARG;
     }
@@ -363,6 +391,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             TRY(dmalloc(&P.Ecell, P.ncell));
             TRY(dmalloc(&c->bhdr[p], (size_t)BH_N * c->nb));
         }
+        if (learned) TRY(ensure_learned_buffers(c));
         TRY(dmalloc(&c->d_bmom, (size_t)BM_N * c->nb));
         TRY(dmalloc(&c->d_tot, PT_N));
         if (cudaMallocHost((void**)&c->h_tot, sizeof(long long) * PT_N) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
@@ -480,9 +509,19 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
     if (part == -1) part = c->last_part == 0 ? 1 : 0;
     DevPart& P = c->part[part];
+    if (c->opt.warm == DD_WARM_MLP && !c->mlp_ready) return DD_ERR_STATE;
     CK(cudaEventRecord(c->ev[0], c->stream));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
+    if (c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT)) {
+        // network inputs from the union boxes; the prediction initialises the solves
+        RET(launch_feat(c, part));
+        c->n_launch += 1;
+        if (c->opt.warm == DD_WARM_MLP) {
+            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
+            c->n_launch += 4;
+        }
+    }
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const long long comp = c->h_tot[PT_COMP], outn = c->h_tot[PT_OUT];
@@ -953,6 +992,28 @@ int dd_get_prebalance(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
             for (int q = 0; q < x[CH_W]; ++q) data[k++] = buf[base + (size_t)r * x[CH_STRIDE] + q];
     }
     *count = n;
+    return DD_OK;
+}
+
+int dd_set_warmstart_weights(dd_ctx* c, const float* params, int64_t n) {
+    if (!c || !params || n != DD_MLP_NPARAMS || c->s != 4) return DD_ERR_ARG;
+    RET(ensure_learned_buffers(c));
+    if (!c->mlp) RET(dd_mlp_create(std::max(c->part[0].ncell, c->part[1].ncell), c->stream, &c->mlp));
+    RET(dd_mlp_set_params(c->mlp, params, n));
+    c->mlp_ready = true;
+    return DD_OK;
+}
+
+int dd_collect_cells(dd_ctx* c, int part, uint16_t* feat_dev, float* targ_dev, int32_t max_rows, int32_t* rows) {
+    if (!c || !rows || part < 0 || part > 1) return DD_ERR_ARG;
+    if (!(c->opt.flags & DD_FLAG_COLLECT) || c->last_part != part || !c->part[part].solved) return DD_ERR_STATE;
+    const int n = c->n_full[part];
+    *rows = n;
+    if (!feat_dev) return DD_OK;
+    if (!targ_dev || max_rows < n) return DD_ERR_ARG;
+    RET(launch_collect(c, n, c->d_full[part], feat_dev, targ_dev));
+    c->n_launch += 1;
+    CK(cudaStreamSynchronize(c->stream));
     return DD_OK;
 }
 

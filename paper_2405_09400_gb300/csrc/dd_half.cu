@@ -31,6 +31,7 @@
 //   beta_t/eps = ln2 (b - 2 k2 d.vbar + k2|d|^2/2) - ln nu_J,
 // with d = (block centre) - (box centre) in pixels (the linear part of the cost
 // is absorbed so that the FP32 duals stay small).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -225,6 +226,10 @@ struct HalfArgs {
     float* gscratch;        // box arrays of cells too large for shared memory
     const long long* goff;  // per cell: offset in gscratch, or -1 (shared memory)
     int smaxA, smaxH, smaxW;  // shared-memory capacities
+    // learned / analytic warm start (cells with a full 2s x 2s block only)
+    int affine;         // start from the cell's affine dual (a = log2 mu in the gauge)
+    const float* pred;  // ncell x DD_MLP_NOUT network outputs (first 64: predicted r), or null
+    float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
 };
 
 // shared-memory layout (floats unless noted); BS = padw(max box width)
@@ -290,6 +295,91 @@ __device__ __forceinline__ float lse2(int n, F term) {
 // neither over- nor underflows: then no significant term was flushed to zero
 __device__ __forceinline__ bool shift_ok(float s) { return s >= 8.67e-19f && s <= 1.15e18f; }  // 2^-60 .. 2^60
 
+constexpr int kMlpBlock = 64;  // X block of a full composite cell (8 x 8 pixels)
+
+// Square root of a symmetric positive semidefinite 2 x 2 matrix [[a, b], [b, c]]:
+// (M + sqrt(det M) I) / sqrt(tr M + 2 sqrt(det M)).
+__device__ void sqrtm2(double a, double b, double c, double& ra, double& rb, double& rc) {
+    const double s = sqrt(fmax(a * c - b * b, 0.0));
+    const double t = sqrt(fmax(a + c + 2.0 * s, 0.0));
+    if (!(t > 0.0)) { ra = rb = rc = 0.0; return; }
+    ra = (a + s) / t; rb = b / t; rc = (c + s) / t;
+}
+
+// The cell's affine dual beyond the gauge. With S, T the covariances of mu_J and
+// nu_J, A = S^(-1/2) (S^(1/2) T S^(1/2))^(1/2) S^(-1/2) is the transport map
+// between Gaussians of those moments; its dual minus the gauge's per-axis part
+// is q(u) = k2 ub' (diag(l) - A) ub, returned as (l1 - A11, -A12, l2 - A22).
+// When det S <= 1e-6 the per-axis map stands in (q = 0).
+__device__ void affine_excess(double s11, double s12, double s22, double t11, double t12, double t22, double l1,
+                              double l2, float& q11, float& q12, float& q22) {
+    q11 = q12 = q22 = 0.f;
+    if (!(s11 * s22 - s12 * s12 > 1e-6)) return;
+    double h11, h12, h22;
+    sqrtm2(s11, s12, s22, h11, h12, h22);
+    const double dh = h11 * h22 - h12 * h12;
+    const double i11 = h22 / dh, i12 = -h12 / dh, i22 = h11 / dh;
+    // M = Sh T Sh
+    const double p11 = h11 * t11 + h12 * t12, p12 = h11 * t12 + h12 * t22;
+    const double p21 = h12 * t11 + h22 * t12, p22 = h12 * t12 + h22 * t22;
+    const double m11 = p11 * h11 + p12 * h12, m12 = p11 * h12 + p12 * h22, m22 = p21 * h12 + p22 * h22;
+    double r11, r12, r22;
+    sqrtm2(m11, m12, m22, r11, r12, r22);
+    // A = Shi R Shi
+    const double e11 = i11 * r11 + i12 * r12, e12 = i11 * r12 + i12 * r22;
+    const double e21 = i12 * r11 + i22 * r12, e22 = i12 * r12 + i22 * r22;
+    const double a11 = e11 * i11 + e12 * i12, a22 = e21 * i12 + e22 * i22;
+    const double a12 = 0.5 * ((e11 * i12 + e12 * i22) + (e21 * i11 + e22 * i12));
+    q11 = (float)(l1 - a11);
+    q12 = (float)(-a12);
+    q22 = (float)(l2 - a22);
+}
+
+// Training targets of the warm-start network for one solved cell: the dual
+// relative to the cell's affine dual, r(u) = a(u) - log2 mu(u) - q(u) in the
+// gauge (q: see affine_excess), with a mu-weighted mean of zero, and the
+// auxiliary Y-side log dual
+//   G(v) = -LSE2_u [a(u) - K(u, v)]
+// at the 16 x 16 sample pixels v = ((2i+1) h div 32, (2j+1) w div 32), with a
+// plain mean of zero. K = table + B (the tables hold K - B).
+__device__ __noinline__ void write_targets(const HalfArgs& A, const Smem& S, int J, const float* aC, int h, int w,
+                                           int bs, int hx, int wx, double musum, float uc1, float uc2, float q11,
+                                           float q12, float q22) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    float* tg = A.targ + (long long)DD_MLP_NOUT * J;
+    auto rr = [&](int u) {
+        const int u1 = u / wx, u2 = u - u1 * wx;
+        const float ub1 = u1 - uc1, ub2 = u2 - uc2;
+        return aC[u] - S.lgm[u] - A.k2 * (q11 * ub1 * ub1 + 2.f * q12 * ub1 * ub2 + q22 * ub2 * ub2);
+    };
+    double cm[1] = {0.0};
+    for (int u = tid; u < hx * wx; u += NT)
+        if (S.lgm[u] > 0.5f * DD_NEG) cm[0] += S.mux[u] * (double)rr(u);
+    block_sum_d<1>(cm, S.red);
+    const float sh = (float)(cm[0] / musum);
+    for (int u = tid; u < hx * wx; u += NT) tg[u] = S.lgm[u] > 0.5f * DD_NEG ? rr(u) - sh : 0.f;
+    double gs[1] = {0.0};
+    for (int p = tid; p < 256; p += NT) {
+        const int v1 = ((2 * (p >> 4) + 1) * h) / 32, v2 = ((2 * (p & 15) + 1) * w) / 32;
+        auto term = [&](int u) {
+            const int u1 = u / wx, u2 = u - u1 * wx;
+            return aC[u] - S.tab1[u1 * h + v1] - S.tab2[u2 * bs + v2];
+        };
+        float m = DD_NEG;
+        for (int u = 0; u < hx * wx; ++u)
+            if (S.lgm[u] > 0.5f * DD_NEG) m = fmaxf(m, term(u));
+        float sacc = 0.f;
+        for (int u = 0; u < hx * wx; ++u)
+            if (S.lgm[u] > 0.5f * DD_NEG) sacc += ex2f(term(u) - m);
+        const float G = -(m + lg2f(sacc)) + (float)(S.B1[v1] + S.B2[v2]);
+        tg[64 + p] = G;
+        gs[0] += G;
+    }
+    block_sum_d<1>(gs, S.red);
+    const float gm = (float)(gs[0] / 256.0);
+    for (int p = tid; p < 256; p += NT) tg[64 + p] -= gm;
+}
+
 template <int NTB>
 __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -344,7 +434,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // ---- 1. gather nu_J ---------------------------------------------------
         // per-thread partial sums in FP32 (a few entries each), block sum in FP64;
         // they only choose the change of gauge, which is exact for any value
-        float gf[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float gf[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int v = tid; v < h * bs; v += NT) {
             const int v1 = v / bs, v2 = v - v1 * bs;
             float lg = DD_NEG;
@@ -363,6 +453,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 if (acc > 0.f) lg = lg2f(acc);
                 const float f1 = (float)v1, f2 = (float)v2;
                 gf[0] += acc; gf[1] += acc * f1; gf[2] += acc * f2; gf[3] += acc * f1 * f1; gf[4] += acc * f2 * f2;
+                gf[10] += acc * f1 * f2;
             }
             lgnu_p[v] = lg;
             b_p[v] = DD_NEG;
@@ -373,11 +464,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             const float mux = (float)A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
             const float f1 = (float)u1, f2 = (float)u2;
             gf[5] += mux; gf[6] += mux * f1; gf[7] += mux * f2; gf[8] += mux * f1 * f1; gf[9] += mux * f2 * f2;
+            gf[11] += mux * f1 * f2;
         }
-        double gm[10];
+        double gm[12];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) gm[k] = gf[k];
-        block_sum_d<10>(gm, S.red);
+        for (int k = 0; k < 12; ++k) gm[k] = gf[k];
+        block_sum_d<12>(gm, S.red);
         // Reparametrisation (exact for any choice): origins at the barycentres of
         // mu_J and nu_J, the linear part of the cost absorbed through d, and a
         // per-axis stretch l_k absorbed so that the kernel
@@ -390,6 +482,11 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const float l1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
         const float l2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
         const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
+        // the affine start (and the learned one) use the full 2 x 2 map
+        float q11 = 0.f, q12 = 0.f, q22 = 0.f;
+        if (A.affine || A.targ)
+            affine_excess(vu1, gm[11] / gm[5] - (double)uc1 * uc2, vu2, vv1, gm[10] / gm[0] - (double)vc1 * vc2, vv2,
+                          l1, l2, q11, q12, q22);
         // Kernel tables. With t = vbar / l_k, the axis kernel is
         //   K_k(u, v) = k2 l_k (ubar - t)^2,
         // its minimum over the block's grid points is B_k(v) = k2 l_k (ubar* - t)^2
@@ -430,6 +527,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const float* ap = A.alpha + (long long)A.amax * J;
         const float* pg = A.gauge + 8 * J;
         const float pd1 = pg[0], pd2 = pg[1], pl1 = pg[2], pl2 = pg[3];
+        // network prediction r of the dual relative to the cell's affine dual
+        const float* pr = (A.pred && nx == kMlpBlock) ? A.pred + (long long)DD_MLP_NOUT * J : nullptr;
         for (int u = tid; u < nx; u += NT) {
             const int u1 = u / wx, u2 = u - u1 * wx;
             const int x = (r0 + u1) * A.N2 + (c0 + u2);
@@ -439,7 +538,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             S.lgm[u] = lg;
             const float ub1 = u1 - uc1, ub2 = u2 - uc2;
             float a0;
-            if (A.warm)
+            const float qa = A.k2 * (q11 * ub1 * ub1 + 2.f * q12 * ub1 * ub2 + q22 * ub2 * ub2);
+            if (pr)
+                a0 = lg + qa + pr[u];
+            else if (A.affine)
+                a0 = lg + qa;
+            else if (A.warm)
                 a0 = ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2) +
                      A.k2 * ((l1 - pl1) * ub1 * ub1 + (l2 - pl2) * ub2 * ub2);
             else
@@ -668,6 +772,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         }
         __syncthreads();  // every thread has read the error partials in S.red
         if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[stalled ? 3 : 0], 1);
+        if (A.targ && nx == kMlpBlock) write_targets(A, S, J, aC, h, w, bs, hx, wx, gm[5], uc1, uc2, q11, q12, q22);
 
         // ---- outputs of the solve: duals, objective --------------------------
         float* apo = A.alpha + (long long)A.amax * J;
@@ -726,6 +831,100 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         }
 
     }
+}
+
+// Input features of the warm-start network for every cell with a full 8 x 8
+// X block (one CTA per cell, before the solve), in BF16, DD_MLP_NIN per cell:
+//   [0, 64)    log2(mu on the block / its mean) / 4,
+//   [64, 320)  nu_J resampled to 16 x 16 by exact area overlap (output row i
+//              covers box rows [i h / 16, (i + 1) h / 16), likewise columns):
+//              log2(value / mean + 1/256) / 4,
+//   [320, 336) scalars of the cell's change of gauge (box extent, barycentre
+//              offset d, stretch l, barycentres, log2 k2, spreads, the
+//              correlation of nu_J).
+// nu_J is gathered from the member boxes as in BasicToComposite.
+__global__ void __launch_bounds__(128) k_feat(HalfArgs A, __nv_bfloat16* __restrict__ feat) {
+    __shared__ float rs[256];
+    __shared__ double red[32 * 12 + 12];
+    const int J = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    const int32_t* xb = A.xblk + XB_N * J;
+    const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX];
+    if (hx * wx != kMlpBlock) return;
+    const int32_t* ch = A.chdr + CH_N * J;
+    const int o1 = ch[CH_O1], o2 = ch[CH_O2], h = ch[CH_H], w = ch[CH_W];
+    for (int k = tid; k < 256; k += NT) rs[k] = 0.f;
+    int32_t mem[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
+    __syncthreads();
+    double g[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g[k] = 0.0;
+    for (int v = tid; v < h * w; v += NT) {
+        const int v1 = v / w, v2 = v - v1 * w;
+        const int y1 = o1 + v1, y2 = o2 + v2;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (mem[k] < 0) continue;
+            const int32_t* bh = A.bhdr_in + BH_N * mem[k];
+            const int p1 = y1 - bh[BH_O1], p2 = y2 - bh[BH_O2];
+            if (p1 >= 0 && p1 < bh[BH_H] && p2 >= 0 && p2 < bh[BH_W])
+                acc += A.pool_in[(long long)bh[BH_START] + (long long)p1 * bh[BH_STRIDE] + p2];
+        }
+        if (!(acc > 0.f)) continue;
+        const double a = acc;
+        g[0] += a; g[1] += a * v1; g[2] += a * v2; g[3] += a * v1 * v1; g[4] += a * v2 * v2; g[10] += a * v1 * v2;
+        // output rows / columns overlapping this pixel, and the overlap lengths
+        const int i0 = (16 * v1) / h, i1 = (16 * (v1 + 1) - 1) / h;
+        const int j0 = (16 * v2) / w, j1 = (16 * (v2 + 1) - 1) / w;
+        for (int i = i0; i <= i1; ++i) {
+            const float ov1 = fminf((float)(v1 + 1), (float)((i + 1) * h) / 16.f) - fmaxf((float)v1, (float)(i * h) / 16.f);
+            for (int j = j0; j <= j1; ++j) {
+                const float ov2 =
+                    fminf((float)(v2 + 1), (float)((j + 1) * w) / 16.f) - fmaxf((float)v2, (float)(j * w) / 16.f);
+                atomicAdd(&rs[16 * i + j], acc * ov1 * ov2);
+            }
+        }
+    }
+    for (int u = tid; u < hx * wx; u += NT) {
+        const int u1 = u / wx, u2 = u - u1 * wx;
+        const double m = A.mu[(r0 + u1) * A.N2 + (c0 + u2)];
+        g[5] += m; g[6] += m * u1; g[7] += m * u2; g[8] += m * u1 * u1; g[9] += m * u2 * u2; g[11] += m * u1 * u2;
+    }
+    block_sum_d<12>(g, red);
+    __nv_bfloat16* out = feat + (long long)DD_MLP_NIN * J;
+    for (int u = tid; u < hx * wx; u += NT) {
+        const int u1 = u / wx, u2 = u - u1 * wx;
+        out[u] = __float2bfloat16_rn((float)(0.25 * log2(A.mu[(r0 + u1) * A.N2 + (c0 + u2)] * 64.0 / g[5])));
+    }
+    for (int k = tid; k < 256; k += NT)
+        out[64 + k] = __float2bfloat16_rn((float)(0.25 * log2(rs[k] * 256.0 / g[0] + 1.0 / 256.0)));
+    if (tid == 0) {
+        const double uc1 = g[6] / g[5], uc2 = g[7] / g[5], vc1 = g[1] / g[0], vc2 = g[2] / g[0];
+        const double vu1 = fmax(g[8] / g[5] - uc1 * uc1, 0.0), vu2 = fmax(g[9] / g[5] - uc2 * uc2, 0.0);
+        const double vv1 = fmax(g[3] / g[0] - vc1 * vc1, 0.0), vv2 = fmax(g[4] / g[0] - vc2 * vc2, 0.0);
+        const double cv = g[10] / g[0] - vc1 * vc2;
+        const double l1 = vu1 > 1e-3 ? fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.0;
+        const double l2 = vu2 > 1e-3 ? fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.0;
+        const double d1 = (r0 - o1) + uc1 - vc1, d2 = (c0 - o2) + uc2 - vc2;
+        const double rho = (vv1 > 0.0 && vv2 > 0.0) ? cv / sqrt(vv1 * vv2) : 0.0;
+        const double sc[16] = {h / 32.0, w / 32.0, d1 / 8.0, d2 / 8.0, log2(l1), log2(l2), (uc1 - 3.5) / 4.0,
+                               (uc2 - 3.5) / 4.0, (vc1 + 0.5) / h - 0.5, (vc2 + 0.5) / w - 0.5, log2(A.k2d),
+                               sqrt(vu1) / 4.0, sqrt(vu2) / 4.0, sqrt(vv1) / 16.0, sqrt(vv2) / 16.0, rho};
+        for (int k = 0; k < 16; ++k) out[320 + k] = __float2bfloat16_rn((float)sc[k]);
+    }
+}
+
+// rows of the cells in `idx` (features, targets) into packed caller buffers
+__global__ void k_collect(int n, const int32_t* __restrict__ idx, const uint4* __restrict__ fsrc,
+                          const uint4* __restrict__ tsrc, uint4* __restrict__ fdst, uint4* __restrict__ tdst) {
+    constexpr int FQ = DD_MLP_NIN * 2 / 16, TQ = DD_MLP_NOUT * 4 / 16;
+    const int r = blockIdx.x;
+    if (r >= n) return;
+    const long long J = idx[r];
+    for (int q = threadIdx.x; q < FQ; q += blockDim.x) fdst[(long long)r * FQ + q] = fsrc[J * FQ + q];
+    for (int q = threadIdx.x; q < TQ; q += blockDim.x) tdst[(long long)r * TQ + q] = tsrc[J * TQ + q];
 }
 
 // CompositeToBasic, D_i, balancing, truncation and compaction of one composite
@@ -1082,9 +1281,26 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;
     A.queue = c->d_queue; A.status = c->d_status;
     A.gscratch = nullptr; A.goff = nullptr;
+    A.affine = (c->opt.warm == DD_WARM_AFFINE || c->opt.warm == DD_WARM_MLP) ? 1 : 0;
+    A.pred = (c->opt.warm == DD_WARM_MLP) ? c->d_pred : nullptr;
+    A.targ = (c->opt.flags & DD_FLAG_COLLECT) ? c->d_targ : nullptr;
     return A;
 }
 }  // namespace
+
+int launch_feat(dd_ctx* c, int part) {
+    HalfArgs A = make_args(c, part);
+    k_feat<<<c->part[part].ncell, 128, 0, c->stream>>>(A, reinterpret_cast<__nv_bfloat16*>(c->d_feat));
+    return launch_status(__func__);
+}
+
+int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* targ) {
+    if (n <= 0) return DD_OK;
+    k_collect<<<n, 64, 0, c->stream>>>(n, idx, reinterpret_cast<const uint4*>(c->d_feat),
+                                       reinterpret_cast<const uint4*>(c->d_targ), reinterpret_cast<uint4*>(feat),
+                                       reinterpret_cast<uint4*>(targ));
+    return launch_status(__func__);
+}
 
 int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 256 ? 256 : 512); }
 

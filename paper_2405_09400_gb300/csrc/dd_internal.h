@@ -119,6 +119,15 @@ struct dd_ctx {
     // CUDA graphs for dd_step
     cudaGraphExec_t gexec = nullptr;
     int graph_cur = -1;
+
+    // learned warm start: network, per-cell features / outputs / targets
+    dd_mlp* mlp = nullptr;
+    bool mlp_ready = false;
+    uint16_t* d_feat = nullptr;  // maxcell x DD_MLP_NIN (BF16)
+    float* d_pred = nullptr;     // maxcell x DD_MLP_NOUT
+    float* d_targ = nullptr;     // maxcell x DD_MLP_NOUT
+    int32_t* d_full[2] = {nullptr, nullptr};  // per partition: cells with a full 8 x 8 block
+    int n_full[2] = {0, 0};
 };
 
 // last CUDA error, kept for dd_last_error()
@@ -141,6 +150,10 @@ int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
 int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem);
 int half_occupancy(int threads, size_t smem);
+int launch_feat(dd_ctx* c, int part);
+int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* targ);
+// dd_mlp.cu
+int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st);
 // dd_flow.cu
 int launch_cbar(dd_ctx* c);
 int launch_plan_exchange(dd_ctx* c);

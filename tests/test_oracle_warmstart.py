@@ -99,6 +99,23 @@ def test_gauge_of_uniform_block():
     assert np.allclose(g["vu"], [63 / 12, 63 / 12]) and np.allclose(g["vv"], [255 / 12, 63 / 12])
     assert np.allclose(g["l"], [np.sqrt(255 / 63), 1.0])
     assert np.allclose(g["d"], [-4 + 3.5 - 7.5, 0.0])
+    # product measures: the Gaussian map is the per-axis stretch
+    assert np.allclose(g["A"], np.diag(g["l"]), atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_gaussian_map_pushes_covariance(seed):
+    """A is symmetric positive semidefinite and A S A = T: the linear map that
+    carries the covariance of mu_J onto that of nu_J (the defining property of
+    the quadratic-cost transport map between Gaussians)."""
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(0.2, 1.0, (8, 8))
+    nu = rng.uniform(0.0, 1.0, (11 + seed, 17 - seed)) ** 3
+    g = ws.cell_gauge(mu, 0, 0, nu, 2, 3)
+    A, S, T = g["A"], g["S"], g["T"]
+    assert np.allclose(A, A.T, atol=1e-12)
+    assert np.linalg.eigvalsh(A).min() >= -1e-12
+    assert np.allclose(A @ S @ A, T, atol=1e-10 * np.abs(T).max())
 
 
 def _solve(mu_blk, r0, c0, nu_arr, o1, o2, eps, h):
@@ -177,9 +194,37 @@ def test_features_of_a_known_cell():
     nu_arr[8:24, :] = 1.0
     f = ws.cell_features(mu_blk, 100, 100, nu_arr, 90, 96, 0.5)
     assert np.allclose(f[:64], 0.0)
-    rs = f[64:320].reshape(16, 16) + 1.0
+    rs = 2.0 ** (4 * f[64:320].reshape(16, 16)) - 1.0 / 256
     assert np.allclose(rs[4:12], 2.0) and np.allclose(rs[:4], 0.0) and np.allclose(rs[12:], 0.0)
     assert np.allclose(f[320:336], [1.0, 0.5, (10 + 3.5 - 15.5) / 8, (4 + 3.5 - 7.5) / 8, np.log2(np.sqrt((255 / 12) / (63 / 12))),
                                     np.log2(np.sqrt((255 / 12) / (63 / 12))), 0.0, 0.0, 0.0, 0.0, -1.0,
                                     np.sqrt(63 / 12) / 4, np.sqrt(63 / 12) / 4, np.sqrt(255 / 12) / 16,
                                     np.sqrt(255 / 12) / 16, 0.0])
+
+
+def test_affine_dual_is_exact_for_a_linear_image():
+    """nu_J the image of mu_J under x -> A0 x + t on a fine enough grid that the
+    moments match: the map A recovered from the moments equals A0, and the
+    target r of the exact unregularised dual vanishes."""
+    rng = np.random.default_rng(3)
+    A0 = np.array([[1.6, 0.4], [0.4, 0.9]])
+    mu = rng.uniform(0.5, 1.5, (8, 8))
+    # the moments of nu_J = the pushforward of mu_J
+    g = ws.cell_gauge(mu, 0, 0, mu, 0, 0)
+    S = g["S"]
+    T = A0 @ S @ A0
+    g2 = dict(g)
+    g2["T"] = T
+    Sh = np.real(ws.sqrtm(S))
+    Shi = np.linalg.inv(Sh)
+    A = Shi @ np.real(ws.sqrtm(Sh @ T @ Sh)) @ Shi
+    assert np.allclose(A, A0, atol=1e-10)
+    g2["A"] = A
+    g2["d"] = np.array([1.5, -2.0])
+    eps, k2 = 1e-3, 0.9
+    ub1, ub2 = ws._ub(g2, 8, 8)
+    # Brenier potential of T(x) = A0 x + t in centred coordinates, in base-2 units
+    alpha = eps * np.log(2.0) * k2 * (ub1 ** 2 + ub2 ** 2 - (A0[0, 0] * ub1 ** 2 + 2 * A0[0, 1] * ub1 * ub2
+                                                             + A0[1, 1] * ub2 ** 2) + 2 * (1.5 * ub1 - 2.0 * ub2))
+    r = ws.alpha_target(alpha, mu, eps, k2, g2)
+    assert np.abs(r).max() <= 1e-9
