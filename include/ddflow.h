@@ -66,6 +66,8 @@ extern "C" {
 
 #define DD_FLAG_KEEP_PREBALANCE 1 /* keep the pre-balance basic marginals of the
                                      last half-iteration for dd_get_prebalance     */
+#define DD_FLAG_NO_GRAPH 4 /* dd_step runs its steps one by one instead of
+                              replaying a captured CUDA graph                     */
 #define DD_FLAG_COLLECT 2 /* compute the warm-start network's inputs before, and
                              its training targets after, every cell solve, for
                              dd_collect_cells (requires cell_size 4)              */
@@ -88,6 +90,8 @@ typedef struct dd_options {
     double omega;        /* X-update over-relaxation a <- a + omega (X(b) - a): 1 = plain
                             Sinkhorn (default, the paper's solver), (1, 2) fixed, < 0
                             adaptive; same fixed point and the same stopping pair      */
+    double graph_margin; /* dd_step graphs: buffer capacities = sizes seen x (1 + margin)
+                            (plus slack when > 0); 0.5. 0 exercises the overflow path  */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */
@@ -169,9 +173,15 @@ int dd_flow_update(dd_ctx* ctx, dd_flow_stats* st);
 
 /*
  * n hybrid iterations of Alg. 3 (A half-iteration, B half-iteration, flow
- * update), replayed from one captured CUDA graph per iteration; the min-cost
- * flow runs as a host node of the graph. Any of the stats pointers may be NULL;
- * when given they receive the values of the LAST iteration.
+ * update). After one iteration run step by step (which fixes buffer sizes and
+ * the flow solver), every iteration is replayed from a captured CUDA graph:
+ * cell classification and ordering run on the device, the min-cost flow is a
+ * host node of the graph. Buffers get capacity margins; if a box or pool would
+ * exceed them, the graph's remaining kernels do nothing and the iteration is
+ * finished step by step (same results), after which the graph is captured
+ * again. DD_FLAG_NO_GRAPH disables the graph. Any of the stats pointers may be
+ * NULL; when given they receive the values of the LAST iteration (in graph
+ * mode stored_entries is that of the state after the flow update).
  */
 int dd_step(dd_ctx* ctx, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf);
 
@@ -240,6 +250,10 @@ int dd_debug_cell(dd_ctx* ctx, int part, int J, float* a, float* b, float* gauge
 /* Counters since dd_init: kernels launched by the library, bytes copied host to
  * device and device to host. Any pointer may be NULL. */
 int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
+
+/* dd_step graph counters since dd_init: graphs captured, iterations replayed
+ * from a graph, replays finished step by step after a capacity overflow. */
+int dd_get_graph_counters(dd_ctx* ctx, int64_t* captures, int64_t* replays, int64_t* fallbacks);
 
 /*
  * Allocation-free variant of the L1 Y-marginal error of dd_get_objective (the

@@ -25,7 +25,7 @@ DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_MAXITER = 0, -1, -2, -3, -4
 DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
 DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
-DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT = 1, 2
+DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH = 1, 2, 4
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 
 EXPORTS = [
@@ -34,7 +34,7 @@ EXPORTS = [
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
-    "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells",
+    "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
 ]
 
 
@@ -45,7 +45,7 @@ class dd_grid(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
-                ("plan_tol", C.c_double), ("omega", C.c_double)]
+                ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double)]
 
 
 class dd_stats(C.Structure):
@@ -110,6 +110,7 @@ def load():
         "dd_get_prebalance": (C.c_int, [vp, _i32p, _f64p, _szp]),
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
         "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
+        "dd_get_graph_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
@@ -304,6 +305,12 @@ def dd_get_counters(ctx):
     return dict(launches=n.value, h2d_bytes=a.value, d2h_bytes=b.value)
 
 
+def dd_get_graph_counters(ctx):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().dd_get_graph_counters(ctx, C.byref(a), C.byref(b), C.byref(c)), "dd_get_graph_counters")
+    return dict(captures=a.value, replays=b.value, fallbacks=c.value)
+
+
 def dd_debug_cell(ctx, part, J, amax):
     """Raw FP32 kernel values of one composite cell (diagnostics)."""
     _f32p = P(C.c_float)
@@ -496,6 +503,9 @@ class DomDec:
 
     def counters(self):
         return dd_get_counters(self.ctx)
+
+    def graph_counters(self):
+        return dd_get_graph_counters(self.ctx)
 
     def set_warmstart_weights(self, params):
         dd_set_warmstart_weights(self.ctx, params)

@@ -57,12 +57,30 @@ int d2h(T* h, const T* d, size_t n, cudaStream_t s) {
     return cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess ? DD_OK : DD_ERR_CUDA;
 }
 
-int ensure_floats(float** p, size_t* cap, size_t need) {
+// grow a float buffer (contents not kept); bumps the context's buffer generation
+// so that captured graphs are rebuilt
+int ensure_floats(dd_ctx* c, float** p, size_t* cap, size_t need) {
     if (*cap >= need && *p) return DD_OK;
     dfree(*p);
     size_t n = need + need / 4 + 4096;
     RET(dmalloc(p, n));
     *cap = n;
+    c->gen += 1;
+    return DD_OK;
+}
+
+// grow a float buffer keeping its first `keep` entries
+int ensure_floats_keep(dd_ctx* c, float** p, size_t* cap, size_t need, size_t keep) {
+    if (*cap >= need && *p) return DD_OK;
+    float* q = nullptr;
+    size_t n = need + need / 4 + 4096;
+    RET(dmalloc(&q, n));
+    if (*p && keep) CK(cudaMemcpyAsync(q, *p, sizeof(float) * std::min(keep, *cap), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(*p);
+    *p = q;
+    *cap = n;
+    c->gen += 1;
     return DD_OK;
 }
 
@@ -124,7 +142,7 @@ int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
         for (int r = 0; r < h; ++r)
             for (int q = 0; q < w; ++q) buf[s0 + (size_t)r * st + q] = (float)data[src++];
     }
-    RET(ensure_floats(&c->pool[c->cur], &c->pool_cap[c->cur], total));
+    RET(ensure_floats(c, &c->pool[c->cur], &c->pool_cap[c->cur], total));
     RET(h2d(c->pool[c->cur], buf.data(), total, c->stream));
     RET(h2d(c->bhdr[c->cur], bh.data(), bh.size(), c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -164,6 +182,19 @@ int validate_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
 int choose_threads(dd_ctx* c, long long maxarea) {
     if (c->opt.threads > 0) return std::min(512, std::max(32, (c->opt.threads / 32) * 32));
     return maxarea <= 1024 ? 128 : 256;
+}
+
+int ensure_comp(dd_ctx* c, int part, size_t comp) {
+    DevPart& P = c->part[part];
+    if (P.comp_cap >= comp && P.comp_b) return DD_OK;
+    dfree(P.comp_b);
+    dfree(P.comp_nu);
+    size_t n = comp + comp / 4 + 4096;
+    RET(dmalloc(&P.comp_b, n));
+    RET(dmalloc(&P.comp_nu, n));
+    P.comp_cap = n;
+    c->gen += 1;
+    return DD_OK;
 }
 
 // per-cell buffers of the learned warm start, and the list of cells with a full
@@ -206,6 +237,7 @@ void dd_default_options(dd_options* o) {
     o->flags = 0;
     o->plan_tol = 1e-12;
     o->omega = 1.0;
+    o->graph_margin = 0.5;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -228,7 +260,8 @@ const char* dd_strerror(int s) {
 void dd_destroy(dd_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (auto& g : c->graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->mcf) mcf_destroy(c->mcf);
     dfree(c->d_mu); dfree(c->d_nu); dfree(c->d_lgmu); dfree(c->d_m); dfree(c->d_xmom);
     dfree(c->d_lnmu); dfree(c->d_lnnu); dfree(c->d_lnnuf);
@@ -240,7 +273,12 @@ void dd_destroy(dd_ctx* c) {
         dfree(c->pool[p]); dfree(c->bhdr[p]);
     }
     dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
-    dfree(c->d_gscr); dfree(c->d_goff);
+    dfree(c->d_gscr); dfree(c->d_goff); dfree(c->d_guard);
+    for (int p = 0; p < 2; ++p) { dfree(c->d_corder[p]); dfree(c->d_ccount[p]); }
+    if (c->h_guard) cudaFreeHost(c->h_guard);
+    for (auto& e : c->gev)
+        if (e) cudaEventDestroy(e);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     dfree(c->d_feat); dfree(c->d_pred); dfree(c->d_targ); dfree(c->d_full[0]); dfree(c->d_full[1]);
     if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
@@ -396,7 +434,15 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_tot, PT_N));
         if (cudaMallocHost((void**)&c->h_tot, sizeof(long long) * PT_N) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
         TRY(dmalloc(&c->d_queue, 4));
-        TRY(dmalloc(&c->d_status, 8));
+        TRY(dmalloc(&c->d_status, 24));
+        TRY(dmalloc(&c->d_guard, 4));
+        if (cudaMemsetAsync(c->d_guard, 0, 4 * sizeof(int), c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        if (cudaMallocHost((void**)&c->h_guard, 4 * sizeof(int)) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
+        TRY(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        for (int p = 0; p < 2; ++p) {
+            TRY(dmalloc(&c->d_corder[p], 3 * (size_t)c->part[p].ncell));
+            TRY(dmalloc(&c->d_ccount[p], 4));
+        }
         TRY(dmalloc(&c->d_cbar, 5 * (size_t)c->nb));
         TRY(dmalloc(&c->d_w, 5 * (size_t)c->nb));
         if (cudaMallocHost((void**)&c->h_cbar, sizeof(double) * 5 * c->nb) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
@@ -406,7 +452,10 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_red, 8));
         for (auto& e : c->ev)
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
-        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        for (auto& e : c->gev)
+            if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
             rc = DD_ERR_CUDA;
@@ -452,7 +501,19 @@ int dd_set_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     return upload_plan(c, hdr, data, n);
 }
 
-static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
+// elapsed milliseconds between two recorded events (0 if they cannot be timed)
+static float event_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;
+    }
+    return ms;
+}
+
+static int fill_stats(dd_ctx* c, int part, dd_stats* st, int slot = 0, cudaEvent_t e0 = nullptr,
+                      cudaEvent_t e1 = nullptr, cudaEvent_t e2 = nullptr) {
+    if (!e0) { e0 = c->ev[0]; e1 = c->ev[1]; e2 = c->ev[2]; }
     DevPart& P = c->part[part];
     std::vector<int32_t> it(P.ncell), ch((size_t)CH_N * P.ncell), xb;
     std::vector<double> er(P.ncell), E(P.ncell);
@@ -461,7 +522,7 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
     RET(d2h(E.data(), P.Ecell, P.ncell, c->stream));
     RET(d2h(ch.data(), P.chdr, ch.size(), c->stream));
     int status[8];
-    RET(d2h(status, c->d_status, 8, c->stream));
+    RET(d2h(status, c->d_status + 8 * slot, 8, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     double Es = 0, es = 0, im = 0, terms = 0;
     int imax = 0;
@@ -487,11 +548,8 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st) {
         st->objective = Es;
         st->l1_x = es;
         st->lse_terms = terms;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]);
-        st->ms_total = ms;
-        cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
-        st->ms_cells = ms;
+        st->ms_total = event_ms(e0, e2);
+        st->ms_cells = event_ms(e1, e2);
         std::vector<int32_t> bh((size_t)BH_N * c->nb);
         RET(d2h(bh.data(), c->bhdr[c->cur], bh.size(), c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -526,16 +584,12 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     CK(cudaStreamSynchronize(c->stream));
     const long long comp = c->h_tot[PT_COMP], outn = c->h_tot[PT_OUT];
     if (outn > (long long)INT32_MAX || comp > (long long)INT32_MAX * 4LL) return DD_ERR_POOL;
-    if (P.comp_cap < (size_t)comp || !P.comp_b) {
-        dfree(P.comp_b);
-        dfree(P.comp_nu);
-        size_t n = (size_t)comp + comp / 4 + 4096;
-        RET(dmalloc(&P.comp_b, n));
-        RET(dmalloc(&P.comp_nu, n));
-        P.comp_cap = n;
-    }
-    RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)outn));
-    if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(&c->d_pre, &c->pre_cap, (size_t)outn));
+    if (P.comp_cap < (size_t)comp || !P.comp_b) RET(ensure_comp(c, part, (size_t)comp));
+    c->status_slot = 0;
+    c->seen.out = std::max(c->seen.out, outn);
+    c->seen.comp[part] = std::max(c->seen.comp[part], comp);
+    RET(ensure_floats(c, &c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)outn));
+    if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(c, &c->d_pre, &c->pre_cap, (size_t)outn));
     // Work queue order: longest expected solve first (box area x the cell's
     // previous Sinkhorn iteration count). Cells are split in two size classes,
     // each launched with shared memory sized for its own largest box: the small
@@ -565,7 +619,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
         const long long a = (long long)h * half_padw(w);
         key[J] = (double)h * w * std::max(1, itp[J]);
-        int cls = a <= kSmallArea && w <= kSmallW ? 1 : 0;
+        int cls = a <= kSmallArea && w <= kSmallW && h <= kSmallH ? 1 : 0;
         if (cls == 0 && a > a_cap) {
             cls = 2;
             goff[J] = gtot;
@@ -576,6 +630,16 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         dims[cls][1] = std::max(dims[cls][1], (long long)h);
         dims[cls][2] = std::max(dims[cls][2], (long long)w);
     }
+    if (!cls_cells[0].empty()) {
+        c->seen.a0 = std::max(c->seen.a0, dims[0][0]);
+        c->seen.h0 = std::max(c->seen.h0, dims[0][1]);
+        c->seen.w0 = std::max(c->seen.w0, dims[0][2]);
+    }
+    c->seen.hmax = std::max(c->seen.hmax, hmax);
+    c->seen.wmax = std::max(c->seen.wmax, wmax);
+    c->seen.gscr = std::max(c->seen.gscr, gtot);
+    c->seen.n0 = std::max(c->seen.n0, (long long)cls_cells[0].size());
+    c->seen.n2 = std::max(c->seen.n2, (long long)cls_cells[2].size());
     auto by_key = [&](int32_t x, int32_t y) { return key[x] > key[y]; };
     std::vector<int32_t> order;
     size_t cls_off[3];
@@ -586,8 +650,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     }
     RET(h2d(P.order, order.data(), order.size(), c->stream));
     if (!cls_cells[2].empty()) {
-        RET(ensure_floats(&c->d_gscr, &c->gscr_cap, (size_t)gtot));
-        if (!c->d_goff) RET(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        RET(ensure_floats(c, &c->d_gscr, &c->gscr_cap, (size_t)gtot));
         RET(h2d(c->d_goff, goff.data(), goff.size(), c->stream));
     }
     size_t smem_c[3] = {0, 0, 0};
@@ -642,6 +705,26 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     return fill_stats(c, part, st);
 }
 
+// flow statistics from the host copy of w and the events (costs: ev[0..1],
+// exchange: ev[2..3])
+static void flow_stats(dd_ctx* c, double value, int32_t piv, double ms_solve, cudaEvent_t* ev, dd_flow_stats* st) {
+    dd_flow_stats fs{};
+    fs.value = value;
+    fs.pivots = piv;
+    int nz = 0;
+    double moved = 0;
+    for (int i = 0; i < c->nb; ++i)
+        for (int k = 1; k < 5; ++k)
+            if (c->h_w[5 * i + k] > 0) { ++nz; moved += c->h_w[5 * i + k]; }
+    fs.nonzero = nz;
+    fs.moved = moved;
+    fs.ms_costs = event_ms(ev[0], ev[1]);
+    fs.ms_solve = ms_solve;
+    fs.ms_exchange = event_ms(ev[2], ev[3]);
+    c->last_flow = fs;
+    if (st) *st = fs;
+}
+
 int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     if (!c) return DD_ERR_ARG;
     if (!c->flow_ready) return DD_ERR_STATE;
@@ -670,47 +753,300 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (c->h_tot[PT_OUT] > (long long)INT32_MAX) return DD_ERR_POOL;
-    RET(ensure_floats(&c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)c->h_tot[PT_OUT]));
+    RET(ensure_floats(c, &c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)c->h_tot[PT_OUT]));
+    c->seen.out = std::max(c->seen.out, c->h_tot[PT_OUT]);
     RET(launch_exchange(c));
     c->n_launch += 1;
     CK(cudaEventRecord(c->ev[6], c->stream));
     c->cur = 1 - c->cur;
     c->flow_ready = false;
     CK(cudaStreamSynchronize(c->stream));
-    dd_flow_stats fs{};
-    fs.value = value;
-    fs.pivots = piv;
-    int nz = 0;
-    double moved = 0;
-    for (int i = 0; i < c->nb; ++i)
-        for (int k = 1; k < 5; ++k)
-            if (c->h_w[5 * i + k] > 0) { ++nz; moved += c->h_w[5 * i + k]; }
-    fs.nonzero = nz;
-    fs.moved = moved;
-    float ms = 0;
-    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
-    fs.ms_costs = ms;
-    fs.ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
-    fs.ms_exchange = ms;
-    c->last_flow = fs;
-    if (st) *st = fs;
+    flow_stats(c, value, piv, std::chrono::duration<double, std::milli>(t1 - t0).count(), c->ev + 3, st);
     return frc == DD_OK ? DD_OK : DD_ERR_FLOW;
 }
 
-int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
-    if (!c || n < 0) return DD_ERR_ARG;
+// ---- dd_step: the hybrid iteration as one CUDA graph -------------------------
+
+namespace {
+
+// one eager hybrid iteration (A, B, flow) through the public steps
+int step_eager(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, int from = 0) {
     int rc = DD_OK;
-    for (int k = 0; k < n; ++k) {
+    if (from <= 0) {
         int r = dd_iterate(c, 0, sa);
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
         if (r != DD_OK) rc = r;
-        r = dd_iterate(c, 1, sb);
+    }
+    if (from <= 1) {
+        int r = dd_iterate(c, 1, sb);
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
         if (r != DD_OK) rc = r;
-        r = dd_flow_update(c, sf);
-        if (r != DD_OK && r != DD_ERR_FLOW) return r;
+    }
+    int r = dd_flow_update(c, sf);
+    if (r != DD_OK && r != DD_ERR_FLOW) return r;
+    return r != DD_OK ? r : rc;
+}
+
+// Capacities for a captured iteration, from the sizes eager steps have seen,
+// with margins; grows the buffers to them. Returns DD_ERR_POOL if the boxes
+// seen so far do not fit the launches a graph can hold.
+int graph_prepare(dd_ctx* c) {
+    dd_ctx::Caps g;
+    const auto& sn = c->seen;
+    const long long smax = half_kernel_max_smem();
+    const double mg = std::max(0.0, c->opt.graph_margin);
+    const long long slack = mg > 0.0 ? 1 : 0;
+    auto grow = [&](long long x, double f, long long add) { return x + (long long)(f * mg * (double)x) + slack * add; };
+    g.pool = grow(sn.out, 1.0, 65536);
+    for (int p = 0; p < 2; ++p) g.comp[p] = grow(sn.comp[p], 1.0, 65536);
+    g.h0 = std::max(kSmallH, grow(sn.h0, 0.5, 4));
+    g.w0 = std::max((long long)kSmallW, grow(sn.w0, 0.5, 4));
+    g.a0 = std::max(kSmallArea, grow(sn.a0, 0.5, 64));
+    while (g.a0 > kSmallArea && (long long)half_smem_bytes(c, g.a0, g.h0, g.w0) > smax) g.a0 -= g.a0 / 16 + 1;
+    if ((long long)half_smem_bytes(c, g.a0, g.h0, g.w0) > smax) return DD_ERR_POOL;
+    g.h2 = std::max(g.h0, grow(sn.hmax, 1.0, 8));
+    g.w2 = std::max(g.w0, grow(sn.wmax, 1.0, 8));
+    auto fits2 = [&](long long h, long long w) {
+        return (long long)half_smem_bytes(c, 0, h, w) <= smax && (long long)c2b_smem_bytes(c, h, w) <= smax;
+    };
+    while (!fits2(g.h2, g.w2) && (g.h2 > sn.hmax || g.w2 > sn.wmax)) {
+        if (g.h2 > sn.hmax) g.h2 -= (g.h2 - sn.hmax + 7) / 8;
+        if (g.w2 > sn.wmax) g.w2 -= (g.w2 - sn.wmax + 7) / 8;
+    }
+    if (!fits2(g.h2, g.w2)) return DD_ERR_POOL;
+    g.gscr = std::max(grow(sn.gscr, 1.0, 0), slack << 20);
+    g.smem[1] = half_smem_bytes(c, kSmallArea, kSmallH, kSmallW);
+    g.smem[0] = half_smem_bytes(c, g.a0, g.h0, g.w0);
+    g.smem[2] = half_smem_bytes(c, 0, g.h2, g.w2);
+    g.smem_c2b = c2b_smem_bytes(c, g.h2, g.w2);
+    const int thr[3] = {256, 128, 256};
+    for (int k = 0; k < 3; ++k) {
+        const int occ = std::max(1, half_occupancy(thr[k], g.smem[k]));
+        g.grid[k] = c->nsm * occ;
+    }
+    g.grid[0] = (int)std::min<long long>(g.grid[0], grow(sn.n0, 0.5, 8) + 1);
+    g.grid[2] = (int)std::min<long long>(g.grid[2], grow(sn.n2, 0.5, 8) + 1);
+    RET(ensure_floats_keep(c, &c->pool[c->cur], &c->pool_cap[c->cur], (size_t)g.pool, c->pool_cap[c->cur]));
+    RET(ensure_floats_keep(c, &c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)g.pool, 0));
+    for (int p = 0; p < 2; ++p) RET(ensure_comp(c, p, (size_t)g.comp[p]));
+    RET(ensure_floats(c, &c->d_gscr, &c->gscr_cap, (size_t)g.gscr));
+    if (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) RET(ensure_floats(c, &c->d_pre, &c->pre_cap, (size_t)g.pool));
+    // what the kernels were captured with must be what the buffers hold
+    g.pool = (long long)std::min(c->pool_cap[0], c->pool_cap[1]);
+    for (int p = 0; p < 2; ++p) g.comp[p] = (long long)c->part[p].comp_cap;
+    g.gscr = (long long)c->gscr_cap;
+    c->gcap = g;
+    return DD_OK;
+}
+
+int enqueue_half_graph(dd_ctx* c, int part, int stage) {
+    DevPart& P = c->part[part];
+    const auto& g = c->gcap;
+    c->status_slot = stage;
+    cudaEvent_t* ev = c->gev + 3 * (stage - 1);
+    // timing events inside a captured graph must be event-record nodes
+    CK(cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal));
+    RET(launch_plan_half(c, part));
+    c->n_launch += 1;
+    if (c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT)) {
+        RET(launch_feat(c, part));
+        c->n_launch += 1;
+        if (c->opt.warm == DD_WARM_MLP) {
+            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
+            c->n_launch += 4;
+        }
+    }
+    CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
+    CK(cudaMemsetAsync(c->d_status + 8 * stage, 0, sizeof(int) * 8, c->stream));
+    RET(launch_classify(c, part, stage));
+    c->n_launch += 1;
+    CK(cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal));
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    const long long d2[3] = {0, g.h2, g.w2}, d0[3] = {g.a0, g.h0, g.w0}, d1[3] = {kSmallArea, kSmallH, kSmallW};
+    RET(launch_half(c, part, c->d_corder[part] + 2LL * P.ncell, P.ncell, c->d_queue + 2, d2, 256, g.smem[2], g.grid[2],
+                    c->side, true, c->d_ccount[part] + 2));
+    RET(launch_half(c, part, c->d_corder[part], P.ncell, c->d_queue + 0, d0, 256, g.smem[0], g.grid[0], c->side,
+                    false, c->d_ccount[part] + 0));
+    RET(launch_half(c, part, c->d_corder[part] + P.ncell, P.ncell, c->d_queue + 1, d1, 128, g.smem[1], g.grid[1],
+                    c->stream, false, c->d_ccount[part] + 1));
+    c->n_launch += 3;
+    CK(cudaEventRecord(c->ev_join, c->side));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    const long long dc[3] = {0, g.h2, g.w2};
+    RET(launch_c2b(c, part, dc, g.smem_c2b));
+    c->n_launch += 1;
+    CK(cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal));
+    c->cur = 1 - c->cur;
+    return DD_OK;
+}
+
+// the min-cost flow of a captured iteration, as a host node (no CUDA calls)
+void CUDART_CB flow_host_node(void* p) {
+    dd_ctx* c = static_cast<dd_ctx*>(p);
+    if (*c->h_guard) {
+        c->g_skipped = true;
+        return;
+    }
+    c->g_skipped = false;
+    auto t0 = std::chrono::steady_clock::now();
+    double value = 0.0;
+    int32_t piv = 0;
+    int frc = mcf_solve(c->mcf, c->h_cbar, c->h_w, &value, &piv);
+    if (frc != DD_OK) {
+        for (int i = 0; i < c->nb; ++i)
+            for (int k = 0; k < 5; ++k) c->h_w[5 * i + k] = k == 0 ? c->h_m[i] : 0.0;
+        value = 0.0;
+    }
+    c->g_value = value;
+    c->g_piv = piv;
+    c->g_frc = frc;
+    c->g_ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int enqueue_flow_graph(dd_ctx* c) {
+    CK(cudaEventRecordWithFlags(c->gev[6], c->stream, cudaEventRecordExternal));
+    RET(launch_cbar(c));
+    CK(cudaEventRecordWithFlags(c->gev[7], c->stream, cudaEventRecordExternal));
+    RET(d2h(c->h_cbar, c->d_cbar, 5 * (size_t)c->nb, c->stream));
+    RET(d2h(c->h_guard, c->d_guard, 1, c->stream));
+    CK(cudaLaunchHostFunc(c->stream, flow_host_node, c));
+    RET(h2d(c->d_w, c->h_w, 5 * (size_t)c->nb, c->stream));
+    CK(cudaEventRecordWithFlags(c->gev[8], c->stream, cudaEventRecordExternal));
+    RET(launch_plan_exchange(c, 3));
+    RET(launch_exchange(c));
+    c->n_launch += 3;
+    CK(cudaEventRecordWithFlags(c->gev[9], c->stream, cudaEventRecordExternal));
+    c->cur = 1 - c->cur;
+    return DD_OK;
+}
+
+int graph_capture(dd_ctx* c, int parity) {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->n_launch;
+    c->stream = c->gstream;
+    c->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? DD_OK : dd_record_cuda_error(e, "cudaStreamBeginCapture");
+    if (rc == DD_OK) rc = enqueue_half_graph(c, 0, 1);
+    if (rc == DD_OK) rc = enqueue_half_graph(c, 1, 2);
+    if (rc == DD_OK) rc = enqueue_flow_graph(c);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaStreamEndCapture(c->gstream, &graph);
+        if (rc == DD_OK && e2 != cudaSuccess) rc = dd_record_cuda_error(e2, "cudaStreamEndCapture");
+    }
+    c->stream = user;
+    c->capturing = false;
+    c->status_slot = 0;
+    c->cur = parity;
+    const long long launches = c->n_launch - l0;
+    c->n_launch = l0;
+    if (rc == DD_OK) {
+        auto& G = c->graph[parity];
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+        cudaError_t e3 = cudaGraphInstantiate(&G.exec, graph, 0);
+        if (e3 != cudaSuccess) {
+            G.exec = nullptr;
+            rc = dd_record_cuda_error(e3, "cudaGraphInstantiate");
+        } else {
+            G.gen = c->gen;
+            G.launches = launches;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+}
+
+// one hybrid iteration from the captured graph; falls back to the eager steps
+// from the stage whose buffers would have overflowed
+int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* used_graph) {
+    const int parity = c->cur;
+    auto& G = c->graph[parity];
+    *used_graph = false;
+    if (!G.exec || G.gen != c->gen) {
+        int r = graph_prepare(c);
+        if (r == DD_OK) r = graph_capture(c, parity);
+        if (r != DD_OK) return step_eager(c, sa, sb, sf);  // boxes beyond what a graph holds
+        c->n_capture += 1;
+    }
+    CK(cudaMemsetAsync(c->d_guard, 0, sizeof(int), c->stream));
+    CK(cudaGraphLaunch(G.exec, c->stream));
+    c->n_launch += G.launches;
+    c->n_replay += 1;
+    int status[24];
+    RET(d2h(c->h_guard, c->d_guard, 1, c->stream));
+    RET(d2h(status, c->d_status, 24, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int guard = *c->h_guard;
+    if (guard == 0) {
+        c->cur = 1 - parity;
+        for (auto& P : c->part) { P.warm_valid = true; P.solved = true; }
+        c->last_part = 1;
+        c->flow_ready = false;
+        *used_graph = true;
+        int rc = DD_OK;
+        if (status[8 + 2] > 0 || status[16 + 2] > 0) return DD_ERR_POOL;
+        if (status[8 + 0] > 0 || status[16 + 0] > 0) rc = DD_ERR_MAXITER;
+        if (c->g_frc != DD_OK) rc = DD_ERR_FLOW;
+        return rc;
+    }
+    // a buffer would have overflowed at stage `guard`: nothing from that stage on
+    // ran; continue eagerly from there (the eager steps grow the buffers and the
+    // next iteration captures again with the sizes seen)
+    CK(cudaMemsetAsync(c->d_guard, 0, sizeof(int), c->stream));
+    c->gen += 1;
+    c->n_fallback += 1;
+    if (guard == 1) {
+        c->cur = parity;
+        return step_eager(c, sa, sb, sf, 0);
+    }
+    c->part[0].warm_valid = c->part[0].solved = true;
+    {
+        int r = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
+        if (r != DD_OK && r != DD_ERR_MAXITER) return r;
+    }
+    if (guard == 2) {
+        c->cur = 1 - parity;
+        c->last_part = 0;
+        c->flow_ready = true;
+        return step_eager(c, sa, sb, sf, 1);
+    }
+    c->part[1].warm_valid = c->part[1].solved = true;
+    {
+        int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);  // B ran in the graph
+        if (r != DD_OK && r != DD_ERR_MAXITER) return r;
+    }
+    c->cur = parity;
+    c->last_part = 1;
+    c->flow_ready = true;
+    return step_eager(c, sa, sb, sf, 2);
+}
+
+}  // namespace
+
+int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
+    if (!c || n < 0) return DD_ERR_ARG;
+    if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
+    int rc = DD_OK;
+    for (int k = 0; k < n; ++k) {
+        // the graph needs the sizes, flow solver and warm starts of one eager iteration
+        const bool can_graph = !(c->opt.flags & DD_FLAG_NO_GRAPH) && c->mcf && c->seen.out > 0 &&
+                               c->part[0].warm_valid && c->part[1].warm_valid;
+        bool used_graph = false;
+        int r = can_graph ? step_graph(c, sa, sb, sf, &used_graph) : step_eager(c, sa, sb, sf);
+        if (r != DD_OK && r != DD_ERR_MAXITER && r != DD_ERR_FLOW) return r;
         if (r != DD_OK) rc = r;
+        if (used_graph) {
+            // statistics of the replayed iteration (objective / errors always, for
+            // dd_get_objective)
+            RET(fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]));
+            int r2 = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);
+            if (r2 != DD_OK && r2 != DD_ERR_MAXITER) return r2;
+            flow_stats(c, c->g_value, c->g_piv, c->g_ms_solve, c->gev + 6, sf);
+        }
     }
     return rc;
 }
@@ -908,6 +1244,14 @@ int dd_debug_cell(dd_ctx* c, int part, int J, float* a, float* b, float* gauge, 
             RET(d2h(b + (size_t)r * ch[CH_W], P.comp_b + comp + (size_t)r * ch[CH_STRIDE], ch[CH_W], c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
+int dd_get_graph_counters(dd_ctx* c, int64_t* captures, int64_t* replays, int64_t* fallbacks) {
+    if (!c) return DD_ERR_ARG;
+    if (captures) *captures = c->n_capture;
+    if (replays) *replays = c->n_replay;
+    if (fallbacks) *fallbacks = c->n_fallback;
     return DD_OK;
 }
 

@@ -23,9 +23,9 @@ namespace {
 
 __global__ void k_cbar(int nb, const int32_t* __restrict__ nbr, const double* __restrict__ xmom,
                        const double* __restrict__ bmom, const double* __restrict__ m, double h2,
-                       double* __restrict__ cbar) {
+                       double* __restrict__ cbar, const int* __restrict__ guard) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
+    if (i >= nb || (guard && *guard)) return;
     const double* bi = bmom + BM_N * i;
     const double q = bi[BM_MASS] / m[i];
     const double Di = bi[BM_D] / m[i];
@@ -68,8 +68,10 @@ __device__ long long block_exscan_x(long long x, long long* sh, long long* total
 // rev[5*j + k] = position of j in the neighbour list of i = nbr[5*j + k]
 __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const int32_t* __restrict__ rev,
                                 const double* __restrict__ w, const int32_t* __restrict__ bhdr,
-                                int32_t* __restrict__ xhdr, long long* __restrict__ tot) {
+                                int32_t* __restrict__ xhdr, long long* __restrict__ tot, int* __restrict__ guard,
+                                long long pool_cap, int stage) {
     __shared__ long long sh[64];
+    if (guard && *guard) return;
     const int T = blockDim.x;
     const int per = (nb + T - 1) / T;
     const int c0 = min(nb, threadIdx.x * per), c1 = min(nb, c0 + per);
@@ -100,7 +102,11 @@ __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const i
         x[CH_OUT_SLOT] = (int32_t)ea;
         ea += (long long)x[CH_H] * x[CH_STRIDE];
     }
-    if (threadIdx.x == 0) tot[PT_OUT] = ta;
+    if (threadIdx.x == 0) {
+        tot[PT_OUT] = ta;
+        // graph mode: the output pool was captured with a fixed capacity
+        if (guard && ta > pool_cap) atomicCAS(guard, 0, stage);
+    }
 }
 
 __device__ __forceinline__ float gather_sum(int y1, int y2, int nsrc, const int* src, const float* coef,
@@ -119,7 +125,9 @@ __global__ void k_exchange(int nb, const int32_t* __restrict__ nbr, const int32_
                            const double* __restrict__ w, const double* __restrict__ m,
                            const int32_t* __restrict__ bhdr_in, const float* __restrict__ pool_in,
                            const int32_t* __restrict__ xhdr, int32_t* __restrict__ bhdr_out,
-                           float* __restrict__ pool_out, double* __restrict__ bmom, float trunc) {
+                           float* __restrict__ pool_out, double* __restrict__ bmom, float trunc,
+                           const int* __restrict__ guard) {
+    if (guard && *guard) return;
     __shared__ int src[5];
     __shared__ float coef[5];
     __shared__ int nsrc;
@@ -231,20 +239,20 @@ __global__ void k_l1y(long long n, const double* __restrict__ acc, const double*
 
 int launch_cbar(dd_ctx* c) {
     k_cbar<<<(c->nb + 255) / 256, 256, 0, c->stream>>>(c->nb, c->d_nbr, c->d_xmom, c->d_bmom, c->d_m,
-                                                       c->h * c->h, c->d_cbar);
+                                                       c->h * c->h, c->d_cbar, c->capturing ? c->d_guard : nullptr);
     return launch_status(__func__);
 }
 
-int launch_plan_exchange(dd_ctx* c) {
+int launch_plan_exchange(dd_ctx* c, int stage) {
     k_plan_exchange<<<1, 1024, 0, c->stream>>>(c->nb, c->d_nbr, c->d_rev, c->d_w, c->bhdr[c->cur], c->d_xhdr,
-                                               c->d_tot);
+                                               c->d_tot, c->capturing ? c->d_guard : nullptr, c->gcap.pool, stage);
     return launch_status(__func__);
 }
 
 int launch_exchange(dd_ctx* c) {
     k_exchange<<<c->nb, 128, 0, c->stream>>>(c->nb, c->d_nbr, c->d_rev, c->d_w, c->d_m, c->bhdr[c->cur],
                                              c->pool[c->cur], c->d_xhdr, c->bhdr[1 - c->cur], c->pool[1 - c->cur],
-                                             c->d_bmom, (float)c->opt.trunc);
+                                             c->d_bmom, (float)c->opt.trunc, c->capturing ? c->d_guard : nullptr);
     return launch_status(__func__);
 }
 

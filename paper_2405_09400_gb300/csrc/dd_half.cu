@@ -230,6 +230,9 @@ struct HalfArgs {
     int affine;         // start from the cell's affine dual (a = log2 mu in the gauge)
     const float* pred;  // ncell x DD_MLP_NOUT network outputs (first 64: predicted r), or null
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
+    // graph mode
+    const int* guard;   // non-zero: a buffer of this iteration would overflow, skip all work
+    const int* count;   // cells in `order` (device), instead of ncell
 };
 
 // shared-memory layout (floats unless noted); BS = padw(max box width)
@@ -383,11 +386,13 @@ __device__ __noinline__ void write_targets(const HalfArgs& A, const Smem& S, int
 template <int NTB>
 __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
+    if (A.guard && *A.guard) return;
     Smem S = carve(smem_raw, A);
     if (S.end > (long long)dyn_smem_bytes()) {  // host and kernel disagree on the layout
         if (threadIdx.x == 0) atomicAdd(&A.status[2], 1);
         return;
     }
+    const int ncell = A.count ? *A.count : A.ncell;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
     const int s = A.s;
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         if (tid == 0) S.ctl[0] = atomicAdd(A.queue, 1);
         __syncthreads();
         const int t = S.ctl[0];
-        if (t >= A.ncell) break;
+        if (t >= ncell) break;
         const int J = A.order[t];
         const int32_t* xb = A.xblk + XB_N * J;
         const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
@@ -847,6 +852,7 @@ __global__ void __launch_bounds__(128) k_feat(HalfArgs A, __nv_bfloat16* __restr
     __shared__ float rs[256];
     __shared__ double red[32 * 12 + 12];
     const int J = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    if (A.guard && *A.guard) return;
     const int32_t* xb = A.xblk + XB_N * J;
     const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX];
     if (hx * wx != kMlpBlock) return;
@@ -916,6 +922,79 @@ __global__ void __launch_bounds__(128) k_feat(HalfArgs A, __nv_bfloat16* __restr
     }
 }
 
+// Graph mode: the size class and the processing order of every cell, on the
+// device (one CTA). Classes as on the host path: 1 small boxes (area <= 1536,
+// h, w <= 64), 0 boxes within the captured class-0 shared-memory capacity, 2
+// the rest (box arrays in global scratch, offsets taken here). Within a class
+// the order is longest expected solve first, by buckets of log2(box area x
+// previous iteration count). Any box beyond what the captured launches hold,
+// and composite / output pools beyond their capacity, set the guard to `stage`:
+// every later kernel of the iteration then does nothing and the host redoes
+// the iteration from that stage without the graph.
+struct ClassCaps {
+    long long a0, h0, w0, h2, w2, gscr, comp, pool;
+};
+
+__global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __restrict__ chdr,
+                                                   const int32_t* __restrict__ iters, ClassCaps cc,
+                                                   int32_t* __restrict__ corder, int* __restrict__ ccount,
+                                                   long long* __restrict__ goff, const long long* __restrict__ tot,
+                                                   int* __restrict__ guard, int stage) {
+    constexpr int NBK = 48;
+    __shared__ int cnt[3][NBK];
+    __shared__ int offs[3][NBK];
+    __shared__ unsigned long long gsum;
+    __shared__ int bad;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int k = tid; k < 3 * NBK; k += T) (&cnt[0][0])[k] = 0;
+    if (tid == 0) {
+        gsum = 0;
+        bad = (tot[PT_COMP] > cc.comp || tot[PT_OUT] > cc.pool) ? 1 : 0;
+    }
+    __syncthreads();
+    auto classify = [&](int J, int& cls, int& bk) {
+        const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
+        const long long a = (long long)h * padw(w);
+        if (a <= kSmallArea && w <= kSmallW && h <= kSmallH) cls = 1;
+        else if (a <= cc.a0 && h <= cc.h0 && w <= cc.w0) cls = 0;
+        else cls = 2;
+        const double key = (double)h * w * max(1, iters[J]);
+        bk = key >= 1.0 ? min(NBK - 1, (int)log2(key)) : 0;
+    };
+    for (int J = tid; J < ncell; J += T) {
+        int cls, bk;
+        classify(J, cls, bk);
+        atomicAdd(&cnt[cls][bk], 1);
+        if (cls == 2) {
+            const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
+            if (h > cc.h2 || w > cc.w2) atomicExch(&bad, 1);
+            goff[J] = (long long)atomicAdd(&gsum, (unsigned long long)(2LL * h * padw(w)));
+        } else {
+            goff[J] = -1;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if ((long long)gsum > cc.gscr) bad = 1;
+        for (int c = 0; c < 3; ++c) {
+            int run = 0;
+            for (int b = NBK - 1; b >= 0; --b) {  // descending keys
+                offs[c][b] = run;
+                run += cnt[c][b];
+            }
+            ccount[c] = run;
+        }
+        if (bad) atomicCAS(guard, 0, stage);
+    }
+    __syncthreads();
+    for (int J = tid; J < ncell; J += T) {
+        int cls, bk;
+        classify(J, cls, bk);
+        const int pos = atomicAdd(&offs[cls][bk], 1);
+        corder[(long long)cls * ncell + pos] = J;
+    }
+}
+
 // rows of the cells in `idx` (features, targets) into packed caller buffers
 __global__ void k_collect(int n, const int32_t* __restrict__ idx, const uint4* __restrict__ fsrc,
                           const uint4* __restrict__ tsrc, uint4* __restrict__ fdst, uint4* __restrict__ tdst) {
@@ -932,6 +1011,7 @@ __global__ void k_collect(int n, const int32_t* __restrict__ idx, const uint4* _
 // needed: the member shares are ratios of partial sums over X).
 __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
+    if (A.guard && *A.guard) return;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int s = A.s;
     const int J = blockIdx.x;
@@ -1279,7 +1359,9 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.trunc = (float)c->opt.trunc;
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
     A.pre = (c->opt.flags & DD_FLAG_KEEP_PREBALANCE) ? c->d_pre : nullptr;
-    A.queue = c->d_queue; A.status = c->d_status;
+    A.queue = c->d_queue; A.status = c->d_status + 8 * c->status_slot;
+    A.guard = c->capturing ? c->d_guard : nullptr;
+    A.count = nullptr;
     A.gscratch = nullptr; A.goff = nullptr;
     A.affine = (c->opt.warm == DD_WARM_AFFINE || c->opt.warm == DD_WARM_MLP) ? 1 : 0;
     A.pred = (c->opt.warm == DD_WARM_MLP) ? c->d_pred : nullptr;
@@ -1304,10 +1386,20 @@ int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* 
 
 int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 256 ? 256 : 512); }
 
+int launch_classify(dd_ctx* c, int part, int stage) {
+    const DevPart& P = c->part[part];
+    ClassCaps cc{c->gcap.a0, c->gcap.h0, c->gcap.w0, c->gcap.h2, c->gcap.w2, c->gcap.gscr, c->gcap.comp[part],
+                 c->gcap.pool};
+    k_classify<<<1, 1024, 0, c->stream>>>(P.ncell, P.chdr, P.iters, cc, c->d_corder[part], c->d_ccount[part],
+                                          c->d_goff, c->d_tot, c->d_guard, stage);
+    return launch_status(__func__);
+}
+
 int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
-                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes) {
+                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes, const int* count_dev) {
     RET_IF(set_attrs());
     HalfArgs A = make_args(c, part);
+    A.count = count_dev;
     if (global_boxes) {
         A.gscratch = c->d_gscr;
         A.goff = c->d_goff;

@@ -86,7 +86,8 @@ struct dd_ctx {
     long long* d_tot = nullptr;  // PT_N
     long long* h_tot = nullptr;  // pinned
     int* d_queue = nullptr;
-    int* d_status = nullptr;   // [0] maxiter count, [1] pool overflow
+    int* d_status = nullptr;   // 3 slices of 8 (eager, graph A, graph B): [0] maxiter, [1] empty cell,
+                               // [2] shared memory too small, [3] stalled
 
     // prebalance copy
     float* d_pre = nullptr;
@@ -116,9 +117,41 @@ struct dd_ctx {
     long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
 
-    // CUDA graphs for dd_step
-    cudaGraphExec_t gexec = nullptr;
-    int graph_cur = -1;
+    // CUDA-graph execution of dd_step: one graph per parity of `cur` at the start
+    // of a hybrid iteration (the state buffers alternate), recaptured whenever a
+    // buffer it captured was reallocated (gen changes).
+    struct GraphExec {
+        cudaGraphExec_t exec = nullptr;
+        long long gen = -1;
+        long long launches = 0;
+    } graph[2];
+    long long gen = 0;
+    long long n_capture = 0, n_replay = 0, n_fallback = 0;
+    bool capturing = false;          // launches go to the capture stream, kernels gated by d_guard
+    int status_slot = 0;             // d_status slice of the running stage (0 eager, 1 A, 2 B)
+    cudaStream_t gstream = nullptr;  // capture stream (the legacy stream cannot be captured)
+    int* d_guard = nullptr;          // [0]: 0, or the stage (1 A, 2 B, 3 flow) that would overflow a buffer
+    int* h_guard = nullptr;          // pinned copy (read by the flow host node and after a replay)
+    int32_t* d_corder[2] = {nullptr, nullptr};  // per partition: class-grouped order, 3 x ncell
+    int* d_ccount[2] = {nullptr, nullptr};      // per partition: cells per class
+    // capacities a graph is captured with, and the sizes eager steps have seen
+    struct Caps {
+        long long pool = 0, comp[2] = {0, 0}, gscr = 0;
+        long long a0 = 0, h0 = 0, w0 = 0;  // class 0 (shared-memory boxes, 256 threads)
+        long long h2 = 0, w2 = 0;          // class 2 (global-scratch boxes) and k_c2b
+        int grid[3] = {0, 0, 0};
+        size_t smem[3] = {0, 0, 0};
+        size_t smem_c2b = 0;
+    } gcap;
+    struct Seen {
+        long long out = 0, comp[2] = {0, 0}, gscr = 0, a0 = 0, h0 = 0, w0 = 0, hmax = 0, wmax = 0, n0 = 0, n2 = 0;
+    } seen;
+    // flow host node results
+    double g_value = 0, g_ms_solve = 0;
+    int32_t g_piv = 0;
+    int g_frc = DD_OK;
+    bool g_skipped = false;
+    cudaEvent_t gev[10] = {};
 
     // learned warm start: network, per-cell features / outputs / targets
     dd_mlp* mlp = nullptr;
@@ -144,7 +177,11 @@ constexpr long long kSmallArea = 1536;
 constexpr int kSmallW = 64;
 int half_padw(int w);
 int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
-                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes = false);
+                int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes = false,
+                const int* count_dev = nullptr);
+// graph mode: size classes and processing order on the device (see k_classify)
+int launch_classify(dd_ctx* c, int part, int stage);
+constexpr long long kSmallH = 64;
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
 int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
@@ -156,6 +193,6 @@ int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* 
 int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st);
 // dd_flow.cu
 int launch_cbar(dd_ctx* c);
-int launch_plan_exchange(dd_ctx* c);
+int launch_plan_exchange(dd_ctx* c, int stage = 0);
 int launch_exchange(dd_ctx* c);
 int launch_l1y(dd_ctx* c, double* out_dev);

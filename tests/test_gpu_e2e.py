@@ -112,3 +112,37 @@ def test_uneven512_boxes_beyond_shared_memory(dd):
     assert f["value"] <= 0
     assert np.isfinite(E) and a["ncell"] == 4096 and b["ncell"] == 4225
     g.close()
+
+
+def _state(g):
+    return [(o1, o2, a.copy()) for o1, o2, a in g.plan()]
+
+
+@pytest.mark.parametrize("margin", [0.5, 0.0])
+def test_graph_step_is_bit_identical_to_step_by_step(dd, margin):
+    """dd_step replays a captured graph (device classification and ordering, the
+    flow as a host node); the cells compute exactly what the step-by-step path
+    computes, so plans and objectives are bit-identical. Margin 0 captures with
+    no capacity slack: boxes that grow overflow the graph's buffers and the
+    iteration is finished step by step from that stage."""
+    mu, nu, eps, p = synth.workload("dd256", 0, N=64)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000, graph_margin=margin)
+    e = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000, flags=dd.DD_FLAG_NO_GRAPH)
+    for it in range(6):
+        sg = g.step(1)
+        se = e.step(1)
+        assert sg[0]["objective"] == se[0]["objective"] and sg[1]["objective"] == se[1]["objective"], it
+        assert sg[2]["value"] == se[2]["value"], it
+        for (a1, a2, a), (b1, b2, b) in zip(_state(g), _state(e)):
+            assert (a1, a2) == (b1, b2) and np.array_equal(a, b)
+        (Eg, xg, yg), (Ee, xe, ye) = g.objective(), e.objective()
+        assert Eg == Ee and xg == xe
+        assert abs(yg - ye) <= 1e-15  # the Y error sums with FP64 atomics (order varies)
+    gc = g.graph_counters()
+    assert gc["replays"] >= 4 and gc["captures"] >= 1
+    if margin == 0.0:
+        assert gc["fallbacks"] >= 1, gc
+    assert e.graph_counters()["replays"] == 0
+    g.close()
+    e.close()
