@@ -59,10 +59,13 @@ extern "C" {
                             when nu_J is mu_J translated and stretched per axis
                             (barycentres and variances of the two marginals);
                             not in the paper                                     */
-#define DD_WARM_MLP 3  /* alpha_init = affine dual + the learned correction of
-                          dd_set_warmstart_weights (cells with a full 8 x 8
-                          block; the others use the affine dual); not in the
-                          paper, requires cell_size 4                            */
+#define DD_WARM_MLP 3  /* learned (dd_set_warmstart_weights; cells with a full
+                          8 x 8 block, the others as DD_WARM_PREV): the first
+                          solve of a partition starts from affine dual + the
+                          network's correction, every later one from the
+                          previous dual + the network's predicted change of the
+                          dual between the two solves; not in the paper,
+                          requires cell_size 4                                   */
 
 #define DD_FLAG_KEEP_PREBALANCE 1 /* keep the pre-balance basic marginals of the
                                      last half-iteration for dd_get_prebalance     */
@@ -250,6 +253,41 @@ int dd_debug_cell(dd_ctx* ctx, int part, int J, float* a, float* b, float* gauge
 /* Counters since dd_init: kernels launched by the library, bytes copied host to
  * device and device to host. Any pointer may be NULL. */
 int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
+
+/*
+ * Launch configuration of the cell kernels (the persistent Sinkhorn kernel runs
+ * one CTA per composite cell at a time, in three size classes):
+ *   class 1: padded box area <= small_area and box height, width <= small_side
+ *            (shared memory, many CTAs per SM),
+ *   class 0: other boxes that fit shared memory,
+ *   class 2: boxes beyond shared memory (their arrays in global scratch).
+ * threads[k] is the CTA size of class k (128, 256 or 512).
+ */
+typedef struct dd_tuning {
+    int32_t threads[3];
+    int32_t small_area;
+    int32_t small_side;
+    double ms_default; /* dd_autotune: time of the trial run with the defaults   */
+    double ms_best;    /* and with the chosen configuration (ms)                 */
+    int32_t trials;    /* configurations timed (0: taken from the cache file)    */
+} dd_tuning;
+
+/* Defaults: threads {256, 128, 256}, small_area 1536, small_side 64. */
+int dd_get_tuning(dd_ctx* ctx, dd_tuning* t);
+int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
+
+/*
+ * Autotuner: times every candidate configuration (threads of the small and
+ * large classes, the small-class limit) on the context's current state, both
+ * partitions, every cell solved to the context's tolerance from the current
+ * warm start (restored before each trial and after the last, so every
+ * configuration does the same solves and the state and next solve are
+ * unchanged), and keeps the fastest. With cache_path not NULL the
+ * result is looked up in / appended to that text file, keyed by GPU name, SM
+ * count, grid, cell size, eps / h^2 and the median / largest box area of the
+ * state. The chosen configuration is in *out (may be NULL).
+ */
+int dd_autotune(dd_ctx* ctx, const char* cache_path, dd_tuning* out);
 
 /* dd_step graph counters since dd_init: graphs captured, iterations replayed
  * from a graph, replays finished step by step after a capacity overflow. */

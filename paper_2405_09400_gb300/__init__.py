@@ -35,6 +35,7 @@ EXPORTS = [
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
     "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
+    "dd_get_tuning", "dd_set_tuning", "dd_autotune",
 ]
 
 
@@ -64,6 +65,15 @@ class dd_flow_stats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class dd_tuning(C.Structure):
+    _fields_ = [("threads", C.c_int32 * 3), ("small_area", C.c_int32), ("small_side", C.c_int32),
+                ("ms_default", C.c_double), ("ms_best", C.c_double), ("trials", C.c_int32)]
+
+    def as_dict(self):
+        return dict(threads=list(self.threads), small_area=self.small_area, small_side=self.small_side,
+                    ms_default=self.ms_default, ms_best=self.ms_best, trials=self.trials)
 
 
 class DDError(RuntimeError):
@@ -111,6 +121,9 @@ def load():
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
         "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_get_graph_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
+        "dd_get_tuning": (C.c_int, [vp, P(dd_tuning)]),
+        "dd_set_tuning": (C.c_int, [vp, P(dd_tuning)]),
+        "dd_autotune": (C.c_int, [vp, C.c_char_p, P(dd_tuning)]),
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
@@ -311,6 +324,25 @@ def dd_get_graph_counters(ctx):
     return dict(captures=a.value, replays=b.value, fallbacks=c.value)
 
 
+def dd_get_tuning(ctx):
+    t = dd_tuning()
+    _check(load().dd_get_tuning(ctx, C.byref(t)), "dd_get_tuning")
+    return t.as_dict()
+
+
+def dd_set_tuning(ctx, threads, small_area, small_side):
+    t = dd_tuning()
+    t.threads = (C.c_int32 * 3)(*threads)
+    t.small_area, t.small_side = int(small_area), int(small_side)
+    _check(load().dd_set_tuning(ctx, C.byref(t)), "dd_set_tuning")
+
+
+def dd_autotune(ctx, cache_path=None):
+    t = dd_tuning()
+    _check(load().dd_autotune(ctx, cache_path.encode() if cache_path else None, C.byref(t)), "dd_autotune")
+    return t.as_dict()
+
+
 def dd_debug_cell(ctx, part, J, amax):
     """Raw FP32 kernel values of one composite cell (diagnostics)."""
     _f32p = P(C.c_float)
@@ -506,6 +538,15 @@ class DomDec:
 
     def graph_counters(self):
         return dd_get_graph_counters(self.ctx)
+
+    def tuning(self):
+        return dd_get_tuning(self.ctx)
+
+    def set_tuning(self, threads, small_area, small_side):
+        dd_set_tuning(self.ctx, threads, small_area, small_side)
+
+    def autotune(self, cache_path=None):
+        return dd_autotune(self.ctx, cache_path)
 
     def set_warmstart_weights(self, params):
         dd_set_warmstart_weights(self.ctx, params)

@@ -49,12 +49,14 @@ void dfree(T*& p) {
 template <typename T>
 int h2d(T* d, const T* h, size_t n, cudaStream_t s) {
     if (n == 0) return DD_OK;
-    return cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, s) == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    cudaError_t e = cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? DD_OK : dd_record_cuda_error(e, "host to device copy");
 }
 template <typename T>
 int d2h(T* h, const T* d, size_t n, cudaStream_t s) {
     if (n == 0) return DD_OK;
-    return cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? DD_OK : dd_record_cuda_error(e, "device to host copy");
 }
 
 // grow a float buffer (contents not kept); bumps the context's buffer generation
@@ -204,6 +206,7 @@ int ensure_learned_buffers(dd_ctx* c) {
     const size_t mc = (size_t)std::max(c->part[0].ncell, c->part[1].ncell);
     RET(dmalloc(&c->d_feat, mc * DD_MLP_NIN));
     RET(dmalloc(&c->d_pred, mc * DD_MLP_NOUT));
+    for (int p = 0; p < 2; ++p) RET(dmalloc(&c->d_pred_old[p], mc * DD_MLP_NOUT));
     RET(dmalloc(&c->d_targ, mc * DD_MLP_NOUT));
     CK(cudaMemsetAsync(c->d_feat, 0, mc * DD_MLP_NIN * sizeof(uint16_t), c->stream));
     CK(cudaMemsetAsync(c->d_pred, 0, mc * DD_MLP_NOUT * sizeof(float), c->stream));
@@ -280,6 +283,7 @@ void dd_destroy(dd_ctx* c) {
         if (e) cudaEventDestroy(e);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     dfree(c->d_feat); dfree(c->d_pred); dfree(c->d_targ); dfree(c->d_full[0]); dfree(c->d_full[1]);
+    dfree(c->d_pred_old[0]); dfree(c->d_pred_old[1]);
     if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
     if (c->h_tot) cudaFreeHost(c->h_tot);
@@ -317,6 +321,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     dd_ctx* c = new (std::nothrow) dd_ctx();
     if (!c) return DD_ERR_OOM;
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
+    c->tune.threads[0] = 256; c->tune.threads[1] = 128; c->tune.threads[2] = 256;
+    c->tune.small_area = 1536; c->tune.small_side = 64;
     const bool learned = c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT);
     if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
@@ -454,8 +460,13 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         for (auto& e : c->gev)
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
+        // the large-box cells run on a high-priority stream: their CTAs are placed
+        // before the small-box kernel's persistent grid fills the SMs, so the
+        // longest solves start first (in graphs too: node priorities)
+        int prio_lo = 0, prio_hi = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
             rc = DD_ERR_CUDA;
@@ -557,17 +568,15 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st, int slot = 0, cudaEvent
         for (int i = 0; i < c->nb; ++i) ent += (int64_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
         st->stored_entries = ent;
     }
-    if (status[2] > 0) return DD_ERR_POOL;  // a kernel found its shared memory too small and skipped
+    // a kernel found its shared memory too small, or a pool slot beyond its buffer, and skipped
+    if (status[2] > 0 || status[4] > 0) return DD_ERR_POOL;
     return status[0] > 0 ? DD_ERR_MAXITER : DD_OK;
 }
 
-int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
-    if (!c) return DD_ERR_ARG;
-    if (part < -1 || part > 1) return DD_ERR_ARG;
-    if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
-    if (part == -1) part = c->last_part == 0 ? 1 : 0;
+}  // extern "C"
+
+int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     DevPart& P = c->part[part];
-    if (c->opt.warm == DD_WARM_MLP && !c->mlp_ready) return DD_ERR_STATE;
     CK(cudaEventRecord(c->ev[0], c->stream));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
@@ -619,7 +628,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
         const long long a = (long long)h * half_padw(w);
         key[J] = (double)h * w * std::max(1, itp[J]);
-        int cls = a <= kSmallArea && w <= kSmallW && h <= kSmallH ? 1 : 0;
+        int cls = a <= c->tune.small_area && w <= c->tune.small_side && h <= c->tune.small_side ? 1 : 0;
         if (cls == 0 && a > a_cap) {
             cls = 2;
             goff[J] = gtot;
@@ -659,9 +668,9 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         smem_c[k] = half_smem_bytes(c, k == 2 ? 0 : dims[k][0], dims[k][1], dims[k][2]);
         if (smem_c[k] > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
     }
-    const int thr_c[3] = {c->opt.threads > 0 ? choose_threads(c, 0) : 256,
-                          c->opt.threads > 0 ? choose_threads(c, 0) : 128,
-                          c->opt.threads > 0 ? choose_threads(c, 0) : 256};
+    const int thr_c[3] = {c->opt.threads > 0 ? choose_threads(c, 0) : c->tune.threads[0],
+                          c->opt.threads > 0 ? choose_threads(c, 0) : c->tune.threads[1],
+                          c->opt.threads > 0 ? choose_threads(c, 0) : c->tune.threads[2]};
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
@@ -687,7 +696,10 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         CK(cudaEventRecord(c->ev_join, c->side));
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
-    {
+    if (c->opt.warm == DD_WARM_MLP && with_c2b)
+        CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    if (with_c2b) {
         const long long dall[3] = {std::max({dims[0][0], dims[1][0], dims[2][0]}),
                                    std::max({dims[0][1], dims[1][1], dims[2][1]}),
                                    std::max({dims[0][2], dims[1][2], dims[2][2]})};
@@ -697,9 +709,23 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
         c->n_launch += 1;
     }
     CK(cudaEventRecord(c->ev[2], c->stream));
+    return DD_OK;
+}
+
+extern "C" {
+
+int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
+    if (!c) return DD_ERR_ARG;
+    if (part < -1 || part > 1) return DD_ERR_ARG;
+    if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
+    if (part == -1) part = c->last_part == 0 ? 1 : 0;
+    DevPart& P = c->part[part];
+    if (c->opt.warm == DD_WARM_MLP && !c->mlp_ready) return DD_ERR_STATE;
+    RET(half_iteration_eager(c, part, true));
     c->cur = 1 - c->cur;
     P.warm_valid = true;
     P.solved = true;
+    P.pred_old_valid = c->opt.warm == DD_WARM_MLP;
     c->last_part = part;
     c->flow_ready = true;
     return fill_stats(c, part, st);
@@ -755,12 +781,16 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     if (c->h_tot[PT_OUT] > (long long)INT32_MAX) return DD_ERR_POOL;
     RET(ensure_floats(c, &c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)c->h_tot[PT_OUT]));
     c->seen.out = std::max(c->seen.out, c->h_tot[PT_OUT]);
+    CK(cudaMemsetAsync(c->d_status + 5, 0, sizeof(int), c->stream));
     RET(launch_exchange(c));
     c->n_launch += 1;
     CK(cudaEventRecord(c->ev[6], c->stream));
     c->cur = 1 - c->cur;
     c->flow_ready = false;
+    int xs = 0;
+    RET(d2h(&xs, c->d_status + 5, 1, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (xs > 0) return DD_ERR_POOL;
     flow_stats(c, value, piv, std::chrono::duration<double, std::milli>(t1 - t0).count(), c->ev + 3, st);
     return frc == DD_OK ? DD_OK : DD_ERR_FLOW;
 }
@@ -799,10 +829,11 @@ int graph_prepare(dd_ctx* c) {
     auto grow = [&](long long x, double f, long long add) { return x + (long long)(f * mg * (double)x) + slack * add; };
     g.pool = grow(sn.out, 1.0, 65536);
     for (int p = 0; p < 2; ++p) g.comp[p] = grow(sn.comp[p], 1.0, 65536);
-    g.h0 = std::max(kSmallH, grow(sn.h0, 0.5, 4));
-    g.w0 = std::max((long long)kSmallW, grow(sn.w0, 0.5, 4));
-    g.a0 = std::max(kSmallArea, grow(sn.a0, 0.5, 64));
-    while (g.a0 > kSmallArea && (long long)half_smem_bytes(c, g.a0, g.h0, g.w0) > smax) g.a0 -= g.a0 / 16 + 1;
+    const long long sa = c->tune.small_area, ss = c->tune.small_side;
+    g.h0 = std::max(ss, grow(sn.h0, 0.5, 4));
+    g.w0 = std::max(ss, grow(sn.w0, 0.5, 4));
+    g.a0 = std::max(sa, grow(sn.a0, 0.5, 64));
+    while (g.a0 > sa && (long long)half_smem_bytes(c, g.a0, g.h0, g.w0) > smax) g.a0 -= g.a0 / 16 + 1;
     if ((long long)half_smem_bytes(c, g.a0, g.h0, g.w0) > smax) return DD_ERR_POOL;
     g.h2 = std::max(g.h0, grow(sn.hmax, 1.0, 8));
     g.w2 = std::max(g.w0, grow(sn.wmax, 1.0, 8));
@@ -814,18 +845,23 @@ int graph_prepare(dd_ctx* c) {
         if (g.w2 > sn.wmax) g.w2 -= (g.w2 - sn.wmax + 7) / 8;
     }
     if (!fits2(g.h2, g.w2)) return DD_ERR_POOL;
+    // one launch for every large box: the tables sized for (h2, w2), box arrays
+    // of up to a0 in shared memory, larger ones in global scratch
+    while (g.a0 > 0 && (long long)half_smem_bytes(c, g.a0, g.h2, g.w2) > smax) g.a0 -= g.a0 / 16 + 4;
+    g.a0 = std::max(0LL, g.a0);
     g.gscr = std::max(grow(sn.gscr, 1.0, 0), slack << 20);
-    g.smem[1] = half_smem_bytes(c, kSmallArea, kSmallH, kSmallW);
-    g.smem[0] = half_smem_bytes(c, g.a0, g.h0, g.w0);
-    g.smem[2] = half_smem_bytes(c, 0, g.h2, g.w2);
+    g.smem[1] = half_smem_bytes(c, sa, ss, ss);
+    g.smem[0] = half_smem_bytes(c, g.a0, g.h2, g.w2);
+    g.smem[2] = 0;
     g.smem_c2b = c2b_smem_bytes(c, g.h2, g.w2);
-    const int thr[3] = {256, 128, 256};
-    for (int k = 0; k < 3; ++k) {
+    const int* thr = c->tune.threads;
+    for (int k = 0; k < 2; ++k) {
         const int occ = std::max(1, half_occupancy(thr[k], g.smem[k]));
         g.grid[k] = c->nsm * occ;
     }
-    g.grid[0] = (int)std::min<long long>(g.grid[0], grow(sn.n0, 0.5, 8) + 1);
-    g.grid[2] = (int)std::min<long long>(g.grid[2], grow(sn.n2, 0.5, 8) + 1);
+
+    // full persistent grids: the class sizes vary between iterations, CTAs that
+    // find the queue empty exit at once
     RET(ensure_floats_keep(c, &c->pool[c->cur], &c->pool_cap[c->cur], (size_t)g.pool, c->pool_cap[c->cur]));
     RET(ensure_floats_keep(c, &c->pool[1 - c->cur], &c->pool_cap[1 - c->cur], (size_t)g.pool, 0));
     for (int p = 0; p < 2; ++p) RET(ensure_comp(c, p, (size_t)g.comp[p]));
@@ -863,16 +899,20 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     CK(cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal));
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    const long long d2[3] = {0, g.h2, g.w2}, d0[3] = {g.a0, g.h0, g.w0}, d1[3] = {kSmallArea, kSmallH, kSmallW};
-    RET(launch_half(c, part, c->d_corder[part] + 2LL * P.ncell, P.ncell, c->d_queue + 2, d2, 256, g.smem[2], g.grid[2],
-                    c->side, true, c->d_ccount[part] + 2));
-    RET(launch_half(c, part, c->d_corder[part], P.ncell, c->d_queue + 0, d0, 256, g.smem[0], g.grid[0], c->side,
-                    false, c->d_ccount[part] + 0));
-    RET(launch_half(c, part, c->d_corder[part] + P.ncell, P.ncell, c->d_queue + 1, d1, 128, g.smem[1], g.grid[1],
+    // large boxes (high-priority stream, pending from the start) and small boxes
+    const long long d0[3] = {g.a0, g.h2, g.w2};
+    const long long d1[3] = {c->tune.small_area, c->tune.small_side, c->tune.small_side};
+    const int* thr = c->tune.threads;
+    RET(launch_half(c, part, c->d_corder[part], P.ncell, c->d_queue + 0, d0, thr[0], g.smem[0], g.grid[0], c->side,
+                    true, c->d_ccount[part] + 0));
+    RET(launch_half(c, part, c->d_corder[part] + P.ncell, P.ncell, c->d_queue + 1, d1, thr[1], g.smem[1], g.grid[1],
                     c->stream, false, c->d_ccount[part] + 1));
-    c->n_launch += 3;
+    c->n_launch += 2;
     CK(cudaEventRecord(c->ev_join, c->side));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (c->opt.warm == DD_WARM_MLP)
+        CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
+                           cudaMemcpyDeviceToDevice, c->stream));
     const long long dc[3] = {0, g.h2, g.w2};
     RET(launch_c2b(c, part, dc, g.smem_c2b));
     c->n_launch += 1;
@@ -913,6 +953,7 @@ int enqueue_flow_graph(dd_ctx* c) {
     CK(cudaLaunchHostFunc(c->stream, flow_host_node, c));
     RET(h2d(c->d_w, c->h_w, 5 * (size_t)c->nb, c->stream));
     CK(cudaEventRecordWithFlags(c->gev[8], c->stream, cudaEventRecordExternal));
+    CK(cudaMemsetAsync(c->d_status + 5, 0, sizeof(int), c->stream));
     RET(launch_plan_exchange(c, 3));
     RET(launch_exchange(c));
     c->n_launch += 3;
@@ -946,7 +987,7 @@ int graph_capture(dd_ctx* c, int parity) {
         auto& G = c->graph[parity];
         if (G.exec) cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
-        cudaError_t e3 = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaError_t e3 = cudaGraphInstantiate(&G.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         if (e3 != cudaSuccess) {
             G.exec = nullptr;
             rc = dd_record_cuda_error(e3, "cudaGraphInstantiate");
@@ -976,6 +1017,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     CK(cudaGraphLaunch(G.exec, c->stream));
     c->n_launch += G.launches;
     c->n_replay += 1;
+    CK(cudaStreamSynchronize(c->stream));
     int status[24];
     RET(d2h(c->h_guard, c->d_guard, 1, c->stream));
     RET(d2h(status, c->d_status, 24, c->stream));
@@ -983,12 +1025,13 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     const int guard = *c->h_guard;
     if (guard == 0) {
         c->cur = 1 - parity;
-        for (auto& P : c->part) { P.warm_valid = true; P.solved = true; }
+        for (auto& P : c->part) { P.warm_valid = true; P.solved = true; P.pred_old_valid = c->opt.warm == DD_WARM_MLP; }
         c->last_part = 1;
         c->flow_ready = false;
         *used_graph = true;
         int rc = DD_OK;
-        if (status[8 + 2] > 0 || status[16 + 2] > 0) return DD_ERR_POOL;
+        if (status[8 + 2] > 0 || status[16 + 2] > 0 || status[8 + 4] > 0 || status[16 + 4] > 0 || status[5] > 0)
+            return DD_ERR_POOL;
         if (status[8 + 0] > 0 || status[16 + 0] > 0) rc = DD_ERR_MAXITER;
         if (c->g_frc != DD_OK) rc = DD_ERR_FLOW;
         return rc;
@@ -1004,6 +1047,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
         return step_eager(c, sa, sb, sf, 0);
     }
     c->part[0].warm_valid = c->part[0].solved = true;
+    c->part[0].pred_old_valid = c->opt.warm == DD_WARM_MLP;
     {
         int r = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
@@ -1015,6 +1059,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
         return step_eager(c, sa, sb, sf, 1);
     }
     c->part[1].warm_valid = c->part[1].solved = true;
+    c->part[1].pred_old_valid = c->opt.warm == DD_WARM_MLP;
     {
         int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);  // B ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;

@@ -126,7 +126,7 @@ __global__ void k_exchange(int nb, const int32_t* __restrict__ nbr, const int32_
                            const int32_t* __restrict__ bhdr_in, const float* __restrict__ pool_in,
                            const int32_t* __restrict__ xhdr, int32_t* __restrict__ bhdr_out,
                            float* __restrict__ pool_out, double* __restrict__ bmom, float trunc,
-                           const int* __restrict__ guard) {
+                           const int* __restrict__ guard, long long out_cap, int* __restrict__ status) {
     if (guard && *guard) return;
     __shared__ int src[5];
     __shared__ float coef[5];
@@ -152,6 +152,10 @@ __global__ void k_exchange(int nb, const int32_t* __restrict__ nbr, const int32_
     const int32_t* x = xhdr + CH_N * j;
     const int o1 = x[CH_O1], o2 = x[CH_O2], h = x[CH_H], ww = x[CH_W];
     const long long start = x[CH_OUT_SLOT];
+    if (start + (long long)h * x[CH_STRIDE] > out_cap) {  // beyond the output pool: skip, report
+        if (threadIdx.x == 0) atomicAdd(status, 1);
+        return;
+    }
     // pass 1: minimal box of the entries >= trunc
     int lo1 = INT32_MAX, hi1 = -1, lo2 = INT32_MAX, hi2 = -1;
     for (int v = threadIdx.x; v < h * ww; v += blockDim.x) {
@@ -252,7 +256,8 @@ int launch_plan_exchange(dd_ctx* c, int stage) {
 int launch_exchange(dd_ctx* c) {
     k_exchange<<<c->nb, 128, 0, c->stream>>>(c->nb, c->d_nbr, c->d_rev, c->d_w, c->d_m, c->bhdr[c->cur],
                                              c->pool[c->cur], c->d_xhdr, c->bhdr[1 - c->cur], c->pool[1 - c->cur],
-                                             c->d_bmom, (float)c->opt.trunc, c->capturing ? c->d_guard : nullptr);
+                                             c->d_bmom, (float)c->opt.trunc, c->capturing ? c->d_guard : nullptr,
+                                             (long long)c->pool_cap[1 - c->cur], c->d_status + 5);
     return launch_status(__func__);
 }
 

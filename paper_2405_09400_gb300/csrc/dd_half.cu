@@ -229,10 +229,14 @@ struct HalfArgs {
     // learned / analytic warm start (cells with a full 2s x 2s block only)
     int affine;         // start from the cell's affine dual (a = log2 mu in the gauge)
     const float* pred;  // ncell x DD_MLP_NOUT network outputs (first 64: predicted r), or null
+    const float* pred_old;  // the outputs of the previous solve of this partition, or null
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
     // graph mode
     const int* guard;   // non-zero: a buffer of this iteration would overflow, skip all work
     const int* count;   // cells in `order` (device), instead of ncell
+    // capacities (floats) of the pools the kernels write: a cell whose slots would
+    // reach beyond them is skipped and counted in status[4] (never expected)
+    long long comp_cap, out_cap, gscr_cap, pre_cap;
 };
 
 // shared-memory layout (floats unless noted); BS = padw(max box width)
@@ -269,8 +273,10 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.B2 = d;
     d += BS;
     float* f = reinterpret_cast<float*>(((uintptr_t)d + 15) & ~(uintptr_t)15);  // float4 rows
-    S.lgnu = f; f += A.smaxA;
-    S.b = f; f += A.smaxA;
+    // every array after this point is read as float4 rows: keep 16-byte offsets
+    const int A4 = (A.smaxA + 3) & ~3;
+    S.lgnu = f; f += A4;
+    S.b = f; f += A4;
     S.T = f; f += s2 * BS;
     S.R = f; f += A.smaxH * s2;
     S.tab1 = f; f += A.smaxH * s2;
@@ -415,6 +421,11 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // log2 nu_J and b~ live in shared memory, or for boxes too large for it
         // in a global scratch slot of the cell (L2-resident)
         const long long go = A.goff ? A.goff[J] : -1;
+        if (comp + area > A.comp_cap || (go >= 0 && go + 2LL * h * bs > A.gscr_cap)) {
+            if (tid == 0) atomicAdd(&A.status[4], 1);
+            __syncthreads();
+            continue;
+        }
         float* const lgnu_p = go >= 0 ? A.gscratch + go : S.lgnu;
         float* const b_p = go >= 0 ? A.gscratch + go + (long long)h * bs : S.b;
         int32_t mem[4];
@@ -532,8 +543,10 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const float* ap = A.alpha + (long long)A.amax * J;
         const float* pg = A.gauge + 8 * J;
         const float pd1 = pg[0], pd2 = pg[1], pl1 = pg[2], pl2 = pg[3];
-        // network prediction r of the dual relative to the cell's affine dual
+        // network prediction r of the dual relative to the cell's affine dual, and
+        // the prediction for the previous solve of the cell (same X block)
         const float* pr = (A.pred && nx == kMlpBlock) ? A.pred + (long long)DD_MLP_NOUT * J : nullptr;
+        const float* pro = (pr && A.pred_old && A.warm) ? A.pred_old + (long long)DD_MLP_NOUT * J : nullptr;
         for (int u = tid; u < nx; u += NT) {
             const int u1 = u / wx, u2 = u - u1 * wx;
             const int x = (r0 + u1) * A.N2 + (c0 + u2);
@@ -544,13 +557,19 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             const float ub1 = u1 - uc1, ub2 = u2 - uc2;
             float a0;
             const float qa = A.k2 * (q11 * ub1 * ub1 + 2.f * q12 * ub1 * ub2 + q22 * ub2 * ub2);
-            if (pr)
+            // the previous dual of this cell in the new gauge (mu_J, hence uc, is
+            // the same; only d and l change): exact change of gauge
+            const float aprev = A.warm ? ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2) +
+                                             A.k2 * ((l1 - pl1) * ub1 * ub1 + (l2 - pl2) * ub2 * ub2)
+                                       : 0.f;
+            if (pro)  // previous dual + the network's predicted change of the dual
+                a0 = aprev + (pr[u] - pro[u]);
+            else if (pr)  // first solve: the network's prediction
                 a0 = lg + qa + pr[u];
+            else if (A.warm)
+                a0 = aprev;
             else if (A.affine)
                 a0 = lg + qa;
-            else if (A.warm)
-                a0 = ap[u] + 2.f * A.k2 * ((pd1 - d1) * ub1 + (pd2 - d2) * ub2) +
-                     A.k2 * ((l1 - pl1) * ub1 * ub1 + (l2 - pl2) * ub2 * ub2);
             else
                 a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2) + A.k2 * ((l1 - 1.f) * ub1 * ub1 + (l2 - 1.f) * ub2 * ub2);
             aC[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
@@ -923,16 +942,17 @@ __global__ void __launch_bounds__(128) k_feat(HalfArgs A, __nv_bfloat16* __restr
 }
 
 // Graph mode: the size class and the processing order of every cell, on the
-// device (one CTA). Classes as on the host path: 1 small boxes (area <= 1536,
-// h, w <= 64), 0 boxes within the captured class-0 shared-memory capacity, 2
-// the rest (box arrays in global scratch, offsets taken here). Within a class
-// the order is longest expected solve first, by buckets of log2(box area x
-// previous iteration count). Any box beyond what the captured launches hold,
-// and composite / output pools beyond their capacity, set the guard to `stage`:
+// device (one CTA). Two classes: 1 small boxes (area and sides within the tuned
+// small-class limits), 0 all others, in one launch: boxes within the captured
+// shared-memory capacity (a0, h0, w0) keep their arrays in shared memory, the
+// rest in global scratch (offsets taken here). Within a class the order is
+// longest expected solve first, by buckets of log2(box area x previous
+// iteration count). Any box beyond what the captured launch holds, and
+// composite / output pools beyond their capacity, set the guard to `stage`:
 // every later kernel of the iteration then does nothing and the host redoes
 // the iteration from that stage without the graph.
 struct ClassCaps {
-    long long a0, h0, w0, h2, w2, gscr, comp, pool;
+    long long a0, h0, w0, h2, w2, gscr, comp, pool, sa, ss;
 };
 
 __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __restrict__ chdr,
@@ -941,12 +961,12 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
                                                    long long* __restrict__ goff, const long long* __restrict__ tot,
                                                    int* __restrict__ guard, int stage) {
     constexpr int NBK = 48;
-    __shared__ int cnt[3][NBK];
-    __shared__ int offs[3][NBK];
+    __shared__ int cnt[2][NBK];
+    __shared__ int offs[2][NBK];
     __shared__ unsigned long long gsum;
     __shared__ int bad;
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int k = tid; k < 3 * NBK; k += T) (&cnt[0][0])[k] = 0;
+    for (int k = tid; k < 2 * NBK; k += T) (&cnt[0][0])[k] = 0;
     if (tid == 0) {
         gsum = 0;
         bad = (tot[PT_COMP] > cc.comp || tot[PT_OUT] > cc.pool) ? 1 : 0;
@@ -955,9 +975,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     auto classify = [&](int J, int& cls, int& bk) {
         const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
         const long long a = (long long)h * padw(w);
-        if (a <= kSmallArea && w <= kSmallW && h <= kSmallH) cls = 1;
-        else if (a <= cc.a0 && h <= cc.h0 && w <= cc.w0) cls = 0;
-        else cls = 2;
+        cls = (a <= cc.sa && w <= cc.ss && h <= cc.ss) ? 1 : 0;
         const double key = (double)h * w * max(1, iters[J]);
         bk = key >= 1.0 ? min(NBK - 1, (int)log2(key)) : 0;
     };
@@ -965,8 +983,9 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
         int cls, bk;
         classify(J, cls, bk);
         atomicAdd(&cnt[cls][bk], 1);
-        if (cls == 2) {
-            const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
+        const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
+        const long long a = (long long)h * padw(w);
+        if (cls == 0 && !(a <= cc.a0 && h <= cc.h0 && w <= cc.w0)) {
             if (h > cc.h2 || w > cc.w2) atomicExch(&bad, 1);
             goff[J] = (long long)atomicAdd(&gsum, (unsigned long long)(2LL * h * padw(w)));
         } else {
@@ -976,7 +995,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     __syncthreads();
     if (tid == 0) {
         if ((long long)gsum > cc.gscr) bad = 1;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 2; ++c) {
             int run = 0;
             for (int b = NBK - 1; b >= 0; --b) {  // descending keys
                 offs[c][b] = run;
@@ -1025,6 +1044,10 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     const int nx = hx * wx, nA = h * w;
     const int bs = padw(w);
     if (nA == 0) return;  // handled (empty outputs) by k_sink
+    if (comp + area > A.comp_cap || slot0 + nmem * area > A.out_cap || (A.pre && slot0 + nmem * area > A.pre_cap)) {
+        if (tid == 0) atomicAdd(&A.status[4], 1);
+        return;
+    }
     int32_t mem[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
@@ -1305,6 +1328,7 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
 
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
+    maxarea = (maxarea + 3) & ~3LL;  // as in carve()
     size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS) + 16;
     size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 4 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
@@ -1351,7 +1375,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.bhdr_out = c->bhdr[1 - c->cur]; A.pool_out = c->pool[1 - c->cur];
     A.chdr = P.chdr; A.comp_b = P.comp_b; A.comp_nu = P.comp_nu;
     A.alpha = P.alpha; A.gauge = P.gauge;
-    A.warm = (c->opt.warm == DD_WARM_PREV && P.warm_valid) ? 1 : 0;
+    A.warm = ((c->opt.warm == DD_WARM_PREV || c->opt.warm == DD_WARM_MLP) && P.warm_valid) ? 1 : 0;
     A.lgmu = c->d_lgmu; A.mu = c->d_mu; A.nu = c->d_nu; A.m = c->d_m;
     A.lnmu = c->d_lnmu; A.lnnu = c->d_lnnu; A.lnnuf = c->d_lnnuf;
     A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
@@ -1362,9 +1386,14 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.queue = c->d_queue; A.status = c->d_status + 8 * c->status_slot;
     A.guard = c->capturing ? c->d_guard : nullptr;
     A.count = nullptr;
+    A.comp_cap = (long long)P.comp_cap;
+    A.out_cap = (long long)c->pool_cap[1 - c->cur];
+    A.gscr_cap = (long long)c->gscr_cap;
+    A.pre_cap = (long long)c->pre_cap;
     A.gscratch = nullptr; A.goff = nullptr;
     A.affine = (c->opt.warm == DD_WARM_AFFINE || c->opt.warm == DD_WARM_MLP) ? 1 : 0;
     A.pred = (c->opt.warm == DD_WARM_MLP) ? c->d_pred : nullptr;
+    A.pred_old = (c->opt.warm == DD_WARM_MLP && P.pred_old_valid) ? c->d_pred_old[part] : nullptr;
     A.targ = (c->opt.flags & DD_FLAG_COLLECT) ? c->d_targ : nullptr;
     return A;
 }
@@ -1389,7 +1418,7 @@ int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 
 int launch_classify(dd_ctx* c, int part, int stage) {
     const DevPart& P = c->part[part];
     ClassCaps cc{c->gcap.a0, c->gcap.h0, c->gcap.w0, c->gcap.h2, c->gcap.w2, c->gcap.gscr, c->gcap.comp[part],
-                 c->gcap.pool};
+                 c->gcap.pool, c->tune.small_area, c->tune.small_side};
     k_classify<<<1, 1024, 0, c->stream>>>(P.ncell, P.chdr, P.iters, cc, c->d_corder[part], c->d_ccount[part],
                                           c->d_goff, c->d_tot, c->d_guard, stage);
     return launch_status(__func__);

@@ -46,6 +46,7 @@ struct DevPart {
     size_t comp_cap = 0;
     bool warm_valid = false;
     bool solved = false;
+    bool pred_old_valid = false;  // d_pred_old holds the network outputs of this partition's last solve
     std::vector<int32_t> h_members;  // host copy
     std::vector<int32_t> h_xblk;     // host copy
 };
@@ -74,6 +75,7 @@ struct dd_ctx {
 
     DevPart part[2];
     int last_part = -1;
+    dd_tuning tune{};  // launch configuration of the cell kernels
     bool flow_ready = false;
 
     // basic state, double buffered
@@ -158,6 +160,7 @@ struct dd_ctx {
     bool mlp_ready = false;
     uint16_t* d_feat = nullptr;  // maxcell x DD_MLP_NIN (BF16)
     float* d_pred = nullptr;     // maxcell x DD_MLP_NOUT
+    float* d_pred_old[2] = {nullptr, nullptr};  // per partition: the outputs used by its last solve
     float* d_targ = nullptr;     // maxcell x DD_MLP_NOUT
     int32_t* d_full[2] = {nullptr, nullptr};  // per partition: cells with a full 8 x 8 block
     int n_full[2] = {0, 0};
@@ -172,16 +175,15 @@ inline int launch_status(const char* where) {
 
 // kernels / launchers (dd_half.cu)
 int launch_plan_half(dd_ctx* c, int part);
-// cells whose padded box area / width exceed these run in the large-box launch
-constexpr long long kSmallArea = 1536;
-constexpr int kSmallW = 64;
 int half_padw(int w);
 int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
                 int threads, size_t smem, int grid, cudaStream_t stream, bool global_boxes = false,
                 const int* count_dev = nullptr);
 // graph mode: size classes and processing order on the device (see k_classify)
 int launch_classify(dd_ctx* c, int part, int stage);
-constexpr long long kSmallH = 64;
+// one eager half-iteration up to the cell kernels (with_c2b: and CompositeToBasic);
+// records ev[0] (start), ev[1] (cells), ev[2] (end); does not flip the state
+int half_iteration_eager(dd_ctx* c, int part, bool with_c2b);
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
 int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);

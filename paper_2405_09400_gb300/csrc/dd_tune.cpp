@@ -1,0 +1,252 @@
+// Autotuner of the cell kernels' launch configuration (dd_autotune).
+//
+// The batched Sinkhorn kernel solves one composite cell per CTA, with the
+// cells split into size classes by their bounding box (see dd_tuning in
+// ddflow.h). Which CTA size serves which boxes best depends on the GPU and on
+// the distribution of box sizes of the problem, so the library measures it:
+// every candidate configuration runs the cell kernels of both partitions on the
+// context's current state, each cell solved to the context's tolerance from the
+// current warm start (restored before every trial, so every configuration does
+// the same solves, tail of slow cells included), and the fastest configuration
+// is kept. Results can be cached in a text file keyed by the GPU
+// and a signature of the problem.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dd_internal.h"
+
+namespace {
+
+struct Saved {
+    float* alpha = nullptr;
+    float* gauge = nullptr;
+    int32_t* iters = nullptr;
+    double* err = nullptr;
+    double* E = nullptr;
+};
+
+template <typename T>
+int copy_dev(T* dst, const T* src, size_t n, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? DD_OK
+               : dd_record_cuda_error(cudaGetLastError(), "dd_autotune copy");
+}
+
+// the per-cell results a trial overwrites and the next solve reads (warm start,
+// processing order) or reports (errors, objective)
+int save_part(dd_ctx* c, int p, Saved& S, bool restore) {
+    DevPart& P = c->part[p];
+    const size_t n = (size_t)P.ncell;
+    if (!restore) {
+        if (cudaMalloc(&S.alpha, sizeof(float) * c->amax * n) != cudaSuccess ||
+            cudaMalloc(&S.gauge, sizeof(float) * 8 * n) != cudaSuccess ||
+            cudaMalloc(&S.iters, sizeof(int32_t) * n) != cudaSuccess ||
+            cudaMalloc(&S.err, sizeof(double) * n) != cudaSuccess || cudaMalloc(&S.E, sizeof(double) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return DD_ERR_OOM;
+        }
+    }
+    float* a[2] = {P.alpha, S.alpha};
+    float* g[2] = {P.gauge, S.gauge};
+    int32_t* it[2] = {P.iters, S.iters};
+    double* er[2] = {P.err, S.err};
+    double* E[2] = {P.Ecell, S.E};
+    const int d = restore ? 0 : 1, s = restore ? 1 : 0;
+    int r = copy_dev(a[d], a[s], (size_t)c->amax * n, c->stream);
+    if (r == DD_OK) r = copy_dev(g[d], g[s], 8 * n, c->stream);
+    if (r == DD_OK) r = copy_dev(it[d], it[s], n, c->stream);
+    if (r == DD_OK) r = copy_dev(er[d], er[s], n, c->stream);
+    if (r == DD_OK) r = copy_dev(E[d], E[s], n, c->stream);
+    return r;
+}
+
+void free_saved(Saved& S) {
+    if (S.alpha) cudaFree(S.alpha);
+    if (S.gauge) cudaFree(S.gauge);
+    if (S.iters) cudaFree(S.iters);
+    if (S.err) cudaFree(S.err);
+    if (S.E) cudaFree(S.E);
+    S = Saved{};
+}
+
+// key of the cache: GPU, grid, cell size, eps / h^2, box sizes of the state
+int cache_key(dd_ctx* c, std::string* key) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) return dd_record_cuda_error(cudaGetLastError(), "dd_autotune");
+    std::vector<int32_t> bh((size_t)BH_N * c->nb);
+    if (cudaMemcpyAsync(bh.data(), c->bhdr[c->cur], bh.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return dd_record_cuda_error(cudaGetLastError(), "dd_autotune");
+    std::vector<long long> area(c->nb);
+    for (int i = 0; i < c->nb; ++i) area[i] = (long long)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
+    std::sort(area.begin(), area.end());
+    const int p50 = (int)std::lround(std::log2((double)std::max(1LL, area[area.size() / 2])));
+    const int pmax = (int)std::lround(std::log2((double)std::max(1LL, area.back())));
+    char buf[512];
+    std::string name(prop.name);
+    std::replace(name.begin(), name.end(), ' ', '_');
+    std::snprintf(buf, sizeof(buf), "gpu=%s;sms=%d;grid=%dx%d;s=%d;eps_h2=%.4g;box_log2_p50=%d;box_log2_max=%d",
+                  name.c_str(), prop.multiProcessorCount, c->N1, c->N2, c->s, c->eps / (c->h * c->h), p50, pmax);
+    *key = buf;
+    return DD_OK;
+}
+
+bool cache_lookup(const char* path, const std::string& key, dd_tuning* t) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        const size_t k = key.size();
+        if (std::strncmp(line, key.c_str(), k) != 0 || line[k] != ' ') continue;
+        dd_tuning x{};
+        if (std::sscanf(line + k, " threads=%d,%d,%d small_area=%d small_side=%d ms_default=%lf ms_best=%lf",
+                        &x.threads[0], &x.threads[1], &x.threads[2], &x.small_area, &x.small_side, &x.ms_default,
+                        &x.ms_best) == 7) {
+            *t = x;
+            found = true;  // the last entry for the key wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, const dd_tuning& t) {
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s threads=%d,%d,%d small_area=%d small_side=%d ms_default=%.4f ms_best=%.4f\n", key.c_str(),
+                 t.threads[0], t.threads[1], t.threads[2], t.small_area, t.small_side, t.ms_default, t.ms_best);
+    std::fclose(f);
+}
+
+bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
+
+// cell-kernel time of one configuration: both partitions, best of two runs
+int trial(dd_ctx* c, const dd_tuning& t, Saved* saved, double* ms) {
+    c->tune = t;
+    double best = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+        double tot = 0.0;
+        for (int p = 0; p < 2; ++p) {
+            int r = save_part(c, p, saved[p], true);
+            if (r != DD_OK) return r;
+            r = half_iteration_eager(c, p, false);
+            if (r != DD_OK) return r;
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return dd_record_cuda_error(cudaGetLastError(), "dd_autotune trial");
+            float m = 0.f;
+            if (cudaEventElapsedTime(&m, c->ev[1], c->ev[2]) != cudaSuccess) {
+                cudaGetLastError();
+                m = 0.f;
+            }
+            tot += m;
+        }
+        best = std::min(best, tot);
+    }
+    *ms = best;
+    return DD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dd_get_tuning(dd_ctx* c, dd_tuning* t) {
+    if (!c || !t) return DD_ERR_ARG;
+    *t = c->tune;
+    return DD_OK;
+}
+
+int dd_set_tuning(dd_ctx* c, const dd_tuning* t) {
+    if (!c || !t) return DD_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!valid_threads(t->threads[k])) return DD_ERR_ARG;
+    if (t->small_area < 16 || t->small_side < 4 || t->small_side > 256) return DD_ERR_ARG;
+    if (half_smem_bytes(c, t->small_area, t->small_side, t->small_side) > (size_t)half_kernel_max_smem())
+        return DD_ERR_ARG;
+    c->tune = *t;
+    c->gen += 1;  // captured graphs use the old launch configuration
+    return DD_OK;
+}
+
+int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
+    if (!c) return DD_ERR_ARG;
+    if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
+    if (c->opt.warm == DD_WARM_MLP && !c->mlp_ready) return DD_ERR_STATE;
+    std::string key;
+    int r = cache_key(c, &key);
+    if (r != DD_OK) return r;
+    dd_tuning found{};
+    if (cache_path && cache_lookup(cache_path, key, &found) && dd_set_tuning(c, &found) == DD_OK) {
+        c->tune.trials = 0;
+        if (out) *out = c->tune;
+        return DD_OK;
+    }
+    const dd_tuning defaults = c->tune;
+    Saved saved[2];
+    for (int p = 0; p < 2 && r == DD_OK; ++p) r = save_part(c, p, saved[p], false);
+    dd_tuning best = defaults;
+    double best_ms = 1e300, def_ms = 0.0;
+    int n = 0;
+    if (r == DD_OK) r = trial(c, defaults, saved, &def_ms);
+    if (r == DD_OK) {
+        best_ms = def_ms;
+        ++n;
+    }
+    const int sides[3][2] = {{768, 48}, {1536, 64}, {3072, 96}};
+    for (int t1 : {128, 256}) {
+        for (int t0 : {256, 512}) {
+            for (const auto& sd : sides) {
+                if (r != DD_OK) break;
+                dd_tuning t = defaults;
+                t.threads[0] = t0;
+                t.threads[1] = t1;
+                t.threads[2] = t0;
+                t.small_area = sd[0];
+                t.small_side = sd[1];
+                if (std::memcmp(t.threads, defaults.threads, sizeof(t.threads)) == 0 &&
+                    t.small_area == defaults.small_area && t.small_side == defaults.small_side)
+                    continue;
+                if (half_smem_bytes(c, t.small_area, t.small_side, t.small_side) > (size_t)half_kernel_max_smem())
+                    continue;
+                double ms = 0.0;
+                r = trial(c, t, saved, &ms);
+                ++n;
+                if (r == DD_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+        }
+    }
+    // leave the per-cell state as it was before the trials
+    for (int p = 0; p < 2; ++p) {
+        if (saved[p].alpha) {
+            int r2 = save_part(c, p, saved[p], true);
+            if (r == DD_OK) r = r2;
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    for (auto& S : saved) free_saved(S);
+    if (r != DD_OK) {
+        c->tune = defaults;
+        return r;
+    }
+    best.ms_default = def_ms;
+    best.ms_best = best_ms;
+    best.trials = n;
+    c->tune = best;
+    c->gen += 1;
+    if (cache_path) cache_store(cache_path, key, best);
+    if (out) *out = best;
+    return DD_OK;
+}
+
+}  // extern "C"

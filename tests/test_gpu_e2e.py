@@ -146,3 +146,31 @@ def test_graph_step_is_bit_identical_to_step_by_step(dd, margin):
     assert e.graph_counters()["replays"] == 0
     g.close()
     e.close()
+
+
+def test_autotune_restores_state_and_caches(dd, tmp_path):
+    """The autotuner's trials leave the state and warm starts as they were: the
+    next half-iterations equal those of a context given the chosen
+    configuration directly (bit-identical). A second context reads the choice
+    from the cache file without trials."""
+    mu, nu, eps, p = synth.workload("dd256", 0, N=64)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    cache = str(tmp_path / "tune.txt")
+    a = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000)
+    b = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000)
+    a.step(1)
+    b.step(1)
+    t = a.autotune(cache)
+    assert t["trials"] >= 2 and 0 < t["ms_best"] <= t["ms_default"]
+    b.set_tuning(t["threads"], t["small_area"], t["small_side"])
+    for part in (0, 1, 0):
+        sa, sb = a.iterate(part), b.iterate(part)
+        assert sa["objective"] == sb["objective"] and sa["iters_mean"] == sb["iters_mean"]
+    for (a1, a2, x), (b1, b2, y) in zip(_state(a), _state(b)):
+        assert (a1, a2) == (b1, b2) and np.array_equal(x, y)
+    c = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000)
+    c.step(1)
+    t2 = c.autotune(cache)
+    assert t2["trials"] == 0 and t2["threads"] == t["threads"] and t2["small_area"] == t["small_area"]
+    for g in (a, b, c):
+        g.close()
