@@ -38,6 +38,9 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 EX2_PER_CLK_SM = 32  # MUFU ex2 issue rate per SM per clock (see the design notes)
+# cell solver of every arm: eps-scaling inside each solve (eps 16, 4, 1 x the
+# target; the stop and the solution are those of the target eps)
+SOLVER = dict(eps_levels=2, eps_factor=4.0, eps_tol=1e-3)
 
 
 def peaks():
@@ -122,7 +125,7 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
     import torch
 
     g = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=warm, weights=weights,
-                  flags=flags)
+                  flags=flags, **SOLVER)
     if tune is not None:
         g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"])
     # the first hybrid iteration from the initial coupling (cold solves for the
@@ -183,21 +186,30 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     weights, _ = ws.load_params()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    arms = set(args.arms.split(","))
     # autotune the cell-kernel launch configuration on this GPU and workload
-    tctx = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
-                     weights=weights)
-    tctx.step(2, stats=False)
-    tune = tctx.autotune()
-    tctx.close()
+    tune = None
+    if not args.no_tune:
+        tctx = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
+                         weights=weights, **SOLVER)
+        tctx.step(2, stats=False)
+        tune = tctx.autotune()
+        tctx.close()
     if world > 1:
         torch.distributed.barrier()
+    none = None
     with ClockSampler(local) as clk:
-        plain = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_PREV, None, args, flush, stream, tune)
+        plain = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_PREV, None, args, flush, stream, tune) \
+            if "plain" in arms else none
         warm = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_MLP, weights, args, flush, stream, tune)
-    affine = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_AFFINE, None, args, flush, stream, tune)
-    eager = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_MLP, weights, args, flush, stream, tune, dd.DD_FLAG_NO_GRAPH)
+    affine = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_AFFINE, None, args, flush, stream, tune) \
+        if "affine" in arms else none
+    eager = _arm(dd, mu, nu, eps, p, boxes, dd.DD_WARM_MLP, weights, args, flush, stream, tune,
+                 dd.DD_FLAG_NO_GRAPH) if "eager" in arms else none
 
     def total(x):
+        if x is None:
+            return float("nan")
         t = sum(x["step_ms"])
         if world > 1:
             tt = torch.tensor([t], device="cuda")
@@ -222,7 +234,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         ge2 = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, plan_tol=1e-5,
-                        warm=dd.DD_WARM_MLP, weights=weights)
+                        warm=dd.DD_WARM_MLP, weights=weights, **SOLVER)
         ge2.set_tuning(tune["threads"], tune["small_area"], tune["small_side"])
         for _ in range(args.warmup):
             ge2.step(1, stats=False)
@@ -249,6 +261,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(bo)}
         ge2.close()
 
+    arm_map = {k: x for k, x in (("plain", plain), ("warm", warm), ("affine", affine)) if x is not None}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args, mu, nu, eps, p, boxes)
@@ -265,19 +278,15 @@ def run_ours(args):
                                "cell tol 1e-5; a step = one hybrid iteration (A, B, flow) replayed from a CUDA "
                                "graph, every cell solved to L1 X error <= 1e-5 of its mass",
                    "cells_per_half_iteration": [1024, 1089], "warm_start": "learned (value); plain = "
-                   "previous-iterate duals (the paper's)", "tuning": tune,
+                   "previous-iterate duals (the paper's)", "tuning": tune, "cell_solver": SOLVER,
                    "l2": "512 MB buffer written between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "plain_ms_per_step": round(ms_plain, 4), "warm_start_ms_per_step": round(ms_warm, 4),
-        "affine_start_ms_per_step": round(ms_aff, 4),
-        "warm_start_step_by_step_ms_per_step": round(ms_eager, 4),
-        "speedup_warm_vs_plain": round(ms_plain / ms_warm, 3),
-        "first_step_ms": {"plain": round(plain["first_ms"], 3), "warm": round(warm["first_ms"], 3),
-                          "affine": round(affine["first_ms"], 3)},
-        "sinkhorn_iters_mean": {"plain": round(float(np.mean(plain["iters_mean"])), 2),
-                                "warm": round(float(np.mean(warm["iters_mean"])), 2),
-                                "affine": round(float(np.mean(affine["iters_mean"])), 2)},
-        "sinkhorn_iters_max_mean": {"plain": round(float(np.mean(plain["iters_max"])), 1),
-                                    "warm": round(float(np.mean(warm["iters_max"])), 1)},
+        "plain_ms_per_step": round(ms_plain, 4) if plain else None, "warm_start_ms_per_step": round(ms_warm, 4),
+        "affine_start_ms_per_step": round(ms_aff, 4) if affine else None,
+        "warm_start_step_by_step_ms_per_step": round(ms_eager, 4) if eager else None,
+        "speedup_warm_vs_plain": round(ms_plain / ms_warm, 3) if plain else None,
+        "first_step_ms": {k: round(x["first_ms"], 3) for k, x in arm_map.items()},
+        "sinkhorn_iters_mean": {k: round(float(np.mean(x["iters_mean"])), 2) for k, x in arm_map.items()},
+        "sinkhorn_iters_max_mean": {k: round(float(np.mean(x["iters_max"])), 1) for k, x in arm_map.items()},
         "iterations_per_s": round(1e3 / ms_warm, 3),
         "cells_per_s": round(warm["cells"] / (sum(warm["step_ms"]) * 1e-3), 1),
         "graph": warm["graph"],
@@ -388,6 +397,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default launch configuration (no autotuning)")
+    ap.add_argument("--arms", default="plain,warm,affine,eager",
+                    help="comma list of arms to time besides the learned warm start (plain, affine, eager)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

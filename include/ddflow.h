@@ -95,6 +95,11 @@ typedef struct dd_options {
                             adaptive; same fixed point and the same stopping pair      */
     double graph_margin; /* dd_step graphs: buffer capacities = sizes seen x (1 + margin)
                             (plus slack when > 0); 0.5. 0 exercises the overflow path  */
+    int32_t eps_levels;  /* eps-scaling inside every cell solve (tolerance mode): first
+                            at eps f^L, ..., eps f, then at eps with the usual stop; the
+                            solution is that of eps. 0 (default) = plain solve         */
+    double eps_factor;   /* f > 1; 4                                                    */
+    double eps_tol;      /* a coarse level ends at L1 X error <= eps_tol mu(X_J); 1e-3 */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */

@@ -46,7 +46,8 @@ class dd_grid(C.Structure):
 class dd_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
-                ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double)]
+                ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double),
+                ("eps_levels", C.c_int32), ("eps_factor", C.c_double), ("eps_tol", C.c_double)]
 
 
 class dd_stats(C.Structure):

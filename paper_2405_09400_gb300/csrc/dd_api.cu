@@ -241,6 +241,9 @@ void dd_default_options(dd_options* o) {
     o->plan_tol = 1e-12;
     o->omega = 1.0;
     o->graph_margin = 0.5;
+    o->eps_levels = 0;
+    o->eps_factor = 4.0;
+    o->eps_tol = 1e-3;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -326,7 +329,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     const bool learned = c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT);
     if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
-        (learned && s != 4)) {
+        c->opt.eps_levels < 0 || c->opt.eps_levels > 8 ||
+        (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4)) {
         delete c;
         return DD_ERR_ARG;
     }

@@ -231,6 +231,10 @@ struct HalfArgs {
     const float* pred;  // ncell x DD_MLP_NOUT network outputs (first 64: predicted r), or null
     const float* pred_old;  // the outputs of the previous solve of this partition, or null
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
+    // eps-scaling inside each solve (tolerance mode only): levels eps f^L .. eps
+    int eps_levels;
+    float eps_factor;
+    double eps_tol;     // a coarse level ends at L1 X error <= eps_tol * mu(X_J)
     // graph mode
     const int* guard;   // non-zero: a buffer of this iteration would overflow, skip all work
     const int* count;   // cells in `order` (device), instead of ncell
@@ -342,6 +346,46 @@ __device__ void affine_excess(double s11, double s12, double s22, double t11, do
     q11 = (float)(l1 - a11);
     q12 = (float)(-a12);
     q22 = (float)(l2 - a22);
+}
+
+// Kernel tables of one cell at cost scale k2d (base-2 units per squared pixel).
+// With t = vbar / l_k, the axis kernel is
+//   K_k(u, v) = k2 l_k (ubar - t)^2,
+// its minimum over the block's grid points is B_k(v) = k2 l_k (ubar* - t)^2 at
+// the grid point ubar* nearest to t, and the table holds
+//   K_k - B_k = k2 l_k D (D + w0),  D = u - u* (integer), w0 = 2 (ubar* - t),
+// w0 taken in FP64 per v and rounded once, so that the small values that matter
+// keep full FP32 precision. The Y dual is stored as b~ = b - B_1(v1) - B_2(v2)
+// (an exact change of gauge). No barrier: the caller synchronises.
+__device__ void build_tables(const Smem& S, double k2d, int h, int w, int bs, int hx, int wx, float uc1, float uc2,
+                             float vc1, float vc2, float l1, float l2) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    for (int v1 = tid; v1 < h; v1 += NT) {
+        const double tt = (v1 - (double)vc1) / (double)l1;
+        const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
+        const double w0 = 2.0 * ((us - (double)uc1) - tt);
+        S.B1[v1] = 0.25 * k2d * l1 * w0 * w0;
+        const float w0f = (float)w0, kl = (float)(k2d * l1);
+        for (int u1 = 0; u1 < hx; ++u1) {
+            const float D = (float)(u1 - us);
+            S.tab1[u1 * h + v1] = kl * D * (D + w0f);
+        }
+    }
+    for (int v2 = tid; v2 < bs; v2 += NT) {
+        if (v2 >= w) {
+            for (int u2 = 0; u2 < wx; ++u2) S.tab2[u2 * bs + v2] = 0.f;
+            continue;
+        }
+        const double tt = (v2 - (double)vc2) / (double)l2;
+        const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
+        const double w0 = 2.0 * ((us - (double)uc2) - tt);
+        S.B2[v2] = 0.25 * k2d * l2 * w0 * w0;
+        const float w0f = (float)w0, kl = (float)(k2d * l2);
+        for (int u2 = 0; u2 < wx; ++u2) {
+            const float D = (float)(u2 - us);
+            S.tab2[u2 * bs + v2] = kl * D * (D + w0f);
+        }
+    }
 }
 
 // Training targets of the warm-start network for one solved cell: the dual
@@ -503,40 +547,13 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         if (A.affine || A.targ)
             affine_excess(vu1, gm[11] / gm[5] - (double)uc1 * uc2, vu2, vv1, gm[10] / gm[0] - (double)vc1 * vc2, vv2,
                           l1, l2, q11, q12, q22);
-        // Kernel tables. With t = vbar / l_k, the axis kernel is
-        //   K_k(u, v) = k2 l_k (ubar - t)^2,
-        // its minimum over the block's grid points is B_k(v) = k2 l_k (ubar* - t)^2
-        // at the grid point ubar* nearest to t, and the table holds
-        //   K_k - B_k = k2 l_k D (D + w0),  D = u - u* (integer), w0 = 2 (ubar* - t),
-        // w0 taken in FP64 per v and rounded once, so that the small values that
-        // matter keep full FP32 precision. The Y dual is stored as
-        // b~ = b - B_1(v1) - B_2(v2) (an exact change of gauge).
-        for (int v1 = tid; v1 < h; v1 += NT) {
-            const double tt = (v1 - (double)vc1) / (double)l1;
-            const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
-            const double w0 = 2.0 * ((us - (double)uc1) - tt);
-            S.B1[v1] = 0.25 * A.k2d * l1 * w0 * w0;
-            const float w0f = (float)w0, kl = (float)(A.k2d * l1);
-            for (int u1 = 0; u1 < hx; ++u1) {
-                const float D = (float)(u1 - us);
-                S.tab1[u1 * h + v1] = kl * D * (D + w0f);
-            }
-        }
-        for (int v2 = tid; v2 < bs; v2 += NT) {
-            if (v2 >= w) {
-                for (int u2 = 0; u2 < wx; ++u2) S.tab2[u2 * bs + v2] = 0.f;
-                continue;
-            }
-            const double tt = (v2 - (double)vc2) / (double)l2;
-            const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
-            const double w0 = 2.0 * ((us - (double)uc2) - tt);
-            S.B2[v2] = 0.25 * A.k2d * l2 * w0 * w0;
-            const float w0f = (float)w0, kl = (float)(A.k2d * l2);
-            for (int u2 = 0; u2 < wx; ++u2) {
-                const float D = (float)(u2 - us);
-                S.tab2[u2 * bs + v2] = kl * D * (D + w0f);
-            }
-        }
+        // Kernel tables (see build_tables), at the coarsest level of the optional
+        // eps-scaling: eps_L = eps f^L, the cost in base-2 units k2 / f^L.
+        const bool scaling = A.eps_levels > 0 && A.fixed_iters <= 0;
+        int lev = scaling ? A.eps_levels : 0;
+        float lev_scale = 1.f;  // eps / eps_level
+        for (int k = 0; k < lev; ++k) lev_scale /= A.eps_factor;
+        build_tables(S, A.k2d * (double)lev_scale, h, w, bs, hx, wx, uc1, uc2, vc1, vc2, l1, l2);
         // X side: log2 mu and the warm start
         float* aC = S.a;
         float* aN = S.a + A.amax;
@@ -572,7 +589,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 a0 = lg + qa;
             else
                 a0 = lg - 2.f * A.k2 * (d1 * ub1 + d2 * ub2) + A.k2 * ((l1 - 1.f) * ub1 * ub1 + (l2 - 1.f) * ub2 * ub2);
-            aC[u] = lg > 0.5f * DD_NEG ? a0 : DD_NEG;
+            // at a coarser level the dual relative to log2 mu scales as 1 / eps
+            aC[u] = lg > 0.5f * DD_NEG ? lg + lev_scale * (a0 - lg) : DD_NEG;
         }
         {
             // the duals are defined up to (a + C, b - C): start every solve with
@@ -787,6 +805,37 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 }
             }
             err_prev = err;
+            if (lev > 0) {
+                // coarse level: refine once its error is within eps_tol (or it
+                // stalls), a <- log2 mu + f (a' - log2 mu) with the newest X dual,
+                // tables at the finer scale, exact shifts on the next iteration
+                if (err <= A.eps_tol * A.mJ[J] || stalled || it >= A.max_iter) {
+                    // out of iterations: straight to the target eps (one last
+                    // iteration there keeps the outputs consistent)
+                    float f = A.eps_factor;
+                    if (it >= A.max_iter) {
+                        f = 1.f / lev_scale;
+                        lev = 1;
+                    }
+                    --lev;
+                    lev_scale *= f;
+                    __syncthreads();  // every thread has read aN / the error partials
+                    for (int u = tid; u < nx; u += NT)
+                        aC[u] = S.lgm[u] > 0.5f * DD_NEG ? S.lgm[u] + f * (aN[u] - S.lgm[u]) : DD_NEG;
+                    build_tables(S, A.k2d * (double)lev_scale, h, w, bs, hx, wx, uc1, uc2, vc1, vc2, l1, l2);
+                    for (int q = tid; q < hx * bs; q += NT) S.T[q] = DD_NEG;
+                    first = true;
+                    best = 1e300;
+                    since = 0;
+                    stalled = false;
+                    __syncthreads();
+                    continue;
+                }
+                float* tmp = aC;
+                aC = aN;
+                aN = tmp;
+                continue;
+            }
             const bool done = (A.fixed_iters > 0) ? (it >= A.fixed_iters)
                                                   : (err <= tolm || it >= A.max_iter || stalled);
             if (done) break;
@@ -1386,6 +1435,9 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.queue = c->d_queue; A.status = c->d_status + 8 * c->status_slot;
     A.guard = c->capturing ? c->d_guard : nullptr;
     A.count = nullptr;
+    A.eps_levels = c->opt.eps_levels;
+    A.eps_factor = (float)c->opt.eps_factor;
+    A.eps_tol = c->opt.eps_tol;
     A.comp_cap = (long long)P.comp_cap;
     A.out_cap = (long long)c->pool_cap[1 - c->cur];
     A.gscr_cap = (long long)c->gscr_cap;

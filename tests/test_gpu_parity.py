@@ -158,12 +158,15 @@ def test_composite_to_basic_D_and_balancing_from_gpu_duals(dd):
     g.close()
 
 
-@pytest.mark.parametrize("workload,N,init", [("dd32", 32, "product"), ("dd256", 64, "kr")])
-def test_tolerance_mode_marginal_errors(dd, workload, N, init):
+@pytest.mark.parametrize("workload,N,init,levels", [("dd32", 32, "product", 0), ("dd256", 64, "kr", 0),
+                                                     ("dd32", 32, "product", 2), ("dd256", 64, "kr", 2)])
+def test_tolerance_mode_marginal_errors(dd, workload, N, init, levels):
+    """levels > 0: eps-scaling inside each solve (coarser eps first); the stop
+    and the solution are those of the target eps, so the same bounds hold."""
     mu, nu, eps, p = synth.workload(workload, 0, N=N)
     tol = 1e-5
     boxes = None if init == "product" else synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
-    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000)
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000, eps_levels=levels, eps_factor=4.0)
     geom = Geometry(N, N, 4)
     for part in (0, 1, 0):
         st = g.iterate(part)
