@@ -15,10 +15,11 @@
 //    cell grid; it is strongly feasible, and the leaving arc is chosen by
 //    Cunningham's rule (last blocking arc from the apex), which rules out cycling;
 //  * entering arcs by block search over the reduced costs;
-//  * the tree is kept as parent pointers with doubly linked child lists; the
-//    apex of a pivot cycle is found by marking the two upward walks; after a
-//    pivot the cut subtree is re-rooted, and the potentials of the smaller of
-//    the cut subtree and the rest are shifted (only differences matter).
+//  * the tree is kept in preorder-thread form (parent, thread, reverse thread,
+//    subtree size, last node of the subtree): the join of a pivot cycle is found
+//    by climbing from the side with the smaller subtree, the cut subtree is
+//    re-rooted by relinking O(stem) thread segments, and the potentials of the
+//    smaller of the cut subtree and the rest are shifted, walking the thread.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -30,81 +31,93 @@ namespace {
 
 int mcf_block = 0;  // entering-arc block size; 0 = sqrt(#arcs)
 
+// The spanning tree is kept in preorder-thread form: thread[x] is the node after
+// x in a preorder walk of the tree (cyclic), rev_thread its inverse, succ[x] the
+// size of x's subtree and last[x] the last node of x's subtree in that order, so
+// every subtree is one contiguous run of the thread.
 struct NetworkSimplex {
     int nn = 0;  // nodes: sources 0..n-1, sinks n..2n-1
     int na = 0;  // arcs
+    int root = 0;
     std::vector<int> tail, head;
     std::vector<int64_t> cost, flow;
-    std::vector<int> parent, parc, first_child, next_sib, prev_sib;
+    std::vector<int> parent, parc, thread, rev_thread, succ, last;
     std::vector<int64_t> pot;
-    std::vector<int64_t> stamp;  // last pivot that visited the node (apex search)
-    std::vector<int> pos;        // position of the node in its apex-search path
     std::vector<char> in_tree;
-    std::vector<int> pu, pv, path, arcs, s1, s2, l1, l2;
+    std::vector<int> pu, pv, stem, seg;
     int64_t pivots = 0;
 #ifdef MCF_STATS
     int64_t st_refresh = 0, st_path = 0, st_scan = 0, st_degenerate = 0;
 #endif
 
-    void add_child(int p, int c) {
-        prev_sib[c] = -1;
-        next_sib[c] = first_child[p];
-        if (first_child[p] >= 0) prev_sib[first_child[p]] = c;
-        first_child[p] = c;
-    }
-    void remove_child(int p, int c) {
-        if (prev_sib[c] >= 0)
-            next_sib[prev_sib[c]] = next_sib[c];
-        else
-            first_child[p] = next_sib[c];
-        if (next_sib[c] >= 0) prev_sib[next_sib[c]] = prev_sib[c];
-        next_sib[c] = prev_sib[c] = -1;
-    }
     int64_t rc(int a) const { return cost[a] + pot[tail[a]] - pot[head[a]]; }
 
-    // potentials of the whole tree from the root (node 0), tree arcs priced at 0
+    // thread, sizes and last nodes from parent pointers (child lists built here)
+    void build_thread() {
+        std::vector<int> first_child(nn, -1), next_sib(nn, -1);
+        for (int x = nn - 1; x >= 0; --x)
+            if (parent[x] >= 0) {
+                next_sib[x] = first_child[parent[x]];
+                first_child[parent[x]] = x;
+            }
+        thread.assign(nn, -1);
+        rev_thread.assign(nn, -1);
+        succ.assign(nn, 1);
+        last.assign(nn, -1);
+        std::vector<int> order, st;
+        order.reserve(nn);
+        st.push_back(root);
+        while (!st.empty()) {
+            int x = st.back();
+            st.pop_back();
+            order.push_back(x);
+            std::vector<int> ch;
+            for (int c = first_child[x]; c >= 0; c = next_sib[c]) ch.push_back(c);
+            for (int k = (int)ch.size() - 1; k >= 0; --k) st.push_back(ch[k]);
+        }
+        for (int k = 0; k < nn; ++k) {
+            thread[order[k]] = order[(k + 1) % nn];
+            rev_thread[order[(k + 1) % nn]] = order[k];
+        }
+        for (int k = nn - 1; k >= 0; --k) {
+            int x = order[k];
+            if (parent[x] >= 0) succ[parent[x]] += succ[x];
+        }
+        for (int k = 0; k < nn; ++k) {
+            int x = order[k];
+            last[x] = order[k + succ[x] - 1];
+        }
+    }
+
+    // potentials of the whole tree from the root, tree arcs priced at 0
     void price_tree() {
-        s1.clear();
-        pot[0] = 0;
-        for (int c = first_child[0]; c >= 0; c = next_sib[c]) s1.push_back(c);
-        while (!s1.empty()) {
-            int x = s1.back();
-            s1.pop_back();
-            int p = parent[x], a = parc[x];
+        pot[root] = 0;
+        for (int x = thread[root]; x != root; x = thread[x]) {
+            const int p = parent[x], a = parc[x];
             pot[x] = (tail[a] == p) ? pot[p] + cost[a] : pot[p] - cost[a];
-            for (int c = first_child[x]; c >= 0; c = next_sib[c]) s1.push_back(c);
         }
     }
 
     bool pivot(int a) {
         const int u = tail[a], v = head[a];
-        const int64_t tag = pivots + 1;
-        // apex: walk up from u and v alternately, marking the nodes of each walk;
-        // the first node reached that the other walk already marked is the apex.
-        // pu / pv end up holding the nodes strictly below the apex on each side.
+        // join of the two tree paths: climb from the side with the smaller subtree
+        // (an ancestor's subtree is strictly larger); pu / pv hold the nodes
+        // strictly below the join on each side, from u resp. v upwards
         pu.clear();
         pv.clear();
-        stamp[u] = tag; pos[u] = 0; pu.push_back(u);
-        stamp[v] = -tag; pos[v] = 0; pv.push_back(v);
-        int x = u, y = v, apex = -1;
-        while (apex < 0) {
-            bool moved = false;
-            if (parent[x] >= 0) {
-                moved = true;
+        int x = u, y = v;
+        while (x != y) {
+            if (succ[x] < succ[y]) {
+                pu.push_back(x);
                 x = parent[x];
-                if (stamp[x] == -tag) { apex = x; pv.resize(pos[x]); break; }
-                stamp[x] = tag; pos[x] = (int)pu.size(); pu.push_back(x);
-            }
-            if (parent[y] >= 0) {
-                moved = true;
+            } else {
+                pv.push_back(y);
                 y = parent[y];
-                if (stamp[y] == tag) { apex = y; pu.resize(pos[y]); break; }
-                stamp[y] = -tag; pos[y] = (int)pv.size(); pv.push_back(y);
             }
-            if (!moved) return false;  // not a tree (cannot happen)
         }
-        // backward arcs: on the u path (traversed apex -> u, downwards) arcs
-        // pointing up; on the v path (traversed v -> apex, upwards) arcs pointing down.
+        const int join = x;
+        // cycle join -> u, a, v -> join: on the u path arcs pointing up are
+        // backward, on the v path arcs pointing down
         int64_t theta = INT64_MAX;
         for (int z : pu) {
             int e = parc[z];
@@ -119,19 +132,21 @@ struct NetworkSimplex {
         st_path += pu.size() + pv.size();
         if (theta == 0) ++st_degenerate;
 #endif
-        // leaving arc: last blocking arc in the order apex->u, a, v->apex
-        int leave_node = -1;
+        // leaving arc: the last blocking arc of the cycle from the join (keeps the
+        // basis strongly feasible, no cycling)
+        int q = -1;
         bool on_v = false;
         for (int k = (int)pv.size() - 1; k >= 0; --k) {
             int z = pv[k], e = parc[z];
-            if (head[e] == z && flow[e] == theta) { leave_node = z; on_v = true; break; }
+            if (head[e] == z && flow[e] == theta) { q = z; on_v = true; break; }
         }
-        if (leave_node < 0) {
+        if (q < 0) {
             for (int k = 0; k < (int)pu.size(); ++k) {
                 int z = pu[k], e = parc[z];
-                if (tail[e] == z && flow[e] == theta) { leave_node = z; break; }
+                if (tail[e] == z && flow[e] == theta) { q = z; break; }
             }
         }
+        if (q < 0) return false;
         if (theta > 0) {
             for (int z : pu) {
                 int e = parc[z];
@@ -143,59 +158,80 @@ struct NetworkSimplex {
             }
             flow[a] += theta;
         }
-        // the subtree T_q below the leaving arc re-hangs at the endpoint r of a
-        // inside it; its potentials shift by delta relative to the rest. Only
-        // differences matter, so the smaller of T_q and the rest is shifted:
-        // the two are enumerated in lockstep until one is exhausted.
-        const int q = leave_node;
-        const int r = on_v ? v : u;
-        const int o = on_v ? u : v;
+        // the subtree S of q is cut at its parent and hung at the endpoint u_in
+        // of a inside S below the other endpoint v_in; its potentials shift by
+        // delta (only differences matter: the smaller of S and the rest moves)
+        const int u_in = on_v ? v : u, v_in = on_v ? u : v;
         const int64_t delta = on_v ? rc(a) : -rc(a);
+        const int p_out = parent[q];
+        const int nS = succ[q];
         in_tree[parc[q]] = 0;
         in_tree[a] = 1;
-        remove_child(parent[q], q);
-        {
-            s1.clear(); s2.clear(); l1.clear(); l2.clear();
-            s1.push_back(q);
-            s2.push_back(0);
-            int done = 0;
-            while (!done) {
-                if (!s1.empty()) {
-                    int z = s1.back(); s1.pop_back(); l1.push_back(z);
-                    for (int c = first_child[z]; c >= 0; c = next_sib[c]) s1.push_back(c);
-                } else done = 1;
-                if (!done) {
-                    if (!s2.empty()) {
-                        int z = s2.back(); s2.pop_back(); l2.push_back(z);
-                        for (int c = first_child[z]; c >= 0; c = next_sib[c]) s2.push_back(c);
-                    } else done = 2;
-                }
+        // stem u_in = w0, w1, ..., wk = q (old ancestors of u_in inside S)
+        stem.clear();
+        for (int z = u_in; z != q; z = parent[z]) stem.push_back(z);
+        stem.push_back(q);
+        const int k = (int)stem.size() - 1;
+        // 1. take S out of the thread (old links), fix sizes / last nodes above it
+        const int lastS = last[q], before = rev_thread[q], after = thread[lastS];
+        thread[before] = after;
+        rev_thread[after] = before;
+        for (int z = p_out; z != join; z = parent[z]) succ[z] -= nS;
+        for (int z = p_out; z >= 0 && last[z] == lastS; z = parent[z]) last[z] = before;
+        // 2. the new preorder of S rooted at w0: the old block of w0, then for
+        //    i = 1..k the rest of w_i's old block (the part before w_{i-1}'s
+        //    block, then the part after it). All old links are read first.
+        seg.resize(3 * (size_t)(k + 1));
+        for (int i = 1; i <= k; ++i) {
+            const int wi = stem[i], wp = stem[i - 1];
+            seg[3 * i] = rev_thread[wp];                                  // end of the part before
+            seg[3 * i + 1] = last[wp] != last[wi] ? thread[last[wp]] : -1;  // start of the part after
+            seg[3 * i + 2] = last[wi];                                    // its end
+        }
+        int tailS = last[stem[0]];
+        for (int i = 1; i <= k; ++i) {
+            const int wi = stem[i];
+            thread[tailS] = wi;
+            rev_thread[wi] = tailS;
+            tailS = seg[3 * i];
+            if (seg[3 * i + 1] >= 0) {
+                thread[tailS] = seg[3 * i + 1];
+                rev_thread[seg[3 * i + 1]] = tailS;
+                tailS = seg[3 * i + 2];
             }
-            if (done == 1) {
-                for (int z : l1) pot[z] += delta;
-            } else {
-                for (int z : l2) pot[z] -= delta;
-            }
+        }
+        // sizes and last nodes of the stem, parents / tree arcs reversed along it
+        const int nk = succ[q];
+        for (int i = k; i >= 1; --i) succ[stem[i]] = nk - succ[stem[i - 1]];
+        succ[stem[0]] = nk;
+        for (int i = 0; i <= k; ++i) last[stem[i]] = tailS;
+        for (int i = k; i >= 1; --i) {
+            parent[stem[i]] = stem[i - 1];
+            parc[stem[i]] = parc[stem[i - 1]];
+        }
+        parent[u_in] = v_in;
+        parc[u_in] = a;
+        // 3. S after v_in in the thread; sizes / last nodes above v_in
+        const int nxt = thread[v_in];
+        const bool v_leaf = last[v_in] == v_in;
+        thread[v_in] = u_in;
+        rev_thread[u_in] = v_in;
+        thread[tailS] = nxt;
+        rev_thread[nxt] = tailS;
+        for (int z = v_in; z != join; z = parent[z]) succ[z] += nS;
+        if (v_leaf)
+            for (int z = v_in; z >= 0 && last[z] == v_in; z = parent[z]) last[z] = tailS;
+        // 4. potentials
+        if (2 * nS <= nn) {
+            int z = u_in;
+            for (int t = 0; t < nS; ++t, z = thread[z]) pot[z] += delta;
+        } else {
+            int z = thread[tailS];
+            for (int t = 0; t < nn - nS; ++t, z = thread[z]) pot[z] -= delta;
+        }
 #ifdef MCF_STATS
-            st_refresh += l1.size() + l2.size();
+        st_refresh += std::min(nS, nn - nS);
 #endif
-        }
-        // path r -> q, reversed
-        path.clear();
-        for (int z = r; z != q; z = parent[z]) path.push_back(z);
-        path.push_back(q);
-        for (size_t t = 0; t + 1 < path.size(); ++t) remove_child(path[t + 1], path[t]);
-        arcs.resize(path.size());
-        for (size_t t = 0; t + 1 < path.size(); ++t) arcs[t] = parc[path[t]];
-        for (size_t t = 0; t + 1 < path.size(); ++t) {
-            int z0 = path[t], z1 = path[t + 1];
-            parent[z1] = z0;
-            parc[z1] = arcs[t];
-            add_child(z0, z1);
-        }
-        parent[r] = o;
-        parc[r] = a;
-        add_child(o, r);
         ++pivots;
         return true;
     }
@@ -283,11 +319,6 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
     const int nn = ns.nn;
     ns.parent.assign(nn, -1);
     ns.parc.assign(nn, -1);
-    ns.stamp.assign(nn, 0);
-    ns.pos.assign(nn, 0);
-    ns.first_child.assign(nn, -1);
-    ns.next_sib.assign(nn, -1);
-    ns.prev_sib.assign(nn, -1);
     ns.pot.assign(nn, 0);
     ns.in_tree.assign(ns.na, 0);
     // spanning tree of the cell grid by breadth-first search from cell 0, over
@@ -323,19 +354,18 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
             ns.parent[ti] = p;
             ns.parc[ti] = via[i];
             ns.in_tree[via[i]] = 1;
-            ns.add_child(p, ti);
         }
         ns.in_tree[self] = 1;
         if (idx == 0) {  // root s_0; t_0 hangs below it
             ns.parent[ti] = i;
             ns.parc[ti] = self;
-            ns.add_child(i, ti);
+            ns.root = i;
         } else {
             ns.parent[i] = ti;
             ns.parc[i] = self;
-            ns.add_child(ti, i);
         }
     }
+    ns.build_thread();
     *out = S;
     return DD_OK;
 }
@@ -356,7 +386,7 @@ int mcf_solve(McfSolver* S, const double* cbar, double* w, double* value, int32_
             int a = S->arc_of[5 * i + k];
             if (a >= 0) ns.cost[a] = (int64_t)std::llround(cbar[5 * i + k] * cscale);
         }
-    // re-price the current tree from its root (node 0 = s_0 never has a parent)
+    // re-price the current tree from its root
     ns.price_tree();
     const int64_t piv0 = ns.pivots;
     if (!ns.run()) return DD_ERR_FLOW;
