@@ -610,16 +610,20 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // Every log-sum-exp is first taken with the previous iteration's value of
         // the same line as the shift (one pass); lines whose sum over- or
         // underflows, and all lines of the first iteration, use the exact max.
-        const double tolm = A.tol * A.mJ[J];
+        // the error bookkeeping is FP32: it only decides when to stop, and GB300's
+        // FP64 rate (1/64 of FP32) would make a per-iteration FP64 sum by every
+        // thread a large share of an iteration of a big cell
+        const float tolm = (float)(A.tol * A.mJ[J]);
+        const float eps_tolm = (float)(A.eps_tol * A.mJ[J]);
         int it = 0;
-        double err = 0.0, best = 1e300;
+        float err = 0.f, best = 3.0e38f;
         int since = 0;
         bool stalled = false, first = true;
         // over-relaxation of the X-update (same fixed point): a <- a + w (X(b) - a).
         // Adaptive: plain for the first iterations, then w from the observed
         // contraction r of the error, w = 2 / (1 + sqrt(1 - r)) (Young's rule).
         float om = A.omega > 1.f ? A.omega : 1.f;
-        double err_prev = 0.0, err_mark = 0.0;
+        float err_prev = 0.f, err_mark = 0.f;
         int om_start = 5;
         // threads per line of the X-update stage 2 (a power of two, lanes adjacent)
         int P2 = 1;
@@ -784,24 +788,25 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 }
             }
             for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
-            if (lane == 0) S.red[wid] = (double)e_loc;
+            float* const redf = reinterpret_cast<float*>(S.red);
+            if (lane == 0) redf[wid] = e_loc;
             __syncthreads();
-            err = 0.0;
-            for (int k = 0; k < (NT >> 5); ++k) err += S.red[k];
+            err = 0.f;
+            for (int k = 0; k < (NT >> 5); ++k) err += redf[k];
             first = false;
             // stall: no 1% improvement for 64 iterations while already within
             // 50 tol (the FP32 rounding floor of this cell has been reached)
-            if (err < 0.99 * best) { best = err; since = 0; } else ++since;
-            stalled = A.fixed_iters <= 0 && since >= 64 && err <= 50.0 * tolm;
+            if (err < 0.99f * best) { best = err; since = 0; } else ++since;
+            stalled = A.fixed_iters <= 0 && since >= 64 && err <= 50.f * tolm;
             if (A.omega < 0.f) {
-                if (om > 1.f && err > 1.5 * err_prev) {  // diverging: back to plain steps
+                if (om > 1.f && err > 1.5f * err_prev) {  // diverging: back to plain steps
                     om = 1.f;
                     om_start = it + 5;
                 } else if (it == om_start) {
                     err_mark = err;
-                } else if (it == om_start + 5 && err_mark > 0.0) {
-                    const double r = fmin(pow(err / err_mark, 0.2), 0.999);
-                    om = (float)fmin(1.85, fmax(1.0, 2.0 / (1.0 + sqrt(1.0 - r))));
+                } else if (it == om_start + 5 && err_mark > 0.f) {
+                    const float r = fminf(powf(err / err_mark, 0.2f), 0.999f);
+                    om = fminf(1.85f, fmaxf(1.f, 2.f / (1.f + sqrtf(1.f - r))));
                 }
             }
             err_prev = err;
@@ -809,7 +814,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 // coarse level: refine once its error is within eps_tol (or it
                 // stalls), a <- log2 mu + f (a' - log2 mu) with the newest X dual,
                 // tables at the finer scale, exact shifts on the next iteration
-                if (err <= A.eps_tol * A.mJ[J] || stalled || it >= A.max_iter) {
+                if (err <= eps_tolm || stalled || it >= A.max_iter) {
                     // out of iterations: straight to the target eps (one last
                     // iteration there keeps the outputs consistent)
                     float f = A.eps_factor;
@@ -825,7 +830,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     build_tables(S, A.k2d * (double)lev_scale, h, w, bs, hx, wx, uc1, uc2, vc1, vc2, l1, l2);
                     for (int q = tid; q < hx * bs; q += NT) S.T[q] = DD_NEG;
                     first = true;
-                    best = 1e300;
+                    best = 3.0e38f;
                     since = 0;
                     stalled = false;
                     __syncthreads();
