@@ -71,7 +71,8 @@ extern "C" {
                                      last half-iteration for dd_get_prebalance     */
 #define DD_FLAG_NO_GRAPH 4 /* dd_step runs its steps one by one instead of
                               replaying a captured CUDA graph                     */
-#define DD_FLAG_COLLECT 2 /* compute the warm-start network's inputs before, and
+#define DD_FLAG_COLLECT 2
+#define DD_FLAG_TRACE 8 /* record per-cell solve timelines for dd_get_trace       */ /* compute the warm-start network's inputs before, and
                              its training targets after, every cell solve, for
                              dd_collect_cells (requires cell_size 4)              */
 
@@ -293,6 +294,11 @@ int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
  * state. The chosen configuration is in *out (may be NULL).
  */
 int dd_autotune(dd_ctx* ctx, const char* cache_path, dd_tuning* out);
+
+/* With DD_FLAG_TRACE: the timeline of the last solve of every cell of `part`,
+ * ncell x 4 int64 (HOST): start and end of the solve (ns, the GPU's global
+ * timer), the SM it ran on, its CTA size. */
+int dd_get_trace(dd_ctx* ctx, int part, int64_t* trace);
 
 /* dd_step graph counters since dd_init: graphs captured, iterations replayed
  * from a graph, replays finished step by step after a capacity overflow. */

@@ -25,7 +25,7 @@ DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_MAXITER = 0, -1, -2, -3, -4
 DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
 DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
-DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH = 1, 2, 4
+DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 
 EXPORTS = [
@@ -35,7 +35,7 @@ EXPORTS = [
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
     "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
-    "dd_get_tuning", "dd_set_tuning", "dd_autotune",
+    "dd_get_tuning", "dd_set_tuning", "dd_autotune", "dd_get_trace",
 ]
 
 
@@ -125,6 +125,7 @@ def load():
         "dd_get_tuning": (C.c_int, [vp, P(dd_tuning)]),
         "dd_set_tuning": (C.c_int, [vp, P(dd_tuning)]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, P(dd_tuning)]),
+        "dd_get_trace": (C.c_int, [vp, C.c_int, P(C.c_int64)]),
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
@@ -323,6 +324,14 @@ def dd_get_graph_counters(ctx):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load().dd_get_graph_counters(ctx, C.byref(a), C.byref(b), C.byref(c)), "dd_get_graph_counters")
     return dict(captures=a.value, replays=b.value, fallbacks=c.value)
+
+
+def dd_get_trace(ctx, part, ncell):
+    """Per-cell solve timeline of the last half-iteration on `part`: (ncell, 4)
+    int64 (start ns, end ns, SM, CTA size)."""
+    t = np.zeros((ncell, 4), dtype=np.int64)
+    _check(load().dd_get_trace(ctx, int(part), _ptr(t, P(C.c_int64))), "dd_get_trace")
+    return t
 
 
 def dd_get_tuning(ctx):
@@ -542,6 +551,9 @@ class DomDec:
 
     def tuning(self):
         return dd_get_tuning(self.ctx)
+
+    def trace(self, part):
+        return dd_get_trace(self.ctx, part, self.ncell[part])
 
     def set_tuning(self, threads, small_area, small_side):
         dd_set_tuning(self.ctx, threads, small_area, small_side)

@@ -287,6 +287,7 @@ void dd_destroy(dd_ctx* c) {
     if (c->gstream) cudaStreamDestroy(c->gstream);
     dfree(c->d_feat); dfree(c->d_pred); dfree(c->d_targ); dfree(c->d_full[0]); dfree(c->d_full[1]);
     dfree(c->d_pred_old[0]); dfree(c->d_pred_old[1]);
+    dfree(c->d_trace[0]); dfree(c->d_trace[1]);
     if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
     if (c->h_tot) cudaFreeHost(c->h_tot);
@@ -449,6 +450,14 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         if (cudaMemsetAsync(c->d_guard, 0, 4 * sizeof(int), c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         if (cudaMallocHost((void**)&c->h_guard, 4 * sizeof(int)) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
         TRY(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        if (c->opt.flags & DD_FLAG_TRACE)
+            for (int p = 0; p < 2; ++p) {
+                TRY(dmalloc(&c->d_trace[p], 4 * (size_t)c->part[p].ncell));
+                if (cudaMemsetAsync(c->d_trace[p], 0, 4 * sizeof(long long) * c->part[p].ncell, c->stream) != cudaSuccess) {
+                    rc = DD_ERR_CUDA;
+                    goto fail;
+                }
+            }
         for (int p = 0; p < 2; ++p) {
             TRY(dmalloc(&c->d_corder[p], 3 * (size_t)c->part[p].ncell));
             TRY(dmalloc(&c->d_ccount[p], 4));
@@ -1292,6 +1301,14 @@ int dd_debug_cell(dd_ctx* c, int part, int J, float* a, float* b, float* gauge, 
         for (int r = 0; r < ch[CH_H]; ++r)
             RET(d2h(b + (size_t)r * ch[CH_W], P.comp_b + comp + (size_t)r * ch[CH_STRIDE], ch[CH_W], c->stream));
     }
+    CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
+int dd_get_trace(dd_ctx* c, int part, int64_t* trace) {
+    if (!c || !trace || part < 0 || part > 1) return DD_ERR_ARG;
+    if (!(c->opt.flags & DD_FLAG_TRACE)) return DD_ERR_STATE;
+    RET(d2h(reinterpret_cast<long long*>(trace), c->d_trace[part], 4 * (size_t)c->part[part].ncell, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DD_OK;
 }

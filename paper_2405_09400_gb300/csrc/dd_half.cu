@@ -238,6 +238,7 @@ struct HalfArgs {
     // graph mode
     const int* guard;   // non-zero: a buffer of this iteration would overflow, skip all work
     const int* count;   // cells in `order` (device), instead of ncell
+    long long* trace;   // DD_FLAG_TRACE: per cell start / end (ns, globaltimer), SM, CTA size
     // capacities (floats) of the pools the kernels write: a cell whose slots would
     // reach beyond them is skipped and counted in status[4] (never expected)
     long long comp_cap, out_cap, gscr_cap, pre_cap;
@@ -453,6 +454,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const int t = S.ctl[0];
         if (t >= ncell) break;
         const int J = A.order[t];
+        unsigned long long t_start = 0;
+        if (A.trace && tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int32_t* xb = A.xblk + XB_N * J;
         const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
         const int32_t* ch = A.chdr + CH_N * J;
@@ -904,6 +907,17 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             gg[0] = d1; gg[1] = d2; gg[2] = l1; gg[3] = l2;
             gg[4] = uc1; gg[5] = uc2; gg[6] = vc1; gg[7] = vc2;
             A.iters[J] = it;
+            if (A.trace) {
+                unsigned long long t_end;
+                unsigned smid;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+                long long* tr = A.trace + 4LL * J;
+                tr[0] = (long long)t_start;
+                tr[1] = (long long)t_end;
+                tr[2] = (long long)smid;
+                tr[3] = (long long)blockDim.x;
+            }
             A.err[J] = err;
             A.Ecell[J] = A.eps * eloc[0];
         }
@@ -1440,6 +1454,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.queue = c->d_queue; A.status = c->d_status + 8 * c->status_slot;
     A.guard = c->capturing ? c->d_guard : nullptr;
     A.count = nullptr;
+    A.trace = (c->opt.flags & DD_FLAG_TRACE) ? c->d_trace[part] : nullptr;
     A.eps_levels = c->opt.eps_levels;
     A.eps_factor = (float)c->opt.eps_factor;
     A.eps_tol = c->opt.eps_tol;

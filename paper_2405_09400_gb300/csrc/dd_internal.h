@@ -163,6 +163,7 @@ struct dd_ctx {
     float* d_pred_old[2] = {nullptr, nullptr};  // per partition: the outputs used by its last solve
     float* d_targ = nullptr;     // maxcell x DD_MLP_NOUT
     int32_t* d_full[2] = {nullptr, nullptr};  // per partition: cells with a full 8 x 8 block
+    long long* d_trace[2] = {nullptr, nullptr};  // DD_FLAG_TRACE: ncell x 4 per partition
     int n_full[2] = {0, 0};
 };
 

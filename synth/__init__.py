@@ -16,6 +16,8 @@ from .measures import (  # noqa: F401
     WORKLOADS,
 )
 from .couplings import (  # noqa: F401
+    coarsen,
+    prolongate,
     knothe_rosenblatt,
     product_coupling,
     boxes_from_coupling,

@@ -94,3 +94,90 @@ def boxes_from_coupling(shape, s: int, x, y, mass):
         np.add.at(arr, (r - o1, c - o2), m)
         boxes.append((o1, o2, arr))
     return boxes
+
+
+def coarsen(a: np.ndarray) -> np.ndarray:
+    """2 x 2 pixel sums (a measure on an N x N grid -> N/2 x N/2)."""
+    n1, n2 = a.shape
+    return a.reshape(n1 // 2, 2, n2 // 2, 2).sum(axis=(1, 3))
+
+
+def prolongate(boxes_c, mu, nu, s: int, noise: float = 0.01, seed: int = 0, tol: float = 1e-13,
+               max_sweeps: int = 500, trunc: float = 0.0):
+    """A fine initial plan from a coarse one (input recipe of the large 1024 x 1024
+    configuration). boxes_c: basic-cell Y-marginals [(o1, o2, array)] of a plan
+    for the 2 x 2-coarsened measures (coarsen(mu), coarsen(nu)) with the same
+    cell size s; mu, nu the fine measures. Parent basic cell i -> its 4 children
+    i' and coarse pixel y -> its 4 fine pixels y':
+        nu_i'(y') = (m_i' / m_i) nu_i(parent(y')) nu(y') / coarsen(nu)(parent(y')),
+    each entry times (1 + noise u), u ~ U[-1, 1] (seeded), then iterative
+    proportional fitting on that support (rows: basic masses m_i', columns: nu)
+    until both L1 errors are below tol; optionally the entries below `trunc`
+    dropped and the rows scaled back to m_i' (the dropped mass then shows in the
+    Y error). Returns [(o1, o2, array)] on minimal boxes."""
+    rng = np.random.default_rng(seed)
+    N1, N2 = mu.shape
+    n2 = N2 // s
+    nc2 = (N2 // 2) // s
+    m = mu.reshape(N1 // s, s, n2, s).sum(axis=(1, 3)).reshape(-1)
+    nuc = coarsen(nu)
+    # packed fine entries: cell index, pixel index, value
+    cells, pix, vals = [], [], []
+    for ic, (o1, o2, a) in enumerate(boxes_c):
+        a = np.asarray(a, dtype=np.float64)
+        if a.size == 0:
+            continue
+        bi, bj = divmod(ic, nc2)
+        mi = m.reshape(N1 // s, n2)[2 * bi:2 * bi + 2, 2 * bj:2 * bj + 2].reshape(-1)
+        kids = np.array([(2 * bi + di) * n2 + 2 * bj + dj for di in (0, 1) for dj in (0, 1)])
+        y1 = 2 * (o1 + np.arange(a.shape[0]))
+        y2 = 2 * (o2 + np.arange(a.shape[1]))
+        F1 = (y1[:, None] + np.array([0, 1])[None, :]).reshape(-1)   # fine rows
+        F2 = (y2[:, None] + np.array([0, 1])[None, :]).reshape(-1)
+        up = np.kron(a, np.ones((2, 2)))                               # nu_i(parent(y'))
+        ratio = nu[np.ix_(F1, F2)] / np.kron(nuc[o1:o1 + a.shape[0], o2:o2 + a.shape[1]], np.ones((2, 2)))
+        base = up * ratio
+        P = (F1[:, None] * N2 + F2[None, :]).reshape(-1)
+        for k, c in enumerate(kids):
+            v = (mi[k] / mi.sum()) * base.reshape(-1)
+            keep = v > 0
+            cells.append(np.full(keep.sum(), c))
+            pix.append(P[keep])
+            vals.append(v[keep])
+    cell = np.concatenate(cells)
+    pix = np.concatenate(pix)
+    val = np.concatenate(vals) * (1.0 + noise * rng.uniform(-1.0, 1.0, size=sum(len(v) for v in vals)))
+    nuf = nu.reshape(-1)
+    for _ in range(max_sweeps):
+        rs = np.bincount(cell, weights=val, minlength=len(m))
+        val *= (m / rs)[cell]
+        cs = np.bincount(pix, weights=val, minlength=nuf.size)
+        ex = np.abs(rs - m).sum()
+        val *= np.where(cs > 0, nuf / np.where(cs > 0, cs, 1.0), 1.0)[pix]
+        rs2 = np.bincount(cell, weights=val, minlength=len(m))
+        if np.abs(rs2 - m).sum() < tol and ex < tol:
+            break
+    # drop entries below trunc, then the rows back to their masses (the dropped
+    # mass, <= trunc per entry, goes to the Y error)
+    if trunc > 0.0:
+        val[val < trunc] = 0.0
+        rs = np.bincount(cell, weights=val, minlength=len(m))
+        val *= np.where(rs > 0, m / np.where(rs > 0, rs, 1.0), 0.0)[cell]
+    out = []
+    order = np.argsort(cell, kind="stable")
+    cell, pix, val = cell[order], pix[order], val[order]
+    starts = np.searchsorted(cell, np.arange(len(m) + 1))
+    for c in range(len(m)):
+        sl = slice(starts[c], starts[c + 1])
+        p, v = pix[sl], val[sl]
+        nz = v > 0
+        p, v = p[nz], v[nz]
+        if p.size == 0:
+            out.append((0, 0, np.zeros((0, 0))))
+            continue
+        r, q = p // N2, p % N2
+        o1, o2 = int(r.min()), int(q.min())
+        arr = np.zeros((int(r.max()) - o1 + 1, int(q.max()) - o2 + 1))
+        np.add.at(arr, (r - o1, q - o2), v)
+        out.append((o1, o2, arr))
+    return out

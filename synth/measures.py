@@ -84,6 +84,11 @@ WORKLOADS = {
     # eps = (1/512)^2, KR init: widely varying bounding-box sizes.
     "uneven512": dict(N=512, K=8, sigma=(0.01, 0.03), floor=1e-5, eps_h2=1.0, s=4,
                       init="kr", tol=1e-5, iters=None, mu_uniform=True),
+    # 1024x1024, 6-component mixtures, floor 1e-5, eps = 2 (1/1024)^2; initial
+    # plan prolongated from a converged plan of the 2x2-coarsened measures
+    # (couplings.prolongate).
+    "dd1024": dict(N=1024, K=6, sigma=(0.05, 0.2), floor=1e-5, eps_h2=2.0, s=4,
+                   init="prolongated", tol=1e-5, iters=None),
 }
 
 

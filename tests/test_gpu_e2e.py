@@ -174,3 +174,57 @@ def test_autotune_restores_state_and_caches(dd, tmp_path):
     assert t2["trials"] == 0 and t2["threads"] == t["threads"] and t2["small_area"] == t["small_area"]
     for g in (a, b, c):
         g.close()
+
+
+def test_trace_records_every_cell(dd):
+    """DD_FLAG_TRACE: every cell of the last half-iteration has a start <= end
+    inside the half-iteration's span, a valid SM index and its CTA size."""
+    mu, nu, eps, p = synth.workload("dd32", 0, N=64)
+    g = dd.DomDec(mu, nu, eps, 4, tol=1e-5, flags=dd.DD_FLAG_TRACE)
+    g.iterate(0)
+    st = g.iterate(1)
+    tr = g.trace(1)
+    assert tr.shape == (g.ncell[1], 4)
+    assert (tr[:, 0] > 0).all() and (tr[:, 1] >= tr[:, 0]).all()
+    assert (tr[:, 1].max() - tr[:, 0].min()) * 1e-6 <= st["ms_total"] + 1.0
+    assert ((tr[:, 2] >= 0) & (tr[:, 2] < 1024)).all() and set(np.unique(tr[:, 3])) <= {128, 256, 512}
+    g.close()
+
+
+def test_dd1024_maximum_size(dd):
+    """The 1024 x 1024 configuration (65536 basic cells), from the
+    Knothe-Rosenblatt coupling: a cold fixed-iteration A half-iteration matches
+    the oracle on sampled cells; the learned, eps-scaled solver in tolerance
+    mode keeps both marginals over one hybrid iteration."""
+    mu, nu, eps, p = synth.workload("dd1024", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    geom = Geometry(1024, 1024, 4)
+    m = geom.basic_masses(mu)
+    K = 40
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, fixed_iters=K, warm=dd.DD_WARM_COLD,
+                  flags=dd.DD_FLAG_KEEP_PREBALANCE)
+    g.iterate(0)
+    pre = g.prebalance()
+    bx = [Box(o1, o2, np.asarray(a)) for o1, o2, a in boxes]
+    cells = geom.partition(0)
+    rng = np.random.default_rng(5)
+    for J in rng.choice(len(cells), 8, replace=False):
+        members = cells[J]
+        nuJ = basic_to_composite(bx, members)
+        res = solve_cell(geom, mu, eps, 1.0 / 1024, members, nuJ, None, 1e-5, 100000, fixed_iters=K)
+        arrs, _ = composite_to_basic(geom, members, nuJ, res)
+        for k, i in enumerate(members):
+            assert np.abs(pre[i][2] - arrs[k]).sum() <= 1e-4 * m[i], (J, i)
+    g.close()
+    from paper_2405_09400_gb300 import warmstart as ws
+
+    params, _ = ws.load_params()
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000, warm=dd.DD_WARM_MLP, weights=params,
+                  eps_levels=2, eps_factor=4.0)
+    sa, sb, sf = g.step(1)
+    assert sa["n_maxiter"] == 0 and sb["n_maxiter"] == 0 and sa["ncell"] == 65536 // 4
+    E, l1x, l1y = g.objective()
+    assert l1x <= 1e-5 and l1y <= 1e-6
+    got = np.array([b[2].sum() for b in g.plan()])
+    assert np.allclose(got, m, rtol=1e-5)
+    g.close()

@@ -64,3 +64,33 @@ def test_basic_masses():
     for i in range(g.nb):
         X = g.cell_pixels(i)
         assert m[i] == pytest.approx(mu[X[:, 0], X[:, 1]].sum(), rel=1e-15)
+
+
+def test_prolongated_plan_is_feasible():
+    """Input recipe of the 1024 x 1024 configuration, at 64 x 64: a plan of the
+    coarsened measures, prolongated with 1 % noise and rebalanced, has both
+    marginals of the fine measures (X to 1e-12 per basic cell, Y to 1e-12 in L1),
+    and every child box lies inside the refinement of its parent's."""
+    import numpy as np
+
+    import synth
+
+    from oracle.hybrid import OracleDD
+
+    mu, nu, eps, p = synth.workload("dd1024", 0, N=64)
+    muc, nuc = synth.coarsen(mu), synth.coarsen(nu)
+    dd = OracleDD(muc, nuc, 4 * eps, 4, tol=1e-7)
+    dd.step()
+    coarse = [(b.o1, b.o2, b.a) for b in dd.boxes]
+    fine = synth.prolongate(coarse, mu, nu, 4, noise=0.01, seed=0)
+    m = mu.reshape(16, 4, 16, 4).sum(axis=(1, 3)).reshape(-1)
+    assert len(fine) == 256
+    Y = np.zeros_like(nu)
+    for i, (o1, o2, a) in enumerate(fine):
+        assert abs(a.sum() - m[i]) <= 1e-12 * m[i]
+        Y[o1:o1 + a.shape[0], o2:o2 + a.shape[1]] += a
+        bi, bj = divmod(i, 16)
+        co1, co2, ca = coarse[(bi // 2) * 8 + bj // 2]
+        assert 2 * co1 <= o1 and o1 + a.shape[0] <= 2 * (co1 + ca.shape[0])
+        assert 2 * co2 <= o2 and o2 + a.shape[1] <= 2 * (co2 + ca.shape[1])
+    assert np.abs(Y - nu).sum() <= 1e-12
