@@ -189,7 +189,10 @@ def run_ours(args):
     arms = set(args.arms.split(","))
     # autotune the cell-kernel launch configuration on this GPU and workload
     tune = None
-    if not args.no_tune:
+    if args.tuning:
+        t = [int(x) for x in args.tuning.split(",")]
+        tune = dict(threads=t[:3], small_area=t[3], small_side=t[4], ms_default=None, ms_best=None, trials=0)
+    elif not args.no_tune:
         tctx = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
                          weights=weights, **SOLVER)
         tctx.step(2, stats=False)
@@ -398,6 +401,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration (no autotuning)")
+    ap.add_argument("--tuning", default="", help="fixed launch configuration t0,t1,t2,small_area,small_side "
+                                               "instead of autotuning (profiling runs)")
     ap.add_argument("--arms", default="plain,warm,affine,eager",
                     help="comma list of arms to time besides the learned warm start (plain, affine, eager)")
     args = ap.parse_args()
