@@ -101,6 +101,11 @@ typedef struct dd_options {
                             solution is that of eps. 0 (default) = plain solve         */
     double eps_factor;   /* f > 1; 4                                                    */
     double eps_tol;      /* a coarse level ends at L1 X error <= eps_tol mu(X_J); 1e-3 */
+    double tol_share;    /* s in [0, 1]: cell J stops at L1 X error
+                              <= tol ((1 - s) mu(X_J) + s mu(X) / #cells),
+                            budgets that sum to tol mu(X) over the partition, the
+                            bound of the paper's batch stopping criterion (Section 5,
+                            "Stopping criterion"); 0 (default) = tol mu(X_J) per cell */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */
@@ -276,9 +281,18 @@ typedef struct dd_tuning {
     double ms_default; /* dd_autotune: time of the trial run with the defaults   */
     double ms_best;    /* and with the chosen configuration (ms)                 */
     int32_t trials;    /* configurations timed (0: taken from the cache file)    */
+    int32_t cl_size;   /* 2 or 4: the largest-work cells of the large class are
+                          solved by thread-block clusters of this many CTAs (of
+                          threads[0] threads, 256 or 512), one cluster per cell;
+                          1 = off                                                 */
+    int32_t cl_cells;  /* at most this many cells per half-iteration on clusters
+                          (and at most #SMs / cl_size): whole quarter-octave
+                          buckets of the work key h w (previous iterations), from
+                          the top, boxes of at least 1024 entries                */
 } dd_tuning;
 
-/* Defaults: threads {256, 128, 256}, small_area 1536, small_side 64. */
+/* Defaults: threads {256, 128, 256}, small_area 1536, small_side 64, clusters
+   off. */
 int dd_get_tuning(dd_ctx* ctx, dd_tuning* t);
 int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
 

@@ -47,7 +47,8 @@ class dd_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("trunc", C.c_double),
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
                 ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double),
-                ("eps_levels", C.c_int32), ("eps_factor", C.c_double), ("eps_tol", C.c_double)]
+                ("eps_levels", C.c_int32), ("eps_factor", C.c_double), ("eps_tol", C.c_double),
+                ("tol_share", C.c_double)]
 
 
 class dd_stats(C.Structure):
@@ -70,11 +71,13 @@ class dd_flow_stats(C.Structure):
 
 class dd_tuning(C.Structure):
     _fields_ = [("threads", C.c_int32 * 3), ("small_area", C.c_int32), ("small_side", C.c_int32),
-                ("ms_default", C.c_double), ("ms_best", C.c_double), ("trials", C.c_int32)]
+                ("ms_default", C.c_double), ("ms_best", C.c_double), ("trials", C.c_int32),
+                ("cl_size", C.c_int32), ("cl_cells", C.c_int32)]
 
     def as_dict(self):
         return dict(threads=list(self.threads), small_area=self.small_area, small_side=self.small_side,
-                    ms_default=self.ms_default, ms_best=self.ms_best, trials=self.trials)
+                    ms_default=self.ms_default, ms_best=self.ms_best, trials=self.trials, cl_size=self.cl_size,
+                    cl_cells=self.cl_cells)
 
 
 class DDError(RuntimeError):
@@ -340,10 +343,17 @@ def dd_get_tuning(ctx):
     return t.as_dict()
 
 
-def dd_set_tuning(ctx, threads, small_area, small_side):
+def dd_set_tuning(ctx, threads, small_area, small_side, cl_size=None, cl_cells=None):
+    """Launch configuration of the cell kernels; cl_size / cl_cells None keep the
+    context's current cluster setting."""
     t = dd_tuning()
+    _check(load().dd_get_tuning(ctx, C.byref(t)), "dd_get_tuning")
     t.threads = (C.c_int32 * 3)(*threads)
     t.small_area, t.small_side = int(small_area), int(small_side)
+    if cl_size is not None:
+        t.cl_size = int(cl_size)
+    if cl_cells is not None:
+        t.cl_cells = int(cl_cells)
     _check(load().dd_set_tuning(ctx, C.byref(t)), "dd_set_tuning")
 
 
@@ -555,8 +565,8 @@ class DomDec:
     def trace(self, part):
         return dd_get_trace(self.ctx, part, self.ncell[part])
 
-    def set_tuning(self, threads, small_area, small_side):
-        dd_set_tuning(self.ctx, threads, small_area, small_side)
+    def set_tuning(self, threads, small_area, small_side, cl_size=None, cl_cells=None):
+        dd_set_tuning(self.ctx, threads, small_area, small_side, cl_size, cl_cells)
 
     def autotune(self, cache_path=None):
         return dd_autotune(self.ctx, cache_path)

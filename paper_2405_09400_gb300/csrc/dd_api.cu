@@ -244,6 +244,7 @@ void dd_default_options(dd_options* o) {
     o->eps_levels = 0;
     o->eps_factor = 4.0;
     o->eps_tol = 1e-3;
+    o->tol_share = 0.0;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -297,7 +298,9 @@ void dd_destroy(dd_ctx* c) {
         if (e) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->side2) cudaStreamDestroy(c->side2);
     delete c;
 }
 
@@ -327,11 +330,13 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
     c->tune.threads[0] = 256; c->tune.threads[1] = 128; c->tune.threads[2] = 256;
     c->tune.small_area = 1536; c->tune.small_side = 64;
+    c->tune.cl_size = 1; c->tune.cl_cells = 0;
     const bool learned = c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT);
     if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
         c->opt.eps_levels < 0 || c->opt.eps_levels > 8 ||
-        (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4)) {
+        (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4) ||
+        !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0)) {
         delete c;
         return DD_ERR_ARG;
     }
@@ -424,6 +429,9 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             std::vector<double> mJ;
             build_part(c, p, members, xblk, mJ);
             P.ncell = (int)mJ.size();
+            double msum = 0.0;
+            for (double x : mJ) msum += x;
+            P.mbar = P.ncell > 0 ? msum / P.ncell : 0.0;
             P.h_members = members;
             P.h_xblk = xblk;
             std::vector<int32_t> order(P.ncell);
@@ -480,8 +488,10 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
             rc = DD_ERR_CUDA;
             goto fail;
         }
@@ -588,6 +598,12 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st, int slot = 0, cudaEvent
 
 }  // extern "C"
 
+// most cells per half-iteration solved by clusters (0: clusters off)
+static int cluster_cap(dd_ctx* c) {
+    if (c->tune.cl_size < 2 || (c->opt.flags & DD_FLAG_COLLECT)) return 0;
+    return std::max(0, std::min(c->tune.cl_cells, c->nsm / half_cluster_size(c->tune.cl_size)));
+}
+
 int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     DevPart& P = c->part[part];
     CK(cudaEventRecord(c->ev[0], c->stream));
@@ -624,8 +640,8 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     std::vector<double> key(P.ncell);
     // classes: 0 large boxes (second stream), 1 small boxes, 2 boxes beyond shared
     // memory (their two box arrays in global scratch, also on the second stream)
-    std::vector<int32_t> cls_cells[3];
-    long long dims[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [class][area, h, w]
+    std::vector<int32_t> cls_cells[4];
+    long long dims[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [class][area, h, w]
     std::vector<long long> goff(P.ncell, -1);
     long long gtot = 0;
     // largest box area a shared-memory launch can hold next to the tables of the
@@ -662,21 +678,56 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     c->seen.gscr = std::max(c->seen.gscr, gtot);
     c->seen.n0 = std::max(c->seen.n0, (long long)cls_cells[0].size());
     c->seen.n2 = std::max(c->seen.n2, (long long)cls_cells[2].size());
+    // class 3: the largest-work cells of classes 0 and 2 on thread-block clusters,
+    // by the rule k_classify applies in captured graphs (whole quarter-octave key
+    // buckets from the top, at most cluster_cap cells)
+    const int ccap = cluster_cap(c);
+    if (ccap > 0) {
+        std::vector<int> fbk(P.ncell, -1);
+        int cntf[192] = {0};
+        for (int k : {0, 2})
+            for (int32_t J : cls_cells[k]) {
+                const long long h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
+                if (h * w < kClusterMinArea) continue;
+                int bk = 0, fb = 0;
+                cluster_key_bucket(h * w * std::max(1, itp[J]), bk, fb);
+                fbk[J] = fb;
+                ++cntf[fb];
+            }
+        int cum = 0, bstar = 192;
+        for (int f = 191; f >= 0; --f) {
+            if (cntf[f] == 0) continue;
+            if (cum + cntf[f] > ccap) break;
+            cum += cntf[f];
+            bstar = f;
+        }
+        if (cum > 0) {
+            for (int k : {0, 2}) {
+                std::vector<int32_t> keep;
+                for (int32_t J : cls_cells[k]) (fbk[J] >= bstar ? cls_cells[3] : keep).push_back(J);
+                cls_cells[k].swap(keep);
+            }
+            for (int32_t J : cls_cells[3]) {
+                const int h = ch[CH_N * J + CH_H], w = ch[CH_N * J + CH_W];
+                if (goff[J] < 0) dims[3][0] = std::max(dims[3][0], (long long)h * half_padw(w));
+                dims[3][1] = std::max(dims[3][1], (long long)h);
+                dims[3][2] = std::max(dims[3][2], (long long)w);
+            }
+        }
+    }
     auto by_key = [&](int32_t x, int32_t y) { return key[x] > key[y]; };
     std::vector<int32_t> order;
-    size_t cls_off[3];
-    for (int k = 0; k < 3; ++k) {
+    size_t cls_off[4];
+    for (int k = 0; k < 4; ++k) {
         std::stable_sort(cls_cells[k].begin(), cls_cells[k].end(), by_key);
         cls_off[k] = order.size();
         order.insert(order.end(), cls_cells[k].begin(), cls_cells[k].end());
     }
     RET(h2d(P.order, order.data(), order.size(), c->stream));
-    if (!cls_cells[2].empty()) {
-        RET(ensure_floats(c, &c->d_gscr, &c->gscr_cap, (size_t)gtot));
-        RET(h2d(c->d_goff, goff.data(), goff.size(), c->stream));
-    }
-    size_t smem_c[3] = {0, 0, 0};
-    for (int k = 0; k < 3; ++k) {
+    if (gtot > 0) RET(ensure_floats(c, &c->d_gscr, &c->gscr_cap, (size_t)gtot));
+    if (!cls_cells[2].empty() || !cls_cells[3].empty()) RET(h2d(c->d_goff, goff.data(), goff.size(), c->stream));
+    size_t smem_c[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) {
         if (cls_cells[k].empty()) continue;
         smem_c[k] = half_smem_bytes(c, k == 2 ? 0 : dims[k][0], dims[k][1], dims[k][2]);
         if (smem_c[k] > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
@@ -691,6 +742,16 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     if (side_used) {
         CK(cudaEventRecord(c->ev_fork, c->stream));
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    if (!cls_cells[3].empty()) {  // clusters first, on their own high-priority stream
+        CK(cudaEventRecord(c->ev_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+        const int n = (int)cls_cells[3].size();
+        const int ncl = std::max(1, std::min(n, c->nsm / half_cluster_size(c->tune.cl_size)));
+        RET(launch_half_cluster(c, part, P.order + cls_off[3], n, c->d_queue + 3, dims[3], thr_c[0],
+                                c->tune.cl_size, smem_c[3], ncl, c->side2));
+        c->n_launch += 1;
+        CK(cudaEventRecord(c->ev_join2, c->side2));
     }
     for (int k : {2, 0, 1}) {
         if (cls_cells[k].empty()) continue;
@@ -709,13 +770,14 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         CK(cudaEventRecord(c->ev_join, c->side));
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
+    if (!cls_cells[3].empty()) CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
     if (c->opt.warm == DD_WARM_MLP && with_c2b)
         CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
                            cudaMemcpyDeviceToDevice, c->stream));
     if (with_c2b) {
-        const long long dall[3] = {std::max({dims[0][0], dims[1][0], dims[2][0]}),
-                                   std::max({dims[0][1], dims[1][1], dims[2][1]}),
-                                   std::max({dims[0][2], dims[1][2], dims[2][2]})};
+        const long long dall[3] = {std::max({dims[0][0], dims[1][0], dims[2][0], dims[3][0]}),
+                                   std::max({dims[0][1], dims[1][1], dims[2][1], dims[3][1]}),
+                                   std::max({dims[0][2], dims[1][2], dims[2][2], dims[3][2]})};
         const size_t sm = c2b_smem_bytes(c, dall[1], dall[2]);
         if (sm > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
         RET(launch_c2b(c, part, dall, sm));
@@ -867,6 +929,7 @@ int graph_prepare(dd_ctx* c) {
     g.smem[0] = half_smem_bytes(c, g.a0, g.h2, g.w2);
     g.smem[2] = 0;
     g.smem_c2b = c2b_smem_bytes(c, g.h2, g.w2);
+    g.cl_cap = cluster_cap(c);
     const int* thr = c->tune.threads;
     for (int k = 0; k < 2; ++k) {
         const int occ = std::max(1, half_occupancy(thr[k], g.smem[k]));
@@ -916,6 +979,13 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     const long long d0[3] = {g.a0, g.h2, g.w2};
     const long long d1[3] = {c->tune.small_area, c->tune.small_side, c->tune.small_side};
     const int* thr = c->tune.threads;
+    if (g.cl_cap > 0) {  // the cluster class, pending first on its own high-priority stream
+        CK(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+        RET(launch_half_cluster(c, part, c->d_corder[part] + 2LL * P.ncell, P.ncell, c->d_queue + 2, d0, thr[0],
+                                c->tune.cl_size, g.smem[0], g.cl_cap, c->side2, c->d_ccount[part] + 2));
+        c->n_launch += 1;
+        CK(cudaEventRecord(c->ev_join2, c->side2));
+    }
     RET(launch_half(c, part, c->d_corder[part], P.ncell, c->d_queue + 0, d0, thr[0], g.smem[0], g.grid[0], c->side,
                     true, c->d_ccount[part] + 0));
     RET(launch_half(c, part, c->d_corder[part] + P.ncell, P.ncell, c->d_queue + 1, d1, thr[1], g.smem[1], g.grid[1],
@@ -923,6 +993,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     c->n_launch += 2;
     CK(cudaEventRecord(c->ev_join, c->side));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (g.cl_cap > 0) CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
     if (c->opt.warm == DD_WARM_MLP)
         CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
                            cudaMemcpyDeviceToDevice, c->stream));

@@ -31,6 +31,7 @@
 //   beta_t/eps = ln2 (b - 2 k2 d.vbar + k2|d|^2/2) - ln nu_J,
 // with d = (block centre) - (box centre) in pixels (the linear part of the cost
 // is absorbed so that the FP32 duals stay small).
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,8 @@
         int r_ = (x);               \
         if (r_ != DD_OK) return r_; \
     } while (0)
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -213,6 +216,7 @@ struct HalfArgs {
     const float* lnnuf;  // ln nu in FP32
     const double* m;
     double tol;
+    double tol_share, mbar;  // stop budget tol ((1 - share) mu(X_J) + share mbar)
     float omega;  // 1: plain Sinkhorn; (1, 2): fixed over-relaxation; < 0: adaptive
     int max_iter, fixed_iters;
     float trunc;
@@ -259,6 +263,8 @@ struct Smem {
     double* red;  // 32 * 16 + 16
     double* B1;   // maxH: min over u1 of the axis-1 kernel at v1 (FP64)
     double* B2;   // BS: min over u2 of the axis-2 kernel at v2
+    double* clx;  // 16: per-CTA sums exchanged within a cluster
+    float* pm;    // 2 * amax: partial X-update log-sums of this CTA's rows (cluster), two buffers
     float* coef;  // 16
     int* ctl;     // 32
     long long end;  // bytes used
@@ -277,6 +283,8 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     d += A.smaxH;
     S.B2 = d;
     d += BS;
+    S.clx = d;
+    d += 16;
     float* f = reinterpret_cast<float*>(((uintptr_t)d + 15) & ~(uintptr_t)15);  // float4 rows
     // every array after this point is read as float4 rows: keep 16-byte offsets
     const int A4 = (A.smaxA + 3) & ~3;
@@ -289,6 +297,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.a = f; f += 2 * A.amax;
     S.lgm = f; f += A.amax;
     S.muxf = f; f += A.amax;
+    S.pm = f; f += 2 * A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     S.end = reinterpret_cast<char*>(f + 32) - base;
@@ -434,12 +443,43 @@ __device__ __noinline__ void write_targets(const HalfArgs& A, const Smem& S, int
     for (int p = tid; p < 256; p += NT) tg[64 + p] -= gm;
 }
 
-template <int NTB>
+// Sum of per-CTA values (valid in every thread) over the CTAs of the cluster, in
+// rank order, so that every CTA gets the same bits. Slots clx[slot, slot + N) of
+// every CTA are read remotely after the cluster barrier; the caller passes a
+// further cluster barrier before those slots are written again.
+template <int N>
+__device__ void cluster_sum_d(double (&v)[N], double* clx, int slot) {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) clx[slot + k] = v[k];
+    }
+    cl.sync();
+    const unsigned nr = cl.num_blocks();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double x = 0.0;
+        for (unsigned r = 0; r < nr; ++r) x += cl.map_shared_rank(clx, r)[slot + k];
+        v[k] = x;
+    }
+}
+
+// The cell solver. CL = 1: one CTA per cell. CL > 1: the CL CTAs of a thread-block
+// cluster solve one cell together (for the few largest cells, which would
+// otherwise run alone on one SM for most of the half-iteration): rank r owns the
+// box rows [h r / CL, h (r + 1) / CL) for the gather, the Y-update stage 2, the
+// X-update stage 1 and the Y side of the outputs; the X-update stage 2 takes a
+// partial log-sum-exp over the own rows, and the partials of all ranks are
+// combined through distributed shared memory after one cluster barrier per
+// iteration, in rank order, so that every CTA holds the same X dual and error and
+// takes the same branches. The small X-side work (Y-update stage 1, tables) is
+// repeated in every CTA.
+template <int NTB, int CL>
 __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
     if (A.guard && *A.guard) return;
     Smem S = carve(smem_raw, A);
-    if (S.end > (long long)dyn_smem_bytes()) {  // host and kernel disagree on the layout
+    if (S.end > (long long)dyn_smem_bytes() || blockDim.x != NTB) {  // host and kernel disagree on the layout
         if (threadIdx.x == 0) atomicAdd(&A.status[2], 1);
         return;
     }
@@ -447,15 +487,25 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     const int tid = threadIdx.x, NT = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
     const int s = A.s;
+    int crank = 0;
+    if constexpr (CL > 1) crank = (int)cg::this_cluster().block_rank();
+    const bool lead = crank == 0;  // writes the per-cell results
 
     while (true) {
-        if (tid == 0) S.ctl[0] = atomicAdd(A.queue, 1);
-        __syncthreads();
-        const int t = S.ctl[0];
+        if constexpr (CL > 1) cg::this_cluster().sync();  // every CTA is done with the previous cell
+        if (tid == 0 && lead) S.ctl[0] = atomicAdd(A.queue, 1);
+        int t;
+        if constexpr (CL > 1) {
+            cg::this_cluster().sync();
+            t = *cg::this_cluster().map_shared_rank(S.ctl, 0);
+        } else {
+            __syncthreads();
+            t = S.ctl[0];
+        }
         if (t >= ncell) break;
         const int J = A.order[t];
         unsigned long long t_start = 0;
-        if (A.trace && tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+        if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int32_t* xb = A.xblk + XB_N * J;
         const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
         const int32_t* ch = A.chdr + CH_N * J;
@@ -469,17 +519,19 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // in a global scratch slot of the cell (L2-resident)
         const long long go = A.goff ? A.goff[J] : -1;
         if (comp + area > A.comp_cap || (go >= 0 && go + 2LL * h * bs > A.gscr_cap)) {
-            if (tid == 0) atomicAdd(&A.status[4], 1);
+            if (tid == 0 && lead) atomicAdd(&A.status[4], 1);
             __syncthreads();
             continue;
         }
+        // box rows of this CTA
+        const int rlo = (h * crank) / CL, rhi = (h * (crank + 1)) / CL;
         float* const lgnu_p = go >= 0 ? A.gscratch + go : S.lgnu;
         float* const b_p = go >= 0 ? A.gscratch + go + (long long)h * bs : S.b;
         int32_t mem[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
         if (nA == 0) {  // no Y mass in the cell: only possible for an infeasible state
-            if (tid == 0) {
+            if (tid == 0 && lead) {
                 atomicAdd(&A.status[1], 1);
                 A.iters[J] = 0;
                 A.err[J] = A.mJ[J];
@@ -498,7 +550,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // per-thread partial sums in FP32 (a few entries each), block sum in FP64;
         // they only choose the change of gauge, which is exact for any value
         float gf[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int v = tid; v < h * bs; v += NT) {
+        for (int v = rlo * bs + tid; v < rhi * bs; v += NT) {
             const int v1 = v / bs, v2 = v - v1 * bs;
             float lg = DD_NEG;
             if (v2 < w) {
@@ -533,6 +585,11 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) gm[k] = gf[k];
         block_sum_d<12>(gm, S.red);
+        if constexpr (CL > 1) {  // nu_J moments over all rows (the mu moments are complete in every CTA)
+            double nv[6] = {gm[0], gm[1], gm[2], gm[3], gm[4], gm[10]};
+            cluster_sum_d<6>(nv, S.clx, 0);
+            gm[0] = nv[0]; gm[1] = nv[1]; gm[2] = nv[2]; gm[3] = nv[3]; gm[4] = nv[4]; gm[10] = nv[5];
+        }
         // Reparametrisation (exact for any choice): origins at the barycentres of
         // mu_J and nu_J, the linear part of the cost absorbed through d, and a
         // per-axis stretch l_k absorbed so that the kernel
@@ -616,7 +673,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // the error bookkeeping is FP32: it only decides when to stop, and GB300's
         // FP64 rate (1/64 of FP32) would make a per-iteration FP64 sum by every
         // thread a large share of an iteration of a big cell
-        const float tolm = (float)(A.tol * A.mJ[J]);
+        const float tolm = (float)(A.tol * ((1.0 - A.tol_share) * A.mJ[J] + A.tol_share * A.mbar));
         const float eps_tolm = (float)(A.eps_tol * A.mJ[J]);
         int it = 0;
         float err = 0.f, best = 3.0e38f;
@@ -637,6 +694,39 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         while (true) {
             ++it;
             // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1, u2) - K2(u2, v2)]
+            // (full 8 x 8 blocks: all operands loaded first, fixed trip counts)
+            if (hx == 8 && wx == 8) {
+                for (int q = tid; q < 8 * w; q += NT) {
+                    const int u1 = q / w, v2 = q - u1 * w;
+                    const float4 a0 = reinterpret_cast<const float4*>(aC + u1 * 8)[0];
+                    const float4 a1 = reinterpret_cast<const float4*>(aC + u1 * 8)[1];
+                    const float* tb = S.tab2 + v2;
+                    float d[8];
+                    d[0] = a0.x - tb[0]; d[1] = a0.y - tb[bs]; d[2] = a0.z - tb[2 * bs]; d[3] = a0.w - tb[3 * bs];
+                    d[4] = a1.x - tb[4 * bs]; d[5] = a1.y - tb[5 * bs]; d[6] = a1.z - tb[6 * bs];
+                    d[7] = a1.w - tb[7 * bs];
+                    float m = first ? 0.f : S.T[u1 * bs + v2];
+                    float sacc = 0.f;
+                    if (!first) {
+                        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 8; k += 2) {
+                            s0 += ex2f(d[k] - m);
+                            s1 += ex2f(d[k + 1] - m);
+                        }
+                        sacc = s0 + s1;
+                    }
+                    if (first || !shift_ok(sacc)) {
+                        m = DD_NEG;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) m = fmaxf(m, d[k]);
+                        sacc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) sacc += ex2f(d[k] - m);
+                    }
+                    S.T[u1 * bs + v2] = m + lg2f(sacc);
+                }
+            } else
             for (int q = tid; q < hx * w; q += NT) {
                 const int u1 = q / w, v2 = q - u1 * w;
                 const float* ar = aC + u1 * wx;
@@ -664,7 +754,53 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             __syncthreads();
             // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - K1(u1, v1)],
             // four adjacent v2 per thread (float4 rows of T, b, log2 nu_J)
-            for (int q = tid; q < h * nq; q += NT) {
+            if (hx == 8 && !first) {  // full blocks after the first iteration: operands loaded first
+                for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
+                    const int v1 = q / nq, g4 = q - v1 * nq;
+                    const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
+                    const float4 bp4 = b4[v1 * bq + g4];
+                    const float* tb = S.tab1 + v1;
+                    float4 T4[8];
+                    float kk[8];
+#pragma unroll
+                    for (int u1 = 0; u1 < 8; ++u1) {
+                        T4[u1] = reinterpret_cast<const float4*>(S.T + u1 * bs)[g4];
+                        kk[u1] = tb[u1 * h];
+                    }
+                    const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                    const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
+                    float m[4], sa[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        m[k] = ln[k] > 0.5f * DD_NEG ? ln[k] - bp[k] : 0.f;
+                        sa[k] = 0.f;
+                    }
+#pragma unroll
+                    for (int u1 = 0; u1 < 8; ++u1) {
+                        sa[0] += ex2f(T4[u1].x - kk[u1] - m[0]);
+                        sa[1] += ex2f(T4[u1].y - kk[u1] - m[1]);
+                        sa[2] += ex2f(T4[u1].z - kk[u1] - m[2]);
+                        sa[3] += ex2f(T4[u1].w - kk[u1] - m[3]);
+                    }
+                    float out[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int v2 = 4 * g4 + k;
+                        if (v2 >= w || !(ln[k] > 0.5f * DD_NEG)) { out[k] = DD_NEG; continue; }
+                        if (!shift_ok(sa[k])) {
+                            float mm = DD_NEG;
+                            for (int u1 = 0; u1 < 8; ++u1) mm = fmaxf(mm, S.T[u1 * bs + v2] - tb[u1 * h]);
+                            float ss = 0.f;
+                            for (int u1 = 0; u1 < 8; ++u1) ss += ex2f(S.T[u1 * bs + v2] - tb[u1 * h] - mm);
+                            m[k] = mm;
+                            sa[k] = ss;
+                        }
+                        out[k] = ln[k] - (m[k] + lg2f(sa[k]));
+                    }
+                    reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
+                }
+            } else
+            for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
                 const int v1 = q / nq, g4 = q - v1 * nq;
                 const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
                 const float4 bp4 = b4[v1 * bq + g4];
@@ -708,7 +844,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             }
             __syncthreads();
             // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over v2
-            for (int q = tid; q < h * wx; q += NT) {
+            for (int q = rlo * wx + tid; q < rhi * wx; q += NT) {
                 const int v1 = q / wx, u2 = q - v1 * wx;
                 const float4* br = b4 + v1 * bq;
                 const float4* tr = t24 + u2 * bq;
@@ -748,8 +884,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             }
             __syncthreads();
             // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - K1(u1, v1)],
-            // P2 adjacent lanes per line, combined by warp shuffles; L1 X error
+            // P2 adjacent lanes per line, combined by warp shuffles; L1 X error.
+            // In a cluster each CTA first takes the log-sum over its own rows
+            // (shifted by its own previous partial) into pm[it & 1].
             float e_loc = 0.f;
+            float* const pcur = S.pm + (it & 1) * A.amax;
+            const float* const pprev = S.pm + ((it + 1) & 1) * A.amax;
             for (int base = 0; base < nx * P2; base += NT) {
                 const int q = base + tid;
                 const bool act = q < nx * P2;
@@ -759,16 +899,16 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 const bool live = lg > 0.5f * DD_NEG;
                 const float* Rc = S.R + u2;
                 const float* tb = S.tab1 + u1 * h;
-                float m = (first || !live) ? 0.f : lg - aC[line];
+                float m = (first || !live) ? 0.f : (CL > 1 ? pprev[line] : lg - aC[line]);
                 float sacc = 0.f;
                 if (live && !first) {
                     float s0 = 0.f, s1 = 0.f;
-                    int v1 = part;
-                    for (; v1 + P2 < h; v1 += 2 * P2) {
+                    int v1 = rlo + part;
+                    for (; v1 + P2 < rhi; v1 += 2 * P2) {
                         s0 += ex2f(Rc[v1 * wx] - tb[v1] - m);
                         s1 += ex2f(Rc[(v1 + P2) * wx] - tb[v1 + P2] - m);
                     }
-                    if (v1 < h) s0 += ex2f(Rc[v1 * wx] - tb[v1] - m);
+                    if (v1 < rhi) s0 += ex2f(Rc[v1 * wx] - tb[v1] - m);
                     sacc = s0 + s1;
                 }
                 for (int o = 1; o < P2; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
@@ -776,18 +916,47 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 if (__any_sync(0xffffffffu, bad)) {
                     float mm = DD_NEG;
                     if (live)
-                        for (int v1 = part; v1 < h; v1 += P2) mm = fmaxf(mm, Rc[v1 * wx] - tb[v1]);
+                        for (int v1 = rlo + part; v1 < rhi; v1 += P2) mm = fmaxf(mm, Rc[v1 * wx] - tb[v1]);
                     for (int o = 1; o < P2; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
                     float ss = 0.f;
                     if (live)
-                        for (int v1 = part; v1 < h; v1 += P2) ss += ex2f(Rc[v1 * wx] - tb[v1] - mm);
+                        for (int v1 = rlo + part; v1 < rhi; v1 += P2) ss += ex2f(Rc[v1 * wx] - tb[v1] - mm);
                     for (int o = 1; o < P2; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
                     if (bad) { m = mm; sacc = ss; }
                 }
-                if (act && part == 0) {
-                    const float an = live ? lg - (m + lg2f(sacc)) : DD_NEG;
-                    aN[line] = (live && om != 1.f) ? aC[line] + om * (an - aC[line]) : an;
-                    if (live) e_loc += S.muxf[line] * fabsf(expm1f((aC[line] - an) * kLn2));
+                if constexpr (CL > 1) {
+                    if (act && part == 0) pcur[line] = (live && sacc > 0.f) ? m + lg2f(sacc) : DD_NEG;
+                } else {
+                    if (act && part == 0) {
+                        const float an = live ? lg - (m + lg2f(sacc)) : DD_NEG;
+                        aN[line] = (live && om != 1.f) ? aC[line] + om * (an - aC[line]) : an;
+                        if (live) e_loc += S.muxf[line] * fabsf(expm1f((aC[line] - an) * kLn2));
+                    }
+                }
+            }
+            if constexpr (CL > 1) {
+                // combine the partials of all ranks (rank order: identical in every CTA)
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();
+                for (int u = tid; u < nx; u += NT) {
+                    const float lg = S.lgm[u];
+                    if (!(lg > 0.5f * DD_NEG)) {
+                        aN[u] = DD_NEG;
+                        continue;
+                    }
+                    float pr[CL];
+                    float mx = DD_NEG;
+#pragma unroll
+                    for (int r = 0; r < CL; ++r) {
+                        pr[r] = cl.map_shared_rank(pcur, (unsigned)r)[u];
+                        mx = fmaxf(mx, pr[r]);
+                    }
+                    float sm = 0.f;
+#pragma unroll
+                    for (int r = 0; r < CL; ++r) sm += ex2f(pr[r] - mx);
+                    const float an = lg - (mx + lg2f(sm));
+                    aN[u] = om != 1.f ? aC[u] + om * (an - aC[u]) : an;
+                    e_loc += S.muxf[u] * fabsf(expm1f((aC[u] - an) * kLn2));
                 }
             }
             for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
@@ -795,7 +964,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             if (lane == 0) redf[wid] = e_loc;
             __syncthreads();
             err = 0.f;
-            for (int k = 0; k < (NT >> 5); ++k) err += redf[k];
+#pragma unroll
+            for (int k = 0; k < (NTB >> 5); ++k) err += redf[k];  // NTB == blockDim.x
             first = false;
             // stall: no 1% improvement for 64 iterations while already within
             // 50 tol (the FP32 rounding floor of this cell has been reached)
@@ -852,8 +1022,9 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             aN = tmp;
         }
         __syncthreads();  // every thread has read the error partials in S.red
-        if (A.fixed_iters <= 0 && err > tolm && tid == 0) atomicAdd(&A.status[stalled ? 3 : 0], 1);
-        if (A.targ && nx == kMlpBlock) write_targets(A, S, J, aC, h, w, bs, hx, wx, gm[5], uc1, uc2, q11, q12, q22);
+        if (A.fixed_iters <= 0 && err > tolm && tid == 0 && lead) atomicAdd(&A.status[stalled ? 3 : 0], 1);
+        if constexpr (CL == 1)
+            if (A.targ && nx == kMlpBlock) write_targets(A, S, J, aC, h, w, bs, hx, wx, gm[5], uc1, uc2, q11, q12, q22);
 
         // ---- outputs of the solve: duals, objective --------------------------
         float* apo = A.alpha + (long long)A.amax * J;
@@ -862,7 +1033,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const double dx1 = (double)(r0 - o1) + (double)uc1 - (double)vc1;
         const double dx2 = (double)(c0 - o2) + (double)uc2 - (double)vc2;
         const double hd = 0.5 * A.k2d * (dx1 * dx1 + dx2 * dx2);
-        for (int u = tid; u < nx; u += NT) {
+        for (int u = tid; u < (lead ? nx : 0); u += NT) {  // X side: one CTA
             apo[u] = aC[u];
             const float lg = S.lgm[u];
             if (lg > 0.5f * DD_NEG) {
@@ -879,7 +1050,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // (per-thread partials), the separable gauge terms of b through row and
         // column sums of nu_J with FP64 weights, and the constant hd |nu_J|.
         float ef = 0.f;
-        for (int v = tid; v < nA; v += NT) {
+        for (int v = rlo * w + tid; v < rhi * w; v += NT) {  // Y side: the own rows
             const int v1 = v / w, v2 = v - v1 * w;
             const float bv = b_p[v1 * bs + v2];
             A.comp_b[comp + (long long)v1 * stride + v2] = bv;
@@ -889,7 +1060,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             }
         }
         eloc[0] += (double)ef;
-        for (int v1 = tid; v1 < h; v1 += NT) {  // rows: B1 and the axis-1 gauge terms
+        for (int v1 = rlo + tid; v1 < rhi; v1 += NT) {  // rows: B1 and the axis-1 gauge terms
             float rs = 0.f;
             for (int v2 = 0; v2 < w; ++v2) rs += A.comp_nu[comp + (long long)v1 * stride + v2];
             const double vb1 = v1 - (double)vc1;
@@ -897,12 +1068,13 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         }
         for (int v2 = tid; v2 < w; v2 += NT) {  // columns: B2 and the axis-2 gauge terms
             float cs = 0.f;
-            for (int v1 = 0; v1 < h; ++v1) cs += A.comp_nu[comp + (long long)v1 * stride + v2];
+            for (int v1 = rlo; v1 < rhi; ++v1) cs += A.comp_nu[comp + (long long)v1 * stride + v2];
             const double vb2 = v2 - (double)vc2;
             eloc[0] += kLn2d * (S.B2[v2] - A.k2d * (1.0 / l2 - 1.0) * vb2 * vb2 - 2.0 * A.k2d * dx2 * vb2) * cs;
         }
         block_sum_d<1>(eloc, S.red);
-        if (tid == 0) {
+        if constexpr (CL > 1) cluster_sum_d<1>(eloc, S.clx, 8);
+        if (tid == 0 && lead) {
             float* gg = A.gauge + 8 * J;
             gg[0] = d1; gg[1] = d2; gg[2] = l1; gg[3] = l2;
             gg[4] = uc1; gg[5] = uc2; gg[6] = vc1; gg[7] = vc2;
@@ -916,13 +1088,13 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 tr[0] = (long long)t_start;
                 tr[1] = (long long)t_end;
                 tr[2] = (long long)smid;
-                tr[3] = (long long)blockDim.x;
+                tr[3] = (long long)blockDim.x * CL;
             }
             A.err[J] = err;
             A.Ecell[J] = A.eps * eloc[0];
         }
-
     }
+    if constexpr (CL > 1) cg::this_cluster().sync();  // no CTA leaves while others read its shared memory
 }
 
 // Input features of the warm-start network for every cell with a full 8 x 8
@@ -1021,36 +1193,55 @@ __global__ void __launch_bounds__(128) k_feat(HalfArgs A, __nv_bfloat16* __restr
 // the iteration from that stage without the graph.
 struct ClassCaps {
     long long a0, h0, w0, h2, w2, gscr, comp, pool, sa, ss;
+    int cl_cap;          // most cells solved by clusters (0: none)
+    long long cl_area;   // smallest box area h * w solved by a cluster
 };
 
+// Device classification of the cells of a half-iteration for the captured graph:
+// class 1 small boxes, class 0 large boxes (global-scratch offsets for those
+// beyond the shared-memory capacity), class 2 the largest-work cells solved by
+// thread-block clusters. Work key = h w max(1, previous iterations); the cluster
+// class takes whole quarter-octave key buckets from the top while at most
+// cl_cap cells are taken (dd_api.cu applies the same rule on the host). Each
+// list is ordered by descending octave of the key.
 __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __restrict__ chdr,
                                                    const int32_t* __restrict__ iters, ClassCaps cc,
                                                    int32_t* __restrict__ corder, int* __restrict__ ccount,
                                                    long long* __restrict__ goff, const long long* __restrict__ tot,
                                                    int* __restrict__ guard, int stage) {
-    constexpr int NBK = 48;
+    constexpr int NBK = 48, NFB = 4 * NBK;
     __shared__ int cnt[2][NBK];
     __shared__ int offs[2][NBK];
+    __shared__ int cntf[NFB];
+    __shared__ int bstar, clpos;
     __shared__ unsigned long long gsum;
     __shared__ int bad;
     const int tid = threadIdx.x, T = blockDim.x;
     for (int k = tid; k < 2 * NBK; k += T) (&cnt[0][0])[k] = 0;
+    for (int k = tid; k < NFB; k += T) cntf[k] = 0;
     if (tid == 0) {
         gsum = 0;
+        clpos = 0;
         bad = (tot[PT_COMP] > cc.comp || tot[PT_OUT] > cc.pool) ? 1 : 0;
     }
     __syncthreads();
-    auto classify = [&](int J, int& cls, int& bk) {
+    // cls: 0 large, 1 small; bk: octave of the key; fb: quarter octave; el: may be clustered
+    auto classify = [&](int J, int& cls, int& bk, int& fb, bool& el) {
         const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
         const long long a = (long long)h * padw(w);
         cls = (a <= cc.sa && w <= cc.ss && h <= cc.ss) ? 1 : 0;
-        const double key = (double)h * w * max(1, iters[J]);
-        bk = key >= 1.0 ? min(NBK - 1, (int)log2(key)) : 0;
+        const long long key = (long long)h * w * max(1, iters[J]);
+        cluster_key_bucket(key, bk, fb);
+        el = cls == 0 && cc.cl_cap > 0 && (long long)h * w >= cc.cl_area;
     };
     for (int J = tid; J < ncell; J += T) {
-        int cls, bk;
-        classify(J, cls, bk);
-        atomicAdd(&cnt[cls][bk], 1);
+        int cls, bk, fb;
+        bool el;
+        classify(J, cls, bk, fb, el);
+        if (el)
+            atomicAdd(&cntf[fb], 1);
+        else
+            atomicAdd(&cnt[cls][bk], 1);
         const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
         const long long a = (long long)h * padw(w);
         if (cls == 0 && !(a <= cc.a0 && h <= cc.h0 && w <= cc.w0)) {
@@ -1063,6 +1254,15 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     __syncthreads();
     if (tid == 0) {
         if ((long long)gsum > cc.gscr) bad = 1;
+        int cum = 0, bs_ = NFB;
+        for (int f = NFB - 1; f >= 0; --f) {
+            if (cntf[f] == 0) continue;
+            if (cum + cntf[f] > cc.cl_cap) break;
+            cum += cntf[f];
+            bs_ = f;
+        }
+        bstar = bs_;
+        for (int f = 0; f < bs_; ++f) cnt[0][f >> 2] += cntf[f];
         for (int c = 0; c < 2; ++c) {
             int run = 0;
             for (int b = NBK - 1; b >= 0; --b) {  // descending keys
@@ -1071,14 +1271,20 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
             }
             ccount[c] = run;
         }
+        ccount[2] = cum;
         if (bad) atomicCAS(guard, 0, stage);
     }
     __syncthreads();
     for (int J = tid; J < ncell; J += T) {
-        int cls, bk;
-        classify(J, cls, bk);
-        const int pos = atomicAdd(&offs[cls][bk], 1);
-        corder[(long long)cls * ncell + pos] = J;
+        int cls, bk, fb;
+        bool el;
+        classify(J, cls, bk, fb, el);
+        if (el && fb >= bstar) {
+            corder[2LL * ncell + atomicAdd(&clpos, 1)] = J;
+        } else {
+            const int pos = atomicAdd(&offs[cls][bk], 1);
+            corder[(long long)cls * ncell + pos] = J;
+        }
     }
 }
 
@@ -1397,8 +1603,8 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw) {
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
     maxarea = (maxarea + 3) & ~3LL;  // as in carve()
-    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS) + 16;
-    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 4 * (size_t)c->amax + 16 + 32;
+    size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS + 16) + 16;
+    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 6 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
 }
 
@@ -1424,9 +1630,13 @@ bool g_attr_set = false;
 int set_attrs() {
     if (g_attr_set) return DD_OK;
     const int mx = half_kernel_max_smem();
-    if (cudaFuncSetAttribute(k_sink<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sink<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sink<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+    if (cudaFuncSetAttribute(k_sink<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<512, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_c2b, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
         return DD_ERR_CUDA;
     g_attr_set = true;
@@ -1447,6 +1657,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.lgmu = c->d_lgmu; A.mu = c->d_mu; A.nu = c->d_nu; A.m = c->d_m;
     A.lnmu = c->d_lnmu; A.lnnu = c->d_lnnu; A.lnnuf = c->d_lnnuf;
     A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
+    A.tol_share = c->opt.tol_share; A.mbar = P.mbar;
     A.omega = (float)c->opt.omega;
     A.trunc = (float)c->opt.trunc;
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;
@@ -1490,7 +1701,7 @@ int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 
 int launch_classify(dd_ctx* c, int part, int stage) {
     const DevPart& P = c->part[part];
     ClassCaps cc{c->gcap.a0, c->gcap.h0, c->gcap.w0, c->gcap.h2, c->gcap.w2, c->gcap.gscr, c->gcap.comp[part],
-                 c->gcap.pool, c->tune.small_area, c->tune.small_side};
+                 c->gcap.pool, c->tune.small_area, c->tune.small_side, c->gcap.cl_cap, kClusterMinArea};
     k_classify<<<1, 1024, 0, c->stream>>>(P.ncell, P.chdr, P.iters, cc, c->d_corder[part], c->d_ccount[part],
                                           c->d_goff, c->d_tot, c->d_guard, stage);
     return launch_status(__func__);
@@ -1512,10 +1723,50 @@ int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue
     A.smaxH = (int)dims[1];
     A.smaxW = (int)dims[2];
     switch (half_threads(threads)) {
-        case 128: k_sink<128><<<grid, 128, smem, stream>>>(A); break;
-        case 256: k_sink<256><<<grid, 256, smem, stream>>>(A); break;
-        default: k_sink<512><<<grid, 512, smem, stream>>>(A); break;
+        case 128: k_sink<128, 1><<<grid, 128, smem, stream>>>(A); break;
+        case 256: k_sink<256, 1><<<grid, 256, smem, stream>>>(A); break;
+        default: k_sink<512, 1><<<grid, 512, smem, stream>>>(A); break;
     }
+    return launch_status(__func__);
+}
+
+int half_cluster_size(int requested) { return requested >= 4 ? 4 : (requested >= 2 ? 2 : 1); }
+
+int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
+                        int threads, int cl, size_t smem, int nclusters, cudaStream_t stream, const int* count_dev) {
+    RET_IF(set_attrs());
+    HalfArgs A = make_args(c, part);
+    A.count = count_dev;
+    A.gscratch = c->d_gscr;
+    A.goff = c->d_goff;
+    A.ncell = ncell;
+    A.order = order;
+    A.queue = queue;
+    A.smaxA = (int)dims[0];
+    A.smaxH = (int)dims[1];
+    A.smaxW = (int)dims[2];
+    A.targ = nullptr;  // training targets come from one-CTA solves only
+    const int nt = half_threads(threads) >= 512 ? 512 : 256;
+    cl = half_cluster_size(cl);
+    if (cl < 2 || nclusters < 1) return DD_ERR_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * cl), 1, 1);
+    cfg.blockDim = dim3((unsigned)nt, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (nt == 512)
+        e = cl == 4 ? cudaLaunchKernelEx(&cfg, k_sink<512, 4>, A) : cudaLaunchKernelEx(&cfg, k_sink<512, 2>, A);
+    else
+        e = cl == 4 ? cudaLaunchKernelEx(&cfg, k_sink<256, 4>, A) : cudaLaunchKernelEx(&cfg, k_sink<256, 2>, A);
+    if (e != cudaSuccess) return dd_record_cuda_error(e, __func__);
     return launch_status(__func__);
 }
 
@@ -1533,9 +1784,9 @@ int half_occupancy(int threads, size_t smem) {
     if (set_attrs() != DD_OK) return 0;
     int nb = 0;
     switch (half_threads(threads)) {
-        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<128>, 128, smem); break;
-        case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<256>, 256, smem); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<512>, 512, smem); break;
+        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<128, 1>, 128, smem); break;
+        case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<256, 1>, 256, smem); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<512, 1>, 512, smem); break;
     }
     return nb;
 }

@@ -11,6 +11,19 @@
 
 #define DD_NEG (-1.0e30f)  // log2 of zero mass
 
+// Cells solved by thread-block clusters: box area at least this, and the work key
+// (h w max(1, previous iterations)) in the top quarter-octave buckets.
+constexpr long long kClusterMinArea = 1024;
+// octave (bk) and quarter-octave (fb) bucket of a work key; fb / 4 == bk
+__host__ __device__ inline void cluster_key_bucket(long long key, int& bk, int& fb) {
+    int L = 0;
+    while (L < 62 && (key >> (L + 1)) > 0) ++L;  // floor(log2 key), 0 for key < 2
+    const int frac = L >= 2 ? (int)((key >> (L - 2)) & 3) : 0;
+    bk = L < 47 ? L : 47;
+    const int f = 4 * L + frac;
+    fb = f < 191 ? f : 191;
+}
+
 // Box header layout in device memory (int32 x 8 per box).
 enum { BH_O1 = 0, BH_O2, BH_H, BH_W, BH_STRIDE, BH_START, BH_STRIDE_HI, BH_START_HI, BH_N };
 // Composite header (int32 x 8 per cell): box + pool offsets.
@@ -34,6 +47,7 @@ struct DevPart {
     int32_t* members = nullptr;  // ncell x 4, -1 padded
     int32_t* xblk = nullptr;     // ncell x XB_N
     double* mJ = nullptr;        // ncell, mu(X_J)
+    double mbar = 0.0;           // mean of mu(X_J) over the partition
     int32_t* chdr = nullptr;     // ncell x CH_N (last solve)
     float* alpha = nullptr;      // ncell x amax, centred base-2 gauge
     float* gauge = nullptr;      // ncell x 2, displacement (cell centre - box centre) in pixels
@@ -115,7 +129,8 @@ struct dd_ctx {
 
     cudaEvent_t ev[8] = {};
     cudaStream_t side = nullptr;  // second stream: the large-box class of cells
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side2 = nullptr;  // third stream: the cells solved by clusters
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
 
@@ -144,6 +159,7 @@ struct dd_ctx {
         int grid[3] = {0, 0, 0};
         size_t smem[3] = {0, 0, 0};
         size_t smem_c2b = 0;
+        int cl_cap = 0;  // cluster class: most cells (0: off)
     } gcap;
     struct Seen {
         long long out = 0, comp[2] = {0, 0}, gscr = 0, a0 = 0, h0 = 0, w0 = 0, hmax = 0, wmax = 0, n0 = 0, n2 = 0;
@@ -189,6 +205,12 @@ size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long m
 int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
 int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem);
+// the cell kernel on thread-block clusters of `cl` (2 or 4) CTAs, one cluster per
+// cell, nclusters clusters; box arrays of cells with goff >= 0 in global scratch
+int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
+                        int threads, int cl, size_t smem, int nclusters, cudaStream_t stream,
+                        const int* count_dev = nullptr);
+int half_cluster_size(int requested);
 int half_occupancy(int threads, size_t smem);
 int launch_feat(dd_ctx* c, int part);
 int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* targ);

@@ -1,8 +1,8 @@
 // Autotuner of the cell kernels' launch configuration (dd_autotune).
 //
-// The batched Sinkhorn kernel solves one composite cell per CTA, with the
-// cells split into size classes by their bounding box (see dd_tuning in
-// ddflow.h). Which CTA size serves which boxes best depends on the GPU and on
+// The batched Sinkhorn kernel solves one composite cell per CTA (or per
+// thread-block cluster for the largest-work cells), with the cells split into
+// size classes by their bounding box (see dd_tuning in ddflow.h). Which CTA size serves which boxes best depends on the GPU and on
 // the distribution of box sizes of the problem, so the library measures it:
 // every candidate configuration runs the cell kernels of both partitions on the
 // context's current state, each cell solved to the context's tolerance from the
@@ -107,9 +107,10 @@ bool cache_lookup(const char* path, const std::string& key, dd_tuning* t) {
         const size_t k = key.size();
         if (std::strncmp(line, key.c_str(), k) != 0 || line[k] != ' ') continue;
         dd_tuning x{};
-        if (std::sscanf(line + k, " threads=%d,%d,%d small_area=%d small_side=%d ms_default=%lf ms_best=%lf",
-                        &x.threads[0], &x.threads[1], &x.threads[2], &x.small_area, &x.small_side, &x.ms_default,
-                        &x.ms_best) == 7) {
+        if (std::sscanf(line + k,
+                        " threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d ms_default=%lf ms_best=%lf",
+                        &x.threads[0], &x.threads[1], &x.threads[2], &x.small_area, &x.small_side, &x.cl_size,
+                        &x.cl_cells, &x.ms_default, &x.ms_best) == 9) {
             *t = x;
             found = true;  // the last entry for the key wins
         }
@@ -121,8 +122,9 @@ bool cache_lookup(const char* path, const std::string& key, dd_tuning* t) {
 void cache_store(const char* path, const std::string& key, const dd_tuning& t) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s threads=%d,%d,%d small_area=%d small_side=%d ms_default=%.4f ms_best=%.4f\n", key.c_str(),
-                 t.threads[0], t.threads[1], t.threads[2], t.small_area, t.small_side, t.ms_default, t.ms_best);
+    std::fprintf(f, "%s threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d ms_default=%.4f ms_best=%.4f\n",
+                 key.c_str(), t.threads[0], t.threads[1], t.threads[2], t.small_area, t.small_side, t.cl_size,
+                 t.cl_cells, t.ms_default, t.ms_best);
     std::fclose(f);
 }
 
@@ -169,6 +171,7 @@ int dd_set_tuning(dd_ctx* c, const dd_tuning* t) {
     for (int k = 0; k < 3; ++k)
         if (!valid_threads(t->threads[k])) return DD_ERR_ARG;
     if (t->small_area < 16 || t->small_side < 4 || t->small_side > 256) return DD_ERR_ARG;
+    if (!(t->cl_size == 1 || t->cl_size == 2 || t->cl_size == 4) || t->cl_cells < 0) return DD_ERR_ARG;
     if (half_smem_bytes(c, t->small_area, t->small_side, t->small_side) > (size_t)half_kernel_max_smem())
         return DD_ERR_ARG;
     c->tune = *t;
@@ -223,6 +226,25 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
                     best_ms = ms;
                     best = t;
                 }
+            }
+        }
+    }
+    // then thread-block clusters for the largest-work cells, on top of the best
+    // configuration so far
+    const dd_tuning base = best;
+    for (int cls : {2, 4}) {
+        for (int cells : {16, 32}) {
+            if (r != DD_OK) break;
+            if (c->opt.flags & DD_FLAG_COLLECT) break;  // training targets: one-CTA solves only
+            dd_tuning t = base;
+            t.cl_size = cls;
+            t.cl_cells = cells;
+            double ms = 0.0;
+            r = trial(c, t, saved, &ms);
+            ++n;
+            if (r == DD_OK && ms < best_ms) {
+                best_ms = ms;
+                best = t;
             }
         }
     }

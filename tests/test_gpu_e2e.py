@@ -118,6 +118,78 @@ def _state(g):
     return [(o1, o2, a.copy()) for o1, o2, a in g.plan()]
 
 
+@pytest.mark.parametrize("cl", [2, 4])
+def test_cluster_solves_match_oracle(dd, cl):
+    """Thread-block clusters (cl CTAs per cell, own box rows per CTA, partial
+    log-sum-exps of the X-update combined through distributed shared memory):
+    first A half-iteration of the 256 x 256 workload from the KR plan, fixed
+    iterations. The cells that ran on clusters (the trace records cl x threads)
+    match the FP64 oracle like one-CTA solves do (bound of the sampled-cells test),
+    and every cell matches the one-CTA run of the same configuration to FP32
+    rounding (only the order of the row sums differs)."""
+    mu, nu, eps, p = synth.workload("dd256", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    K = 60
+    runs = {}
+    for c in (1, cl):
+        g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, fixed_iters=K, flags=dd.DD_FLAG_KEEP_PREBALANCE | dd.DD_FLAG_TRACE)
+        g.set_tuning([512, 256, 512], 3072, 96, cl_size=c, cl_cells=64)
+        st = g.iterate(0)
+        runs[c] = (g.prebalance(), g.basic_moments()["D"].copy(), g.trace(0)[:, 3].copy(), st["objective"])
+        g.close()
+    pre1, D1, _, E1 = runs[1]
+    pre, D, thr, E = runs[cl]
+    clustered = np.flatnonzero(thr == 512 * cl)
+    assert clustered.size >= 2, thr
+    geom = Geometry(256, 256, 4)
+    m = geom.basic_masses(mu)
+    for a, b, mi in zip(pre1, pre, m):
+        assert (a[0], a[1], a[2].shape) == (b[0], b[1], b[2].shape)
+        assert np.abs(a[2] - b[2]).sum() <= 2e-5 * mi
+    assert np.allclose(D, D1, rtol=2e-5, atol=0)
+    assert abs(E - E1) <= 1e-7 * abs(E1)
+    bx = [Box(o1, o2, np.asarray(a)) for o1, o2, a in boxes]
+    cells = geom.partition(0)
+    for J in clustered[:3]:
+        members = cells[J]
+        nuJ = basic_to_composite(bx, members)
+        res = solve_cell(geom, mu, eps, 1.0 / 256, members, nuJ, None, 1e-5, 100000, fixed_iters=K)
+        arrs, Dref = composite_to_basic(geom, members, nuJ, res)
+        for k, i in enumerate(members):
+            assert np.abs(pre[i][2] - arrs[k]).sum() <= 1e-4 * m[i], (J, i)
+            assert D[i] == pytest.approx(Dref[k], rel=1e-4), (J, i)
+
+
+def test_clusters_in_graph_are_bit_identical_to_step_by_step(dd):
+    """With clusters on, the captured graph (device selection of the cluster
+    cells by k_classify) and the step-by-step path (host selection by the same
+    rule) compute the same cells on clusters, so the states are bit-identical; in
+    tolerance mode with the batch budget every half-iteration keeps the L1 X
+    error within tol."""
+    mu, nu, eps, p = synth.workload("dd256", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    kw = dict(boxes=boxes, tol=1e-5, max_iter=20000, eps_levels=2, eps_factor=4.0, omega=1.4, tol_share=1.0)
+    g = dd.DomDec(mu, nu, eps, 4, flags=dd.DD_FLAG_TRACE, **kw)
+    e = dd.DomDec(mu, nu, eps, 4, flags=dd.DD_FLAG_NO_GRAPH | dd.DD_FLAG_TRACE, **kw)
+    for x in (g, e):
+        x.set_tuning([512, 256, 512], 3072, 96, cl_size=4, cl_cells=16)
+    ncl = 0
+    for it in range(4):
+        sg = g.step(1)
+        se = e.step(1)
+        for k in (0, 1):
+            assert sg[k]["objective"] == se[k]["objective"], it
+            assert sg[k]["l1_x"] <= 1e-5 and sg[k]["n_maxiter"] == 0
+        ncl += int((g.trace(1)[:, 3] == 2048).sum())
+        assert np.array_equal(g.trace(1)[:, 3], e.trace(1)[:, 3])
+        for (a1, a2, a), (b1, b2, b) in zip(_state(g), _state(e)):
+            assert (a1, a2) == (b1, b2) and np.array_equal(a, b)
+    assert ncl > 0
+    assert g.graph_counters()["replays"] >= 2
+    g.close()
+    e.close()
+
+
 @pytest.mark.parametrize("margin", [0.5, 0.0])
 def test_graph_step_is_bit_identical_to_step_by_step(dd, margin):
     """dd_step replays a captured graph (device classification and ordering, the
@@ -162,7 +234,7 @@ def test_autotune_restores_state_and_caches(dd, tmp_path):
     b.step(1)
     t = a.autotune(cache)
     assert t["trials"] >= 2 and 0 < t["ms_best"] <= t["ms_default"]
-    b.set_tuning(t["threads"], t["small_area"], t["small_side"])
+    b.set_tuning(t["threads"], t["small_area"], t["small_side"], t["cl_size"], t["cl_cells"])
     for part in (0, 1, 0):
         sa, sb = a.iterate(part), b.iterate(part)
         assert sa["objective"] == sb["objective"] and sa["iters_mean"] == sb["iters_mean"]
@@ -172,6 +244,7 @@ def test_autotune_restores_state_and_caches(dd, tmp_path):
     c.step(1)
     t2 = c.autotune(cache)
     assert t2["trials"] == 0 and t2["threads"] == t["threads"] and t2["small_area"] == t["small_area"]
+    assert (t2["cl_size"], t2["cl_cells"]) == (t["cl_size"], t["cl_cells"])
     for g in (a, b, c):
         g.close()
 
@@ -187,7 +260,8 @@ def test_trace_records_every_cell(dd):
     assert tr.shape == (g.ncell[1], 4)
     assert (tr[:, 0] > 0).all() and (tr[:, 1] >= tr[:, 0]).all()
     assert (tr[:, 1].max() - tr[:, 0].min()) * 1e-6 <= st["ms_total"] + 1.0
-    assert ((tr[:, 2] >= 0) & (tr[:, 2] < 1024)).all() and set(np.unique(tr[:, 3])) <= {128, 256, 512}
+    assert ((tr[:, 2] >= 0) & (tr[:, 2] < 1024)).all()
+    assert set(np.unique(tr[:, 3])) <= {128, 256, 512, 512 * 2, 512 * 4, 256 * 2, 256 * 4}
     g.close()
 
 
