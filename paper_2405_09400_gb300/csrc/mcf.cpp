@@ -236,6 +236,22 @@ struct NetworkSimplex {
         return true;
     }
 
+    // most negative reduced cost over arcs [a, b); tree arcs price at exactly 0
+    // (integer potentials), so they need no test and are never chosen
+    void scan(int a, int b, int& best, int64_t& best_rc) const {
+        const int64_t* cst = cost.data();
+        const int64_t* pt = pot.data();
+        const int* tl = tail.data();
+        const int* hd = head.data();
+        for (int e = a; e < b; ++e) {
+            const int64_t r = cst[e] + pt[tl[e]] - pt[hd[e]];
+            if (r < best_rc) {
+                best_rc = r;
+                best = e;
+            }
+        }
+    }
+
     bool run() {
         const int block = mcf_block > 0 ? mcf_block : std::max(16, (int)std::sqrt((double)na));
         int next = 0;
@@ -244,17 +260,15 @@ struct NetworkSimplex {
             int64_t best_rc = 0;
             int scanned = 0;
             while (scanned < na) {
-                int lim = std::min(block, na - scanned);
-                for (int t = 0; t < lim; ++t) {
-                    int e = next;
-                    next = (next + 1 == na) ? 0 : next + 1;
-                    if (in_tree[e]) continue;
+                const int lim = std::min(block, na - scanned);
+                const int n1 = std::min(lim, na - next);  // the block wraps at most once
+                scan(next, next + n1, best, best_rc);
+                if (lim > n1) scan(0, lim - n1, best, best_rc);
 #ifdef MCF_STATS
-                    ++st_scan;
+                st_scan += lim;
 #endif
-                    int64_t r = rc(e);
-                    if (r < best_rc) { best_rc = r; best = e; }
-                }
+                next += lim;
+                if (next >= na) next -= na;
                 scanned += lim;
                 if (best >= 0) break;
             }
