@@ -688,6 +688,9 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // threads per line of the X-update stage 2 (a power of two, lanes adjacent)
         int P2 = 1;
         while (P2 * 2 * nx <= NT && P2 < 16) P2 *= 2;
+        const int nxl = (rhi - rlo) * wx;  // X-update stage 1 lines of this CTA
+        int PX = 1;
+        while (PX * 2 * nxl <= NT && PX < 8) PX *= 2;
         const float4* b4 = reinterpret_cast<const float4*>(b_p);
         const float4* t24 = reinterpret_cast<const float4*>(S.tab2);
         const int nq = (w + 3) >> 2;  // float4 groups holding data per row
@@ -754,7 +757,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             __syncthreads();
             // Y-update stage 2: b(v) = log2 nu_J(v) - LSE_u1 [T(u1, v2) - K1(u1, v1)],
             // four adjacent v2 per thread (float4 rows of T, b, log2 nu_J)
-            if (hx == 8 && !first) {  // full blocks after the first iteration: operands loaded first
+            if (NTB < 512 && hx == 8 && !first) {
+                // full blocks after the first iteration: operands loaded first
                 for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
                     const int v1 = q / nq, g4 = q - v1 * nq;
                     const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
@@ -798,6 +802,57 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                         out[k] = ln[k] - (m[k] + lg2f(sa[k]));
                     }
                     reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
+                }
+            } else if (hx == 8 && !first) {
+                // full blocks after the first iteration (512-thread CTAs): a thread
+                // keeps the 8 x 4 values of T of its column group in registers and
+                // walks its rows (row blocks nrb rows apart), so T is read once
+                const int nrows = rhi - rlo;
+                const int nrb = max(1, min(nrows, NT / nq));
+                for (int q = tid; q < nrb * nq; q += NT) {
+                    const int rb = q / nq, g4 = q - rb * nq;
+                    float4 T4[8];
+#pragma unroll
+                    for (int u1 = 0; u1 < 8; ++u1) T4[u1] = reinterpret_cast<const float4*>(S.T + u1 * bs)[g4];
+                    for (int v1 = rlo + rb; v1 < rhi; v1 += nrb) {
+                        const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
+                        const float4 bp4 = b4[v1 * bq + g4];
+                        const float* tb = S.tab1 + v1;
+                        float kk[8];
+#pragma unroll
+                        for (int u1 = 0; u1 < 8; ++u1) kk[u1] = tb[u1 * h];
+                        const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                        const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
+                        float m[4], sa[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            m[k] = ln[k] > 0.5f * DD_NEG ? ln[k] - bp[k] : 0.f;
+                            sa[k] = 0.f;
+                        }
+#pragma unroll
+                        for (int u1 = 0; u1 < 8; ++u1) {
+                            sa[0] += ex2f(T4[u1].x - kk[u1] - m[0]);
+                            sa[1] += ex2f(T4[u1].y - kk[u1] - m[1]);
+                            sa[2] += ex2f(T4[u1].z - kk[u1] - m[2]);
+                            sa[3] += ex2f(T4[u1].w - kk[u1] - m[3]);
+                        }
+                        float out[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int v2 = 4 * g4 + k;
+                            if (v2 >= w || !(ln[k] > 0.5f * DD_NEG)) { out[k] = DD_NEG; continue; }
+                            if (!shift_ok(sa[k])) {
+                                float mm = DD_NEG;
+                                for (int u1 = 0; u1 < 8; ++u1) mm = fmaxf(mm, S.T[u1 * bs + v2] - tb[u1 * h]);
+                                float ss = 0.f;
+                                for (int u1 = 0; u1 < 8; ++u1) ss += ex2f(S.T[u1 * bs + v2] - tb[u1 * h] - mm);
+                                m[k] = mm;
+                                sa[k] = ss;
+                            }
+                            out[k] = ln[k] - (m[k] + lg2f(sa[k]));
+                        }
+                        reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
+                    }
                 }
             } else
             for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
@@ -843,18 +898,24 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
             }
             __syncthreads();
-            // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over v2
-            for (int q = rlo * wx + tid; q < rhi * wx; q += NT) {
-                const int v1 = q / wx, u2 = q - v1 * wx;
+            // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over
+            // v2; PX adjacent lanes per line (strided float4 groups), combined by
+            // warp shuffles, so that short row ranges (clusters) keep every lane busy
+            for (int base = 0; base < nxl * PX; base += NT) {
+                const int q = base + tid;
+                const bool act = q < nxl * PX;
+                const int ql = act ? q / PX : 0, p = q - (q / PX) * PX;
+                const int line = rlo * wx + ql;
+                const int v1 = line / wx, u2 = line - v1 * wx;
                 const float4* br = b4 + v1 * bq;
                 const float4* tr = t24 + u2 * bq;
-                float m = first ? 0.f : S.R[q];
+                float m = (first || !act) ? 0.f : S.R[line];
                 float sacc = 0.f;
-                if (!first) {
+                if (act && !first) {
                     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                    int g = 0;
-                    for (; g + 2 <= nq; g += 2) {
-                        const float4 bb = br[g], tt = tr[g], bc = br[g + 1], tc = tr[g + 1];
+                    int g = p;
+                    for (; g + PX < nq; g += 2 * PX) {
+                        const float4 bb = br[g], tt = tr[g], bc = br[g + PX], tc = tr[g + PX];
                         s0 += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m);
                         s1 += ex2f(bb.z - tt.z - m) + ex2f(bb.w - tt.w - m);
                         s2 += ex2f(bc.x - tc.x - m) + ex2f(bc.y - tc.y - m);
@@ -867,20 +928,27 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     }
                     sacc = (s0 + s1) + (s2 + s3);
                 }
-                if (first || !shift_ok(sacc)) {
-                    m = DD_NEG;
-                    for (int g = 0; g < nq; ++g) {
-                        const float4 bb = br[g], tt = tr[g];
-                        m = fmaxf(fmaxf(fmaxf(m, bb.x - tt.x), fmaxf(bb.y - tt.y, bb.z - tt.z)), bb.w - tt.w);
-                    }
-                    sacc = 0.f;
-                    for (int g = 0; g < nq; ++g) {
-                        const float4 bb = br[g], tt = tr[g];
-                        sacc += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m) + ex2f(bb.z - tt.z - m) +
-                                ex2f(bb.w - tt.w - m);
-                    }
+                for (int o = 1; o < PX; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                const bool bad = act && (first || !shift_ok(sacc));
+                if (__any_sync(0xffffffffu, bad)) {
+                    float mm = DD_NEG;
+                    if (act)
+                        for (int g = p; g < nq; g += PX) {
+                            const float4 bb = br[g], tt = tr[g];
+                            mm = fmaxf(fmaxf(fmaxf(mm, bb.x - tt.x), fmaxf(bb.y - tt.y, bb.z - tt.z)), bb.w - tt.w);
+                        }
+                    for (int o = 1; o < PX; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+                    float ss = 0.f;
+                    if (act)
+                        for (int g = p; g < nq; g += PX) {
+                            const float4 bb = br[g], tt = tr[g];
+                            ss += ex2f(bb.x - tt.x - mm) + ex2f(bb.y - tt.y - mm) + ex2f(bb.z - tt.z - mm) +
+                                  ex2f(bb.w - tt.w - mm);
+                        }
+                    for (int o = 1; o < PX; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    if (bad) { m = mm; sacc = ss; }
                 }
-                S.R[q] = m + lg2f(sacc);
+                if (act && p == 0) S.R[line] = m + lg2f(sacc);
             }
             __syncthreads();
             // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - K1(u1, v1)],
