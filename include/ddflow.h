@@ -169,6 +169,19 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
 int dd_set_plan(dd_ctx* ctx, const int32_t* hdr, const double* data, size_t n);
 
 /*
+ * Change the entropic regularisation eps of the next half-iterations (eps > 0),
+ * for an eps schedule across hybrid iterations (the eps-scaling of the paper's
+ * solvers, Section 5, "Multi-scale and eps-scaling"). The plan is kept. The
+ * stored X duals of both partitions are rescaled so that the dual potentials
+ * alpha (cost units) stay the same: in every cell's gauge a - log2 mu scales as
+ * 1/eps, a <- log2 mu + (eps_old / eps) (a - log2 mu); they warm-start the next
+ * solves. The learned start's stored predictions are dropped (the next solve of
+ * each partition starts from the network's prediction). Captured graphs are
+ * re-captured. Errors: DD_ERR_ARG (eps <= 0 or not finite), DD_ERR_CUDA.
+ */
+int dd_set_eps(dd_ctx* ctx, double eps);
+
+/*
  * One domain-decomposition half-iteration (Alg. 1 in the form of Alg. 4):
  * BasicToComposite, the batched log-domain cell Sinkhorn solves, CompositeToBasic
  * with <c, pi_i>, balancing, truncation. part = 0 (A), 1 (B) or -1 (the other

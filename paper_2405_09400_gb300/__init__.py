@@ -29,7 +29,7 @@ DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 
 EXPORTS = [
-    "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_iterate", "dd_flow_update", "dd_step",
+    "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_set_eps", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
@@ -109,6 +109,7 @@ def load():
         "dd_last_error": (C.c_char_p, []),
         "dd_init": (C.c_int, [_f64p, _f64p, P(dd_grid), C.c_double, C.c_int, P(dd_options), vp, P(vp)]),
         "dd_set_plan": (C.c_int, [vp, _i32p, _f64p, C.c_size_t]),
+        "dd_set_eps": (C.c_int, [vp, C.c_double]),
         "dd_iterate": (C.c_int, [vp, C.c_int, P(dd_stats)]),
         "dd_flow_update": (C.c_int, [vp, P(dd_flow_stats)]),
         "dd_step": (C.c_int, [vp, C.c_int, P(dd_stats), P(dd_stats), P(dd_flow_stats)]),
@@ -194,6 +195,10 @@ def dd_init(mu, nu, eps, cell_size, h=None, options=None, stream=None):
     _check(lib.dd_init(_ptr(mu, _f64p), _ptr(nu, _f64p), C.byref(g), float(eps), int(cell_size), C.byref(opt),
                        stream, C.byref(ctx)), "dd_init")
     return ctx
+
+
+def dd_set_eps(ctx, eps):
+    _check(load().dd_set_eps(ctx, float(eps)), "dd_set_eps")
 
 
 def dd_set_plan(ctx, hdr, data):
@@ -508,6 +513,11 @@ class DomDec:
             self.set_plan(boxes)
         if weights is not None:
             self.set_warmstart_weights(weights)
+
+    def set_eps(self, eps):
+        """eps of the next half-iterations (eps schedule across hybrid iterations)."""
+        dd_set_eps(self.ctx, eps)
+        self.eps = float(eps)
 
     def set_plan(self, boxes):
         hdr, data = boxes if isinstance(boxes, tuple) else boxes_to_arrays(boxes)

@@ -789,6 +789,23 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
 
 extern "C" {
 
+int dd_set_eps(dd_ctx* c, double eps) {
+    if (!c || !(eps > 0.0) || !std::isfinite(eps)) return DD_ERR_ARG;
+    const double f = c->eps / eps;
+    for (int p = 0; p < 2; ++p) {
+        DevPart& P = c->part[p];
+        if (P.warm_valid) RET(launch_rescale_alpha(c, p, f));
+        c->n_launch += P.warm_valid ? 1 : 0;
+        P.pred_old_valid = false;
+    }
+    c->eps = eps;
+    c->k2d = c->h * c->h / eps / kLn2;
+    c->k2 = (float)c->k2d;
+    c->gen += 1;  // captured graphs hold the old cost scale
+    CK(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+}
+
 int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     if (!c) return DD_ERR_ARG;
     if (part < -1 || part > 1) return DD_ERR_ARG;

@@ -1682,6 +1682,31 @@ size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw) {
     return sizeof(double) * (32 * 16 + 16) + sizeof(float) * fl;
 }
 
+namespace {
+// a <- log2 mu + f (a - log2 mu) for the stored X duals of every cell (eps change)
+__global__ void k_rescale_alpha(int ncell, int amax, int N2, const int32_t* __restrict__ xblk,
+                                const float* __restrict__ lgmu, float* __restrict__ alpha, float f) {
+    const int J = blockIdx.x;
+    if (J >= ncell) return;
+    const int32_t* xb = xblk + XB_N * J;
+    const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX];
+    for (int u = threadIdx.x; u < hx * wx && u < amax; u += blockDim.x) {
+        const int u1 = u / wx, u2 = u - u1 * wx;
+        const float lg = lgmu[(long long)(r0 + u1) * N2 + (c0 + u2)];
+        float* a = alpha + (long long)amax * J + u;
+        if (lg > 0.5f * DD_NEG) *a = lg + f * (*a - lg);
+    }
+}
+
+}  // namespace
+
+int launch_rescale_alpha(dd_ctx* c, int part, double f) {
+    const DevPart& P = c->part[part];
+    if (P.ncell <= 0) return DD_OK;
+    k_rescale_alpha<<<P.ncell, 64, 0, c->stream>>>(P.ncell, c->amax, c->N2, P.xblk, c->d_lgmu, P.alpha, (float)f);
+    return launch_status(__func__);
+}
+
 int half_kernel_max_smem() { return 227 * 1024; }
 
 int launch_plan_half(dd_ctx* c, int part) {

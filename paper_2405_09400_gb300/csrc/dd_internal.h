@@ -211,6 +211,8 @@ int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, in
                         int threads, int cl, size_t smem, int nclusters, cudaStream_t stream,
                         const int* count_dev = nullptr);
 int half_cluster_size(int requested);
+// stored X duals of a partition: a <- log2 mu + f (a - log2 mu) (eps change by 1 / f)
+int launch_rescale_alpha(dd_ctx* c, int part, double f);
 int half_occupancy(int threads, size_t smem);
 int launch_feat(dd_ctx* c, int part);
 int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* targ);

@@ -363,3 +363,50 @@ def test_four_bumps_hybrid_matches_oracle(dd):
         bound = 2 * (1e-6 + 1e-8) * t * max(f["moved"], 1e-300) + 1e-15
         assert abs(f["value"] - fo["value"]) <= bound, (it, f["value"], fo["value"], bound)
     g.close()
+
+
+def test_set_eps_keeps_dual_potentials(dd):
+    """dd_set_eps rescales the stored X duals so that the dual potentials alpha
+    (cost units) are unchanged: in a cell's gauge a - log2 mu scales as 1/eps
+    (exact; only the FP32 rounding of the rescaled values remains)."""
+    mu, nu, eps, p = synth.workload("dd32", 0)
+    g = dd.DomDec(mu, nu, eps, 4, tol=1e-7, max_iter=50000)
+    g.iterate(0)
+    g.iterate(1)
+    a0, _ = g.duals(0)
+    g.set_eps(eps / 2)
+    a1, _ = g.duals(0)
+    ok = np.isfinite(a0)
+    assert np.array_equal(ok, np.isfinite(a1))
+    assert np.abs(a1[ok] - a0[ok]).max() <= 1e-6 * np.abs(a0[ok]).max()
+    g.close()
+
+
+def test_eps_schedule_across_hybrid_iterations(dd):
+    """eps-scaling across hybrid iterations (Section 5, "Multi-scale and
+    eps-scaling", without the multiscale layers): 4 eps, 2 eps, then eps. After
+    20 hybrid iterations the objective is as close to the converged one (80
+    iterations at eps, tol 1e-7) as 20 iterations run at eps throughout
+    (measured: 8.7e-5 vs 7.7e-5 relative), with 41 % fewer Sinkhorn iterations
+    (asserted: both within 2e-4, schedule <= 0.8 x the Sinkhorn iterations)."""
+    mu, nu, eps, p = synth.workload("dd32", 0)
+
+    def run(sched, tol=1e-6):
+        g = dd.DomDec(mu, nu, sched[0][0], 4, tol=tol, max_iter=50000)
+        its = 0.0
+        for e, k in sched:
+            g.set_eps(e)
+            for _ in range(k):
+                sa, sb, sf = g.step(1)
+                assert sa["n_maxiter"] == 0 and sb["n_maxiter"] == 0
+                its += sa["iters_mean"] * sa["ncell"] + sb["iters_mean"] * sb["ncell"]
+        E, l1x, l1y = g.objective()
+        assert l1x <= tol and l1y <= 1e-6
+        g.close()
+        return E, its
+
+    Eref, _ = run([(eps, 80)], tol=1e-7)
+    Ed, itd = run([(eps, 20)])
+    Es, its = run([(4 * eps, 4), (2 * eps, 4), (eps, 12)])
+    assert abs(Ed - Eref) <= 2e-4 * Eref and abs(Es - Eref) <= 2e-4 * Eref, (Ed, Es, Eref)
+    assert its <= 0.8 * itd, (its, itd)
