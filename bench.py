@@ -147,13 +147,15 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
     torch.cuda.synchronize()
     n0 = g.counters()["launches"]
     out = dict(step_ms=[], cell_ms=[], terms=[], cells=0, hbm_bytes=[], iters_mean=[], iters_max=[], first_ms=first_ms,
-               stalled=0, maxiter=0, l1x_max=0.0)
+               stalled=0, maxiter=0, l1x_max=0.0, mcf_ms=[], pivots=[])
     for _ in range(args.steps):
         flush.zero_()  # evict the state from L2 between steps (outside the timed events)
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         sa, sb, sf = g.step(1, stats=True)
+        out["mcf_ms"].append(sf["ms_solve"])
+        out["pivots"].append(sf["pivots"])
         a1.record(stream)
         a1.synchronize()
         out["step_ms"].append(a0.elapsed_time(a1))
@@ -303,6 +305,10 @@ def run_ours(args):
         "sinkhorn_iters_mean": {k: round(float(np.mean(x["iters_mean"])), 2) for k, x in arm_map.items()},
         "sinkhorn_iters_max_mean": {k: round(float(np.mean(x["iters_max"])), 1) for k, x in arm_map.items()},
         "cell_solves_stalled_or_capped": {k: x["stalled"] + x["maxiter"] for k, x in arm_map.items()},
+        "step_breakdown_ms": {"cell_kernels_A_plus_B": round(2 * k_ms, 3),
+                              "min_cost_flow_host": round(float(np.mean(warm["mcf_ms"])), 3),
+                              "rest": round(ms_warm - 2 * k_ms - float(np.mean(warm["mcf_ms"])), 3),
+                              "mcf_pivots_mean": round(float(np.mean(warm["pivots"])), 1)},
         "half_iteration_l1x_max": {k: x["l1x_max"] for k, x in arm_map.items()},
         "iterations_per_s": round(1e3 / ms_warm, 3),
         "cells_per_s": round(warm["cells"] / (sum(warm["step_ms"]) * 1e-3), 1),

@@ -60,21 +60,26 @@ extern "C" {
                             (barycentres and variances of the two marginals);
                             not in the paper                                     */
 #define DD_WARM_MLP 3  /* learned (dd_set_warmstart_weights; cells with a full
-                          8 x 8 block, the others as DD_WARM_PREV): the first
-                          solve of a partition starts from affine dual + the
-                          network's correction, every later one from the
-                          previous dual + the network's predicted change of the
-                          dual between the two solves; not in the paper,
-                          requires cell_size 4                                   */
+                          8 x 8 block, the others as DD_WARM_PREV): a solve
+                          without a previous dual of its cell (the first of each
+                          partition) starts from the affine dual + the network's
+                          correction, later ones from the previous dual
+                          (DD_FLAG_MLP_EVERY_SOLVE: from the previous dual + the
+                          network's predicted change of the dual between the two
+                          solves); not in the paper, requires cell_size 4       */
 
 #define DD_FLAG_KEEP_PREBALANCE 1 /* keep the pre-balance basic marginals of the
                                      last half-iteration for dd_get_prebalance     */
-#define DD_FLAG_NO_GRAPH 4 /* dd_step runs its steps one by one instead of
-                              replaying a captured CUDA graph                     */
-#define DD_FLAG_COLLECT 2
-#define DD_FLAG_TRACE 8 /* record per-cell solve timelines for dd_get_trace       */ /* compute the warm-start network's inputs before, and
+#define DD_FLAG_COLLECT 2 /* compute the warm-start network's inputs before, and
                              its training targets after, every cell solve, for
                              dd_collect_cells (requires cell_size 4)              */
+#define DD_FLAG_NO_GRAPH 4 /* dd_step runs its steps one by one instead of
+                              replaying a captured CUDA graph                     */
+#define DD_FLAG_TRACE 8 /* record per-cell solve timelines for dd_get_trace       */
+#define DD_FLAG_MLP_EVERY_SOLVE 16 /* DD_WARM_MLP: evaluate the network before
+                                      every solve (predicted change of the dual),
+                                      not only before solves without a previous
+                                      dual                                        */
 
 typedef struct dd_grid {
     int32_t N1, N2; /* pixels per axis                                          */

@@ -26,6 +26,7 @@ DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
 DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
 DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
+DD_FLAG_MLP_EVERY_SOLVE = 16
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 
 EXPORTS = [

@@ -609,11 +609,11 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     CK(cudaEventRecord(c->ev[0], c->stream));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
-    if (c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT)) {
+    if (mlp_active(c, part) || (c->opt.flags & DD_FLAG_COLLECT)) {
         // network inputs from the union boxes; the prediction initialises the solves
         RET(launch_feat(c, part));
         c->n_launch += 1;
-        if (c->opt.warm == DD_WARM_MLP) {
+        if (mlp_active(c, part)) {
             RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
             c->n_launch += 4;
         }
@@ -771,7 +771,7 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
     if (!cls_cells[3].empty()) CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
-    if (c->opt.warm == DD_WARM_MLP && with_c2b)
+    if (mlp_keeps_old(c) && with_c2b)
         CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
                            cudaMemcpyDeviceToDevice, c->stream));
     if (with_c2b) {
@@ -817,7 +817,7 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     c->cur = 1 - c->cur;
     P.warm_valid = true;
     P.solved = true;
-    P.pred_old_valid = c->opt.warm == DD_WARM_MLP;
+    P.pred_old_valid = mlp_keeps_old(c);
     c->last_part = part;
     c->flow_ready = true;
     return fill_stats(c, part, st);
@@ -977,10 +977,10 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     CK(cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
-    if (c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT)) {
+    if (mlp_active(c, part) || (c->opt.flags & DD_FLAG_COLLECT)) {
         RET(launch_feat(c, part));
         c->n_launch += 1;
-        if (c->opt.warm == DD_WARM_MLP) {
+        if (mlp_active(c, part)) {
             RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
             c->n_launch += 4;
         }
@@ -1011,7 +1011,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     CK(cudaEventRecord(c->ev_join, c->side));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (g.cl_cap > 0) CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
-    if (c->opt.warm == DD_WARM_MLP)
+    if (mlp_keeps_old(c))
         CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
                            cudaMemcpyDeviceToDevice, c->stream));
     const long long dc[3] = {0, g.h2, g.w2};
@@ -1126,7 +1126,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     const int guard = *c->h_guard;
     if (guard == 0) {
         c->cur = 1 - parity;
-        for (auto& P : c->part) { P.warm_valid = true; P.solved = true; P.pred_old_valid = c->opt.warm == DD_WARM_MLP; }
+        for (auto& P : c->part) { P.warm_valid = true; P.solved = true; P.pred_old_valid = mlp_keeps_old(c); }
         c->last_part = 1;
         c->flow_ready = false;
         *used_graph = true;
@@ -1148,7 +1148,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
         return step_eager(c, sa, sb, sf, 0);
     }
     c->part[0].warm_valid = c->part[0].solved = true;
-    c->part[0].pred_old_valid = c->opt.warm == DD_WARM_MLP;
+    c->part[0].pred_old_valid = mlp_keeps_old(c);
     {
         int r = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
@@ -1160,7 +1160,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
         return step_eager(c, sa, sb, sf, 1);
     }
     c->part[1].warm_valid = c->part[1].solved = true;
-    c->part[1].pred_old_valid = c->opt.warm == DD_WARM_MLP;
+    c->part[1].pred_old_valid = mlp_keeps_old(c);
     {
         int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);  // B ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;

@@ -1768,8 +1768,8 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.pre_cap = (long long)c->pre_cap;
     A.gscratch = nullptr; A.goff = nullptr;
     A.affine = (c->opt.warm == DD_WARM_AFFINE || c->opt.warm == DD_WARM_MLP) ? 1 : 0;
-    A.pred = (c->opt.warm == DD_WARM_MLP) ? c->d_pred : nullptr;
-    A.pred_old = (c->opt.warm == DD_WARM_MLP && P.pred_old_valid) ? c->d_pred_old[part] : nullptr;
+    A.pred = mlp_active(c, part) ? c->d_pred : nullptr;
+    A.pred_old = (mlp_active(c, part) && mlp_keeps_old(c) && P.pred_old_valid) ? c->d_pred_old[part] : nullptr;
     A.targ = (c->opt.flags & DD_FLAG_COLLECT) ? c->d_targ : nullptr;
     return A;
 }

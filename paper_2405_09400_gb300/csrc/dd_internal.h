@@ -211,6 +211,14 @@ int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, in
                         int threads, int cl, size_t smem, int nclusters, cudaStream_t stream,
                         const int* count_dev = nullptr);
 int half_cluster_size(int requested);
+// the warm-start network runs before this half-iteration's solves of `part`
+inline bool mlp_active(const dd_ctx* c, int part) {
+    return c->opt.warm == DD_WARM_MLP && (!c->part[part].warm_valid || (c->opt.flags & DD_FLAG_MLP_EVERY_SOLVE));
+}
+// the previous solve's network outputs are kept for the predicted change of the dual
+inline bool mlp_keeps_old(const dd_ctx* c) {
+    return c->opt.warm == DD_WARM_MLP && (c->opt.flags & DD_FLAG_MLP_EVERY_SOLVE);
+}
 // stored X duals of a partition: a <- log2 mu + f (a - log2 mu) (eps change by 1 / f)
 int launch_rescale_alpha(dd_ctx* c, int part, double f);
 int half_occupancy(int threads, size_t smem);
