@@ -1271,21 +1271,22 @@ struct ClassCaps {
 // thread-block clusters. Work key = h w max(1, previous iterations); the cluster
 // class takes whole quarter-octave key buckets from the top while at most
 // cl_cap cells are taken (dd_api.cu applies the same rule on the host). Each
-// list is ordered by descending octave of the key.
+// list is ordered by descending quarter-octave of the key (longest expected
+// solves first).
 __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __restrict__ chdr,
                                                    const int32_t* __restrict__ iters, ClassCaps cc,
                                                    int32_t* __restrict__ corder, int* __restrict__ ccount,
                                                    long long* __restrict__ goff, const long long* __restrict__ tot,
                                                    int* __restrict__ guard, int stage) {
-    constexpr int NBK = 48, NFB = 4 * NBK;
-    __shared__ int cnt[2][NBK];
-    __shared__ int offs[2][NBK];
+    constexpr int NFB = 192;  // quarter-octave buckets of the work key
+    __shared__ int cnt[2][NFB];
+    __shared__ int offs[2][NFB];
     __shared__ int cntf[NFB];
     __shared__ int bstar, clpos;
     __shared__ unsigned long long gsum;
     __shared__ int bad;
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int k = tid; k < 2 * NBK; k += T) (&cnt[0][0])[k] = 0;
+    for (int k = tid; k < 2 * NFB; k += T) (&cnt[0][0])[k] = 0;
     for (int k = tid; k < NFB; k += T) cntf[k] = 0;
     if (tid == 0) {
         gsum = 0;
@@ -1293,7 +1294,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
         bad = (tot[PT_COMP] > cc.comp || tot[PT_OUT] > cc.pool) ? 1 : 0;
     }
     __syncthreads();
-    // cls: 0 large, 1 small; bk: octave of the key; fb: quarter octave; el: may be clustered
+    // cls: 0 large, 1 small; fb: quarter octave of the key (list order); el: may be clustered
     auto classify = [&](int J, int& cls, int& bk, int& fb, bool& el) {
         const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
         const long long a = (long long)h * padw(w);
@@ -1309,7 +1310,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
         if (el)
             atomicAdd(&cntf[fb], 1);
         else
-            atomicAdd(&cnt[cls][bk], 1);
+            atomicAdd(&cnt[cls][fb], 1);
         const int h = chdr[CH_N * J + CH_H], w = chdr[CH_N * J + CH_W];
         const long long a = (long long)h * padw(w);
         if (cls == 0 && !(a <= cc.a0 && h <= cc.h0 && w <= cc.w0)) {
@@ -1330,10 +1331,10 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
             bs_ = f;
         }
         bstar = bs_;
-        for (int f = 0; f < bs_; ++f) cnt[0][f >> 2] += cntf[f];
+        for (int f = 0; f < bs_; ++f) cnt[0][f] += cntf[f];
         for (int c = 0; c < 2; ++c) {
             int run = 0;
-            for (int b = NBK - 1; b >= 0; --b) {  // descending keys
+            for (int b = NFB - 1; b >= 0; --b) {  // descending keys
                 offs[c][b] = run;
                 run += cnt[c][b];
             }
@@ -1350,7 +1351,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
         if (el && fb >= bstar) {
             corder[2LL * ncell + atomicAdd(&clpos, 1)] = J;
         } else {
-            const int pos = atomicAdd(&offs[cls][bk], 1);
+            const int pos = atomicAdd(&offs[cls][fb], 1);
             corder[(long long)cls * ncell + pos] = J;
         }
     }
