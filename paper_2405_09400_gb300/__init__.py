@@ -236,17 +236,24 @@ def dd_step(ctx, n=1, stats=True):
     return (sa.as_dict(), sb.as_dict(), sf.as_dict()) if stats else rc
 
 
-def _boxes_call(fn, ctx, nhdr, *lead):
+def _boxes_call(fn, ctx, nhdr, *lead, out=None):
     cnt = C.c_size_t(0)
     hdr = np.zeros((nhdr, 4), dtype=np.int32)
     _check(fn(ctx, *lead, _ptr(hdr, _i32p), None, C.byref(cnt)), fn.__name__)
-    data = np.zeros(cnt.value, dtype=np.float64)
+    n = cnt.value
+    if out is not None and out.dtype == np.float64 and out.flags.c_contiguous and out.size >= n:
+        data = out[:n]  # caller's buffer (e.g. pinned host memory)
+    else:
+        data = np.zeros(n, dtype=np.float64)
     _check(fn(ctx, *lead, _ptr(hdr, _i32p), _ptr(data, _f64p), C.byref(cnt)), fn.__name__)
     return hdr, data
 
 
-def dd_get_plan(ctx, nbasic):
-    return _boxes_call(load().dd_get_plan, ctx, nbasic)
+def dd_get_plan(ctx, nbasic, out=None):
+    """Current plan as (nbasic x 4 int32 headers, packed float64 boxes); `out`: an
+    optional float64 buffer (e.g. pinned) the boxes are written into when large
+    enough (the returned array is then a view of it)."""
+    return _boxes_call(load().dd_get_plan, ctx, nbasic, out=out)
 
 
 def dd_get_composite(ctx, part, ncell):

@@ -117,67 +117,76 @@ void build_part(dd_ctx* c, int part, std::vector<int32_t>& members, std::vector<
         }
 }
 
-int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
+// box headers of the pool layout (rows of stride ceil(w/4)*4) and each box's
+// offset in the packed array; bounds and sizes checked (host, O(#cells))
+int plan_layout(dd_ctx* c, const int32_t* hdr, size_t n, std::vector<int32_t>& bh, std::vector<long long>& soff,
+                size_t* total) {
     const int nb = c->nb;
-    std::vector<int32_t> bh((size_t)BH_N * nb, 0);
-    size_t total = 0, src = 0;
+    bh.assign((size_t)BH_N * nb, 0);
+    soff.assign((size_t)nb + 1, 0);
+    size_t tot = 0, src = 0;
     for (int i = 0; i < nb; ++i) {
-        int h = hdr[4 * i + 2], w = hdr[4 * i + 3];
+        const int o1 = hdr[4 * i], o2 = hdr[4 * i + 1], h = hdr[4 * i + 2], w = hdr[4 * i + 3];
         if (h < 0 || w < 0 || (h == 0) != (w == 0)) return DD_ERR_ARG;
-        int st = (w + 3) & ~3;
-        bh[BH_N * i + BH_O1] = h ? hdr[4 * i] : 0;
-        bh[BH_N * i + BH_O2] = h ? hdr[4 * i + 1] : 0;
+        if (h && (o1 < 0 || o2 < 0 || o1 + h > c->N1 || o2 + w > c->N2)) return DD_ERR_ARG;
+        const int st = (w + 3) & ~3;
+        bh[BH_N * i + BH_O1] = h ? o1 : 0;
+        bh[BH_N * i + BH_O2] = h ? o2 : 0;
         bh[BH_N * i + BH_H] = h;
         bh[BH_N * i + BH_W] = w;
         bh[BH_N * i + BH_STRIDE] = st;
-        bh[BH_N * i + BH_START] = (int32_t)total;
-        total += (size_t)h * st;
+        bh[BH_N * i + BH_START] = (int32_t)tot;
+        soff[i] = (long long)src;
+        tot += (size_t)h * st;
         src += (size_t)h * w;
+        if (tot > (size_t)INT32_MAX) return DD_ERR_POOL;
     }
+    soff[nb] = (long long)src;
     if (src != n) return DD_ERR_ARG;
-    if (total > (size_t)INT32_MAX) return DD_ERR_POOL;
-    std::vector<float> buf(total, 0.f);
-    src = 0;
-    for (int i = 0; i < nb; ++i) {
-        int h = bh[BH_N * i + BH_H], w = bh[BH_N * i + BH_W], st = bh[BH_N * i + BH_STRIDE];
-        size_t s0 = bh[BH_N * i + BH_START];
-        for (int r = 0; r < h; ++r)
-            for (int q = 0; q < w; ++q) buf[s0 + (size_t)r * st + q] = (float)data[src++];
-    }
-    RET(ensure_floats(c, &c->pool[c->cur], &c->pool_cap[c->cur], total));
-    RET(h2d(c->pool[c->cur], buf.data(), total, c->stream));
-    RET(h2d(c->bhdr[c->cur], bh.data(), bh.size(), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->n_h2d += (long long)(sizeof(float) * total + sizeof(int32_t) * bh.size());
-    c->part[0].solved = c->part[1].solved = false;
-    c->flow_ready = false;
-    c->last_part = -1;
+    *total = tot;
     return DD_OK;
 }
 
-int validate_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
-    std::vector<double> ym((size_t)c->N1 * c->N2, 0.0);
-    size_t src = 0;
-    double xerr = 0.0;
-    for (int i = 0; i < c->nb; ++i) {
-        int o1 = hdr[4 * i], o2 = hdr[4 * i + 1], h = hdr[4 * i + 2], w = hdr[4 * i + 3];
-        if (h < 0 || w < 0 || (h == 0) != (w == 0)) return DD_ERR_ARG;
-        if (h && (o1 < 0 || o2 < 0 || o1 + h > c->N1 || o2 + w > c->N2)) return DD_ERR_ARG;
-        if (src + (size_t)h * w > n) return DD_ERR_ARG;
-        double mass = 0.0;
-        for (int r = 0; r < h; ++r)
-            for (int q = 0; q < w; ++q) {
-                double v = data[src++];
-                if (!(v >= 0.0) || !std::isfinite(v)) return DD_ERR_ARG;
-                mass += v;
-                ym[(size_t)(o1 + r) * c->N2 + o2 + q] += v;
-            }
-        xerr += std::fabs(mass - c->h_m[i]);
-    }
-    if (src != n) return DD_ERR_ARG;
-    double yerr = 0.0;
-    for (size_t k = 0; k < ym.size(); ++k) yerr += std::fabs(ym[k] - c->h_nu[k]);
-    if (xerr > c->opt.plan_tol || yerr > c->opt.plan_tol) return DD_ERR_ARG;
+int ensure_plan64(dd_ctx* c, size_t n) {
+    if (c->plan64_cap >= n && c->d_plan64) return DD_OK;
+    dfree(c->d_plan64);
+    c->plan64_cap = 0;
+    const size_t m = n + n / 4 + 1024;
+    RET(dmalloc(&c->d_plan64, m));
+    c->plan64_cap = m;
+    return DD_OK;
+}
+
+// The caller's FP64 boxes go to the device as they are (one copy) and are packed
+// there into the pool that is not current; with `validate` the device checks
+// the plan in FP64 (entries finite and >= 0, |nu_i| = m_i and sum_i nu_i = nu
+// within plan_tol, L1). The packed plan becomes the state only if it passes.
+int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n, bool validate) {
+    std::vector<int32_t> bh;
+    std::vector<long long> soff;
+    size_t total = 0;
+    RET(plan_layout(c, hdr, n, bh, soff, &total));
+    const int dst = 1 - c->cur;
+    RET(ensure_plan64(c, n));
+    RET(ensure_floats(c, &c->pool[dst], &c->pool_cap[dst], total));
+    RET(h2d(c->d_plan64, data, n, c->stream));
+    RET(h2d(c->d_soff, soff.data(), soff.size(), c->stream));
+    RET(h2d(c->bhdr[dst], bh.data(), bh.size(), c->stream));
+    CK(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 3, c->stream));
+    if (validate) CK(cudaMemsetAsync(c->d_yacc, 0, sizeof(double) * c->N1 * c->N2, c->stream));
+    RET(launch_pack_plan(c, dst, validate));
+    c->n_launch += validate ? 2 : 1;
+    double res[3] = {0.0, 0.0, 0.0};
+    RET(d2h(res, c->d_red, 3, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->n_h2d += (long long)(sizeof(double) * n + sizeof(int32_t) * bh.size() + sizeof(long long) * soff.size());
+    int bad = 0;
+    std::memcpy(&bad, &res[2], sizeof(int));  // the kernels' flag word
+    if (bad || (validate && (!(res[0] <= c->opt.plan_tol) || !(res[1] <= c->opt.plan_tol)))) return DD_ERR_ARG;
+    c->cur = dst;
+    c->part[0].solved = c->part[1].solved = false;
+    c->flow_ready = false;
+    c->last_part = -1;
     return DD_OK;
 }
 
@@ -291,6 +300,7 @@ void dd_destroy(dd_ctx* c) {
     dfree(c->d_trace[0]); dfree(c->d_trace[1]);
     if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
+    dfree(c->d_plan64); dfree(c->d_soff); dfree(c->d_cellmass);
     if (c->h_tot) cudaFreeHost(c->h_tot);
     if (c->h_cbar) cudaFreeHost(c->h_cbar);
     if (c->h_w) cudaFreeHost(c->h_w);
@@ -477,6 +487,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_xhdr, (size_t)CH_N * c->nb));
         TRY(dmalloc(&c->d_yacc, np));
         TRY(dmalloc(&c->d_red, 8));
+        TRY(dmalloc(&c->d_soff, (size_t)c->nb + 1));
+        TRY(dmalloc(&c->d_cellmass, (size_t)c->nb));
         for (auto& e : c->ev)
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         for (auto& e : c->gev)
@@ -516,7 +528,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
                         data.push_back(v >= c->opt.trunc ? v : 0.0);
                     }
             }
-            TRY(upload_plan(c, hdr.data(), data.data(), data.size()));
+            TRY(upload_plan(c, hdr.data(), data.data(), data.size(), false));
         } else {
             if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         }
@@ -531,8 +543,7 @@ fail:
 
 int dd_set_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     if (!c || !hdr || (!data && n)) return DD_ERR_ARG;
-    RET(validate_plan(c, hdr, data, n));
-    return upload_plan(c, hdr, data, n);
+    return upload_plan(c, hdr, data, n, true);
 }
 
 // elapsed milliseconds between two recorded events (0 if they cannot be timed)
@@ -1199,29 +1210,30 @@ int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
 
 int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
     if (!c || !count) return DD_ERR_ARG;
-    std::vector<int32_t> bh((size_t)BH_N * c->nb);
+    const int nb = c->nb;
+    std::vector<int32_t> bh((size_t)BH_N * nb);
     RET(d2h(bh.data(), c->bhdr[c->cur], bh.size(), c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    size_t n = 0, used = 0;
-    for (int i = 0; i < c->nb; ++i) {
+    std::vector<long long> soff((size_t)nb + 1, 0);
+    size_t n = 0;
+    for (int i = 0; i < nb; ++i) {
+        soff[i] = (long long)n;
         n += (size_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
-        used = std::max(used, (size_t)bh[BH_N * i + BH_START] + (size_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_STRIDE]);
     }
+    soff[nb] = (long long)n;
     if (hdr)
-        for (int i = 0; i < c->nb; ++i)
+        for (int i = 0; i < nb; ++i)
             for (int k = 0; k < 4; ++k) hdr[4 * i + k] = bh[BH_N * i + k];
     if (!data) { *count = n; return DD_OK; }
     if (*count < n) return DD_ERR_ARG;
-    std::vector<float> buf(used);
-    RET(d2h(buf.data(), c->pool[c->cur], used, c->stream));
+    // unpack on the device (FP32 pool rows -> packed FP64) and copy out once
+    RET(ensure_plan64(c, n));
+    RET(h2d(c->d_soff, soff.data(), soff.size(), c->stream));
+    RET(launch_unpack_plan(c));
+    c->n_launch += 1;
+    RET(d2h(data, c->d_plan64, n, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->n_d2h += (long long)(sizeof(float) * used + sizeof(int32_t) * bh.size());
-    size_t k = 0;
-    for (int i = 0; i < c->nb; ++i) {
-        const int32_t* b = &bh[BH_N * i];
-        for (int r = 0; r < b[BH_H]; ++r)
-            for (int q = 0; q < b[BH_W]; ++q) data[k++] = buf[(size_t)b[BH_START] + (size_t)r * b[BH_STRIDE] + q];
-    }
+    c->n_d2h += (long long)(sizeof(double) * n + sizeof(int32_t) * bh.size());
     *count = n;
     return DD_OK;
 }

@@ -126,6 +126,12 @@ struct dd_ctx {
     // l1_y scratch
     double* d_yacc = nullptr;
     double* d_red = nullptr;
+    // plan transfer (dd_set_plan / dd_get_plan): packed FP64 boxes, their offsets,
+    // per-cell masses of a plan being checked
+    double* d_plan64 = nullptr;
+    size_t plan64_cap = 0;
+    long long* d_soff = nullptr;
+    double* d_cellmass = nullptr;
 
     cudaEvent_t ev[8] = {};
     cudaStream_t side = nullptr;  // second stream: the large-box class of cells
@@ -219,6 +225,12 @@ inline bool mlp_active(const dd_ctx* c, int part) {
 inline bool mlp_keeps_old(const dd_ctx* c) {
     return c->opt.warm == DD_WARM_MLP && (c->opt.flags & DD_FLAG_MLP_EVERY_SOLVE);
 }
+// plan transfer: pack c->d_plan64 (packed FP64 boxes at offsets c->d_soff) into
+// pool[dst] with the headers in bhdr[dst] (validate: cell masses and the Y
+// marginal against m and nu into d_red[0..1], bad-value flag in d_red[2]);
+// unpack the current pool into c->d_plan64
+int launch_pack_plan(dd_ctx* c, int dst, bool validate);
+int launch_unpack_plan(dd_ctx* c);
 // stored X duals of a partition: a <- log2 mu + f (a - log2 mu) (eps change by 1 / f)
 int launch_rescale_alpha(dd_ctx* c, int part, double f);
 int half_occupancy(int threads, size_t smem);

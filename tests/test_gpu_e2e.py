@@ -412,3 +412,47 @@ def test_eps_schedule_across_hybrid_iterations(dd):
     Es, its = run([(4 * eps, 4), (2 * eps, 4), (eps, 12)])
     assert abs(Ed - Eref) <= 2e-4 * Eref and abs(Es - Eref) <= 2e-4 * Eref, (Ed, Es, Eref)
     assert its <= 0.8 * itd, (its, itd)
+
+
+def test_set_plan_roundtrip_and_rejection(dd):
+    """dd_set_plan checks the plan on the device in FP64 and packs it into the
+    pool that is not current: a feasible plan round-trips through dd_get_plan
+    bit for bit; an infeasible one (mass moved between cells, a negative or a
+    non-finite entry, a box outside the grid) is rejected with DD_ERR_ARG and
+    the state is left as it was."""
+    mu, nu, eps, p = synth.workload("dd32", 0)
+    g = dd.DomDec(mu, nu, eps, 4, tol=1e-6, max_iter=50000)
+    g.step(1)
+    hdr, data = dd.dd_get_plan(g.ctx, g.nbasic)
+    hdr, data = hdr.copy(), data.copy()
+    # the FP32 state round-trips exactly (plan_tol covers the FP32 rounding of the masses)
+    g2 = dd.DomDec(mu, nu, eps, 4, tol=1e-6, max_iter=50000, plan_tol=1e-5)
+    dd.dd_set_plan(g2.ctx, hdr, data)
+    h2, d2 = dd.dd_get_plan(g2.ctx, g2.nbasic)
+    assert np.array_equal(h2, hdr) and np.array_equal(d2, data)
+
+    def rejected(h, d):
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_set_plan(g2.ctx, h, d)
+        assert e.value.code == dd.DD_ERR_ARG
+        h3, d3 = dd.dd_get_plan(g2.ctx, g2.nbasic)
+        assert np.array_equal(h3, hdr) and np.array_equal(d3, data)
+
+    k = int(np.argmax(data))
+    bad = data.copy()
+    bad[k] += 1e-3  # Y and X marginals off
+    rejected(hdr, bad)
+    bad = data.copy()
+    bad[k] = -bad[k]
+    rejected(hdr, bad)
+    bad = data.copy()
+    bad[k] = np.nan
+    rejected(hdr, bad)
+    hb = hdr.copy()
+    i = int(np.flatnonzero(hb[:, 2] > 0)[0])
+    hb[i, 0] = 32 - hb[i, 2] + 1  # box leaves the grid
+    rejected(hb, data)
+    # the state still steps
+    g2.step(1)
+    g.close()
+    g2.close()
