@@ -691,7 +691,8 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     c->seen.n2 = std::max(c->seen.n2, (long long)cls_cells[2].size());
     // class 3: the largest-work cells of classes 0 and 2 on thread-block clusters,
     // by the rule k_classify applies in captured graphs (whole quarter-octave key
-    // buckets from the top, at most cluster_cap cells)
+    // buckets from the top, then the first cells of the next bucket in index
+    // order, cluster_cap cells in all)
     const int ccap = cluster_cap(c);
     if (ccap > 0) {
         std::vector<int> fbk(P.ncell, -1);
@@ -705,17 +706,28 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
                 fbk[J] = fb;
                 ++cntf[fb];
             }
-        int cum = 0, bstar = 192;
+        int cum = 0, bstar = 192, fpart = -1, npart = 0;
         for (int f = 191; f >= 0; --f) {
             if (cntf[f] == 0) continue;
-            if (cum + cntf[f] > ccap) break;
+            if (cum + cntf[f] > ccap) {
+                fpart = f;
+                npart = ccap - cum;
+                break;
+            }
             cum += cntf[f];
             bstar = f;
         }
-        if (cum > 0) {
+        // the partial bucket: its first cells in index order
+        std::vector<char> sel(P.ncell, 0);
+        for (int J = 0, taken = 0; J < P.ncell; ++J) {
+            if (fbk[J] < 0) continue;
+            if (fbk[J] >= bstar) sel[J] = 1;
+            else if (fbk[J] == fpart && taken < npart) { sel[J] = 1; ++taken; }
+        }
+        if (cum + npart > 0) {
             for (int k : {0, 2}) {
                 std::vector<int32_t> keep;
-                for (int32_t J : cls_cells[k]) (fbk[J] >= bstar ? cls_cells[3] : keep).push_back(J);
+                for (int32_t J : cls_cells[k]) (sel[J] ? cls_cells[3] : keep).push_back(J);
                 cls_cells[k].swap(keep);
             }
             for (int32_t J : cls_cells[3]) {

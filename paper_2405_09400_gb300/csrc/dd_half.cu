@@ -1269,8 +1269,9 @@ struct ClassCaps {
 // class 1 small boxes, class 0 large boxes (global-scratch offsets for those
 // beyond the shared-memory capacity), class 2 the largest-work cells solved by
 // thread-block clusters. Work key = h w max(1, previous iterations); the cluster
-// class takes whole quarter-octave key buckets from the top while at most
-// cl_cap cells are taken (dd_api.cu applies the same rule on the host). Each
+// class takes whole quarter-octave key buckets from the top, and from the
+// bucket that would exceed cl_cap its first cells in index order, cl_cap cells
+// in all (dd_api.cu applies the same rule on the host). Each
 // list is ordered by descending quarter-octave of the key (longest expected
 // solves first).
 __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __restrict__ chdr,
@@ -1282,7 +1283,8 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     __shared__ int cnt[2][NFB];
     __shared__ int offs[2][NFB];
     __shared__ int cntf[NFB];
-    __shared__ int bstar, clpos;
+    __shared__ int bstar, clpos, fpart, npart, prank;
+    __shared__ int wsum[32];
     __shared__ unsigned long long gsum;
     __shared__ int bad;
     const int tid = threadIdx.x, T = blockDim.x;
@@ -1291,6 +1293,7 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     if (tid == 0) {
         gsum = 0;
         clpos = 0;
+        prank = 0;
         bad = (tot[PT_COMP] > cc.comp || tot[PT_OUT] > cc.pool) ? 1 : 0;
     }
     __syncthreads();
@@ -1323,15 +1326,24 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
     __syncthreads();
     if (tid == 0) {
         if ((long long)gsum > cc.gscr) bad = 1;
-        int cum = 0, bs_ = NFB;
+        // whole buckets from the top, then the first cells (ascending index) of
+        // the bucket that would overflow the cap
+        int cum = 0, bs_ = NFB, fp = -1, np_ = 0;
         for (int f = NFB - 1; f >= 0; --f) {
             if (cntf[f] == 0) continue;
-            if (cum + cntf[f] > cc.cl_cap) break;
+            if (cum + cntf[f] > cc.cl_cap) {
+                fp = f;
+                np_ = cc.cl_cap - cum;
+                break;
+            }
             cum += cntf[f];
             bs_ = f;
         }
         bstar = bs_;
-        for (int f = 0; f < bs_; ++f) cnt[0][f] += cntf[f];
+        fpart = fp;
+        npart = np_;
+        for (int f = 0; f < bs_; ++f) cnt[0][f] += cntf[f] - (f == fp ? np_ : 0);
+        cum += np_;
         for (int c = 0; c < 2; ++c) {
             int run = 0;
             for (int b = NFB - 1; b >= 0; --b) {  // descending keys
@@ -1344,16 +1356,33 @@ __global__ void __launch_bounds__(1024) k_classify(int ncell, const int32_t* __r
         if (bad) atomicCAS(guard, 0, stage);
     }
     __syncthreads();
-    for (int J = tid; J < ncell; J += T) {
-        int cls, bk, fb;
-        bool el;
-        classify(J, cls, bk, fb, el);
-        if (el && fb >= bstar) {
-            corder[2LL * ncell + atomicAdd(&clpos, 1)] = J;
-        } else {
-            const int pos = atomicAdd(&offs[cls][fb], 1);
-            corder[(long long)cls * ncell + pos] = J;
+    // chunks of T cells in ascending index order: a block scan ranks the cells
+    // of the partial bucket
+    for (int base = 0; base < ncell; base += T) {
+        const int J = base + tid;
+        int cls = 1, bk = 0, fb = 0;
+        bool el = false;
+        if (J < ncell) classify(J, cls, bk, fb, el);
+        const bool inpart = J < ncell && el && fb == fpart;
+        const unsigned bal = __ballot_sync(0xffffffffu, inpart);
+        const int lane = tid & 31, wid = tid >> 5;
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = prank;
+        for (int k = 0; k < wid; ++k) before += wsum[k];
+        const int rank = before + __popc(bal & ((1u << lane) - 1u));
+        if (J < ncell) {
+            if (el && (fb >= bstar || (inpart && rank < npart))) {
+                corder[2LL * ncell + atomicAdd(&clpos, 1)] = J;
+            } else {
+                const int pos = atomicAdd(&offs[cls][fb], 1);
+                corder[(long long)cls * ncell + pos] = J;
+            }
         }
+        __syncthreads();
+        if (tid == 0)
+            for (int k = 0; k < (T >> 5); ++k) prank += wsum[k];
+        __syncthreads();
     }
 }
 

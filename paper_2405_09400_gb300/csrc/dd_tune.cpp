@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "dd_internal.h"
@@ -204,6 +205,8 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
         ++n;
     }
     const int sides[3][2] = {{768, 48}, {1536, 64}, {3072, 96}};
+    std::vector<std::pair<double, dd_tuning>> one_cta;  // phase 1 results
+    if (r == DD_OK) one_cta.push_back({def_ms, defaults});
     for (int t1 : {128, 256}) {
         for (int t0 : {256, 512}) {
             for (const auto& sd : sides) {
@@ -214,11 +217,39 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
                 t.threads[2] = t0;
                 t.small_area = sd[0];
                 t.small_side = sd[1];
+                t.cl_size = 1;
+                t.cl_cells = 0;
                 if (std::memcmp(t.threads, defaults.threads, sizeof(t.threads)) == 0 &&
-                    t.small_area == defaults.small_area && t.small_side == defaults.small_side)
+                    t.small_area == defaults.small_area && t.small_side == defaults.small_side &&
+                    defaults.cl_size == 1)
                     continue;
                 if (half_smem_bytes(c, t.small_area, t.small_side, t.small_side) > (size_t)half_kernel_max_smem())
                     continue;
+                double ms = 0.0;
+                r = trial(c, t, saved, &ms);
+                ++n;
+                if (r == DD_OK) {
+                    one_cta.push_back({ms, t});
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = t;
+                    }
+                }
+            }
+        }
+    }
+    // then thread-block clusters for the largest-work cells, on top of the two
+    // best one-CTA configurations
+    std::sort(one_cta.begin(), one_cta.end(),
+              [](const std::pair<double, dd_tuning>& a, const std::pair<double, dd_tuning>& b) { return a.first < b.first; });
+    for (size_t b = 0; b < std::min<size_t>(2, one_cta.size()); ++b) {
+        for (int cls : {2, 4}) {
+            for (int cells : {16, 32, 48}) {
+                if (r != DD_OK) break;
+                if (c->opt.flags & DD_FLAG_COLLECT) break;  // training targets: one-CTA solves only
+                dd_tuning t = one_cta[b].second;
+                t.cl_size = cls;
+                t.cl_cells = cells;
                 double ms = 0.0;
                 r = trial(c, t, saved, &ms);
                 ++n;
@@ -226,25 +257,6 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
                     best_ms = ms;
                     best = t;
                 }
-            }
-        }
-    }
-    // then thread-block clusters for the largest-work cells, on top of the best
-    // configuration so far
-    const dd_tuning base = best;
-    for (int cls : {2, 4}) {
-        for (int cells : {16, 32}) {
-            if (r != DD_OK) break;
-            if (c->opt.flags & DD_FLAG_COLLECT) break;  // training targets: one-CTA solves only
-            dd_tuning t = base;
-            t.cl_size = cls;
-            t.cl_cells = cells;
-            double ms = 0.0;
-            r = trial(c, t, saved, &ms);
-            ++n;
-            if (r == DD_OK && ms < best_ms) {
-                best_ms = ms;
-                best = t;
             }
         }
     }
