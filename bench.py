@@ -245,6 +245,35 @@ def run_ours(args):
     achieved = k_terms / (k_ms * 1e-3)
     hbm_gbs = (sum(warm["hbm_bytes"]) / len(warm["hbm_bytes"])) / (k_ms * 1e-3) / 1e9
 
+    # cell-LSE microbenchmark (the paper's Fig. 10 setting adapted): every cell of
+    # the bench state solved with a fixed iteration count, so the cell kernels'
+    # exp throughput is measured without the tail of slow cells
+    micro = None
+    if not args.no_micro:
+        gm = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_PREV,
+                       **SOLVER)
+        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        gm.step(args.warmup, stats=False)
+        hdr_m, data_m = dd.dd_get_plan(gm.ctx, gm.nbasic)
+        gm.close()
+        K = 100
+        gm = dd.DomDec(mu, nu, eps, p["s"], boxes=(hdr_m, data_m), fixed_iters=K, plan_tol=1e-5, warm=dd.DD_WARM_COLD,
+                       flags=dd.DD_FLAG_NO_GRAPH)
+        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        gm.iterate(0)  # warm-up (sizes, allocation)
+        rs = []
+        for part in (0, 1, 0, 1):
+            st = gm.iterate(part)
+            rs.append((st["lse_terms"], st["ms_cells"], st["ncell"]))
+        gm.close()
+        terms = sum(r[0] for r in rs)
+        ms = sum(r[1] for r in rs)
+        ach = terms / (ms * 1e-3)
+        micro = {"iterations_per_cell": K, "half_iterations": len(rs), "ms_per_half_iteration": round(ms / len(rs), 4),
+                 "us_per_sinkhorn_iteration_all_cells": round(1e3 * ms / len(rs) / K, 3),
+                 "achieved_texp2_s": round(ach / 1e12, 4), "peak_texp2_s": round(ex2_peak / 1e12, 4),
+                 "frac": round(ach / ex2_peak, 5)}
+
     # end to end through the C ABI with host buffers: H2D of the plan, one
     # hybrid iteration (graph replay), D2H of the plan, every step (pinned host memory)
     e2e = None
@@ -320,6 +349,7 @@ def run_ours(args):
                      "achieved": round(achieved / 1e12, 4), "peak": round(ex2_peak / 1e12, 4), "unit": "Texp2/s",
                      "frac": round(achieved / ex2_peak, 5), "traffic": None, "kernel_ms_mean": round(k_ms, 4),
                      "work_per_launch": k_terms},
+        "cell_lse_fixed_iterations": micro,
         "clocks": clocks,
         "gpu_launches": int(warm["launches"]),
         "e2e": e2e,
@@ -422,6 +452,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration (no autotuning)")
+    ap.add_argument("--no-micro", action="store_true", help="skip the fixed-iteration cell-LSE microbenchmark")
     ap.add_argument("--tuning", default="", help="fixed launch configuration t0,t1,t2,small_area,small_side"
                                                "[,cl_size,cl_cells] instead of autotuning (profiling runs)")
     ap.add_argument("--arms", default="plain,warm,affine,eager",

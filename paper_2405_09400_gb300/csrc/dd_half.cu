@@ -694,13 +694,21 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         const float4* b4 = reinterpret_cast<const float4*>(b_p);
         const float4* t24 = reinterpret_cast<const float4*>(S.tab2);
         const int nq = (w + 3) >> 2;  // float4 groups holding data per row
+        // 2D cursors of the per-entry loops (no integer division per entry):
+        // Y-update 1 over (u1, v2) with rows of w, Y-update 2 over (v1, g4) with rows of nq
+        const int y1u0 = tid / w, y1v0 = tid - y1u0 * w, y1du = NT / w, y1dv = NT - y1du * w;
+        const int y2u0 = rlo + tid / nq, y2v0 = tid - (tid / nq) * nq, y2du = NT / nq, y2dv = NT - y2du * nq;
+        int lp2 = 0, lpx = 0;
+        while ((1 << lp2) < P2) ++lp2;
+        while ((1 << lpx) < PX) ++lpx;
         while (true) {
             ++it;
             // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1, u2) - K2(u2, v2)]
             // (full 8 x 8 blocks: all operands loaded first, fixed trip counts)
             if (hx == 8 && wx == 8) {
-                for (int q = tid; q < 8 * w; q += NT) {
-                    const int u1 = q / w, v2 = q - u1 * w;
+                int u1 = y1u0, v2 = y1v0;
+                for (int q = tid; q < 8 * w; q += NT, u1 += y1du, v2 += y1dv) {
+                    if (v2 >= w) { v2 -= w; ++u1; }
                     const float4 a0 = reinterpret_cast<const float4*>(aC + u1 * 8)[0];
                     const float4 a1 = reinterpret_cast<const float4*>(aC + u1 * 8)[1];
                     const float* tb = S.tab2 + v2;
@@ -730,8 +738,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     S.T[u1 * bs + v2] = m + lg2f(sacc);
                 }
             } else
-            for (int q = tid; q < hx * w; q += NT) {
-                const int u1 = q / w, v2 = q - u1 * w;
+            for (int q = tid, u1 = y1u0, v2 = y1v0; q < hx * w; q += NT, u1 += y1du, v2 += y1dv) {
+                if (v2 >= w) { v2 -= w; ++u1; }
                 const float* ar = aC + u1 * wx;
                 const float* tb = S.tab2 + v2;
                 float m = first ? 0.f : S.T[u1 * bs + v2];
@@ -759,8 +767,9 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             // four adjacent v2 per thread (float4 rows of T, b, log2 nu_J)
             if (NTB < 512 && hx == 8 && !first) {
                 // full blocks after the first iteration: operands loaded first
-                for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
-                    const int v1 = q / nq, g4 = q - v1 * nq;
+                int v1 = y2u0, g4 = y2v0;
+                for (int q = rlo * nq + tid; q < rhi * nq; q += NT, v1 += y2du, g4 += y2dv) {
+                    if (g4 >= nq) { g4 -= nq; ++v1; }
                     const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
                     const float4 bp4 = b4[v1 * bq + g4];
                     const float* tb = S.tab1 + v1;
@@ -855,8 +864,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     }
                 }
             } else
-            for (int q = rlo * nq + tid; q < rhi * nq; q += NT) {
-                const int v1 = q / nq, g4 = q - v1 * nq;
+            for (int q = rlo * nq + tid, v1 = y2u0, g4 = y2v0; q < rhi * nq; q += NT, v1 += y2du, g4 += y2dv) {
+                if (g4 >= nq) { g4 -= nq; ++v1; }
                 const float4 ln4 = reinterpret_cast<const float4*>(lgnu_p)[v1 * bq + g4];
                 const float4 bp4 = b4[v1 * bq + g4];
                 const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
@@ -904,7 +913,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             for (int base = 0; base < nxl * PX; base += NT) {
                 const int q = base + tid;
                 const bool act = q < nxl * PX;
-                const int ql = act ? q / PX : 0, p = q - (q / PX) * PX;
+                const int ql = act ? (q >> lpx) : 0, p = q & (PX - 1);
                 const int line = rlo * wx + ql;
                 const int v1 = line / wx, u2 = line - v1 * wx;
                 const float4* br = b4 + v1 * bq;
@@ -961,8 +970,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             for (int base = 0; base < nx * P2; base += NT) {
                 const int q = base + tid;
                 const bool act = q < nx * P2;
-                const int line = act ? q / P2 : 0, part = q - (q / P2) * P2;
-                const int u1 = line / wx, u2 = line - u1 * wx;
+                const int line = act ? (q >> lp2) : 0, part = q & (P2 - 1);
+                const int u1 = wx == 8 ? (line >> 3) : line / wx, u2 = line - u1 * wx;
                 const float lg = act ? S.lgm[line] : DD_NEG;
                 const bool live = lg > 0.5f * DD_NEG;
                 const float* Rc = S.R + u2;
