@@ -14,7 +14,8 @@
 //    a spanning tree by zero-flow arcs s_p -> t_i along a spanning tree of the
 //    cell grid; it is strongly feasible, and the leaving arc is chosen by
 //    Cunningham's rule (last blocking arc from the apex), which rules out cycling;
-//  * entering arcs by block search over the reduced costs;
+//  * entering arcs from a candidate list of arcs with negative reduced cost,
+//    refilled by block scans;
 //  * the tree is kept in preorder-thread form (parent, thread, reverse thread,
 //    subtree size, last node of the subtree): the join of a pivot cycle is found
 //    by climbing from the side with the smaller subtree, the cut subtree is
@@ -236,43 +237,63 @@ struct NetworkSimplex {
         return true;
     }
 
-    // most negative reduced cost over arcs [a, b); tree arcs price at exactly 0
-    // (integer potentials), so they need no test and are never chosen
-    void scan(int a, int b, int& best, int64_t& best_rc) const {
-        const int64_t* cst = cost.data();
-        const int64_t* pt = pot.data();
-        const int* tl = tail.data();
-        const int* hd = head.data();
-        for (int e = a; e < b; ++e) {
-            const int64_t r = cst[e] + pt[tl[e]] - pt[hd[e]];
-            if (r < best_rc) {
-                best_rc = r;
-                best = e;
-            }
-        }
-    }
+    // Entering arcs by a candidate list: a major pass scans blocks of arcs (in a
+    // rotating order) until it has collected up to kCand arcs of negative reduced
+    // cost; minor passes re-price only the list and pivot on its most negative
+    // arc, dropping arcs that are no longer eligible, until the list is empty.
+    // Tree arcs price at exactly 0 (integer potentials) and are never taken.
+    static constexpr int kCand = 256;
+    std::vector<int> cand;
 
     bool run() {
         const int block = mcf_block > 0 ? mcf_block : std::max(16, (int)std::sqrt((double)na));
+        cand.clear();
         int next = 0;
+        const int64_t* cst = cost.data();
+        const int* tl = tail.data();
+        const int* hd = head.data();
         while (true) {
             int best = -1;
             int64_t best_rc = 0;
-            int scanned = 0;
-            while (scanned < na) {
-                const int lim = std::min(block, na - scanned);
-                const int n1 = std::min(lim, na - next);  // the block wraps at most once
-                scan(next, next + n1, best, best_rc);
-                if (lim > n1) scan(0, lim - n1, best, best_rc);
-#ifdef MCF_STATS
-                st_scan += lim;
-#endif
-                next += lim;
-                if (next >= na) next -= na;
-                scanned += lim;
-                if (best >= 0) break;
+            for (size_t k = 0; k < cand.size();) {  // minor pass
+                const int e = cand[k];
+                const int64_t r = rc(e);
+                if (r >= 0) {
+                    cand[k] = cand.back();
+                    cand.pop_back();
+                    continue;
+                }
+                if (r < best_rc) {
+                    best_rc = r;
+                    best = e;
+                }
+                ++k;
             }
-            if (best < 0) return true;
+            if (best < 0) {  // major pass
+                cand.clear();
+                const int64_t* pt = pot.data();
+                int scanned = 0;
+                while (scanned < na && (int)cand.size() < kCand) {
+                    const int lim = std::min(block, na - scanned);
+                    for (int t = 0; t < lim; ++t) {
+                        const int e = next;
+                        next = (next + 1 == na) ? 0 : next + 1;
+                        const int64_t r = cst[e] + pt[tl[e]] - pt[hd[e]];
+                        if (r < 0) {
+                            cand.push_back(e);
+                            if (r < best_rc) {
+                                best_rc = r;
+                                best = e;
+                            }
+                        }
+                    }
+#ifdef MCF_STATS
+                    st_scan += lim;
+#endif
+                    scanned += lim;
+                }
+                if (best < 0) return true;  // no arc of negative reduced cost: optimal
+            }
             if (!pivot(best)) return false;
         }
     }
