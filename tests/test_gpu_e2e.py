@@ -456,3 +456,37 @@ def test_set_plan_roundtrip_and_rejection(dd):
     g2.step(1)
     g.close()
     g2.close()
+
+
+@pytest.mark.parametrize("cl", [2, 4])
+def test_clusters_on_boxes_beyond_shared_memory(dd, cl):
+    """The 512 x 512 uneven workload's largest boxes (~5e4 pixels) live in the
+    global scratch: solved by clusters, each CTA writes its own rows of the
+    scratch arrays. Fixed iterations from the KR plan: every cell matches the
+    one-CTA run to FP32 rounding; then one tolerance-mode hybrid iteration keeps
+    the state feasible."""
+    mu, nu, eps, p = synth.workload("uneven512", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    m = Geometry(512, 512, 4).basic_masses(mu)
+    res = {}
+    for c in (1, cl):
+        g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, fixed_iters=30, flags=dd.DD_FLAG_TRACE | dd.DD_FLAG_NO_GRAPH)
+        g.set_tuning([512, 256, 512], 1536, 64, cl_size=c, cl_cells=16)
+        st = g.iterate(0)
+        res[c] = (g.plan(), st["objective"], g.trace(0)[:, 3].copy())
+        g.close()
+    assert (res[cl][2] == 512 * cl).sum() >= 8
+    assert abs(res[cl][1] - res[1][1]) <= 1e-6 * abs(res[1][1])
+    for (a1, a2, a), (b1, b2, b), mi in zip(res[1][0], res[cl][0], m):
+        assert (a1, a2, a.shape) == (b1, b2, b.shape)
+        assert np.abs(a - b).sum() <= 2e-5 * mi
+    # tolerance mode (a few cells of this workload reach the iteration cap from the
+    # KR plan, with or without clusters): the state stays feasible
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=2000, eps_levels=2, eps_factor=4.0)
+    g.set_tuning([512, 256, 512], 1536, 64, cl_size=cl, cl_cells=16)
+    sa, sb, sf = g.step(1)
+    E, l1x, l1y = g.objective()
+    assert l1y <= 1e-6 and np.isfinite(E)
+    got = np.array([bb[2].sum() for bb in g.plan()])
+    assert np.allclose(got, m, rtol=1e-5)
+    g.close()
