@@ -264,7 +264,8 @@ struct Smem {
     double* B1;   // maxH: min over u1 of the axis-1 kernel at v1 (FP64)
     double* B2;   // BS: min over u2 of the axis-2 kernel at v2
     double* clx;  // 16: per-CTA sums exchanged within a cluster
-    float* pm;    // 2 * amax: partial X-update log-sums of this CTA's rows (cluster), two buffers
+    float* pm;    // 8 * amax: partial X-update log-sums of every rank of a cluster
+                  // ([buffer][rank][u], two buffers, up to 4 ranks), written by the ranks
     float* coef;  // 16
     int* ctl;     // 32
     long long end;  // bytes used
@@ -297,7 +298,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.a = f; f += 2 * A.amax;
     S.lgm = f; f += A.amax;
     S.muxf = f; f += A.amax;
-    S.pm = f; f += 2 * A.amax;
+    S.pm = f; f += 8 * A.amax;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     S.end = reinterpret_cast<char*>(f + 32) - base;
@@ -965,8 +966,10 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             // In a cluster each CTA first takes the log-sum over its own rows
             // (shifted by its own previous partial) into pm[it & 1].
             float e_loc = 0.f;
-            float* const pcur = S.pm + (it & 1) * A.amax;
-            const float* const pprev = S.pm + ((it + 1) & 1) * A.amax;
+            // [buffer][rank][u]: every rank stores its partials into every rank's
+            // buffer, so that the combine reads local shared memory
+            float* const pcur = S.pm + (it & 1) * 4 * A.amax;
+            const float* const pprev = S.pm + ((it + 1) & 1) * 4 * A.amax + crank * A.amax;
             for (int base = 0; base < nx * P2; base += NT) {
                 const int q = base + tid;
                 const bool act = q < nx * P2;
@@ -1002,7 +1005,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     if (bad) { m = mm; sacc = ss; }
                 }
                 if constexpr (CL > 1) {
-                    if (act && part == 0) pcur[line] = (live && sacc > 0.f) ? m + lg2f(sacc) : DD_NEG;
+                    if (act && part == 0) {
+                        const float L = (live && sacc > 0.f) ? m + lg2f(sacc) : DD_NEG;
+#pragma unroll
+                        for (int r = 0; r < CL; ++r)
+                            cg::this_cluster().map_shared_rank(pcur, (unsigned)r)[crank * A.amax + line] = L;
+                    }
                 } else {
                     if (act && part == 0) {
                         const float an = live ? lg - (m + lg2f(sacc)) : DD_NEG;
@@ -1025,7 +1033,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     float mx = DD_NEG;
 #pragma unroll
                     for (int r = 0; r < CL; ++r) {
-                        pr[r] = cl.map_shared_rank(pcur, (unsigned)r)[u];
+                        pr[r] = pcur[r * A.amax + u];
                         mx = fmaxf(mx, pr[r]);
                     }
                     float sm = 0.f;
@@ -1711,7 +1719,7 @@ size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long m
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
     maxarea = (maxarea + 3) & ~3LL;  // as in carve()
     size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS + 16) + 16;
-    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 6 * (size_t)c->amax + 16 + 32;
+    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 12 * (size_t)c->amax + 16 + 32;
     return bytes + sizeof(float) * fl;
 }
 
