@@ -37,7 +37,7 @@ int mcf_block = 0;  // entering-arc block size; 0 = sqrt(#arcs)
 // size of x's subtree and last[x] the last node of x's subtree in that order, so
 // every subtree is one contiguous run of the thread.
 struct NetworkSimplex {
-    int nn = 0;  // nodes: sources 0..n-1, sinks n..2n-1
+    int nn = 0;  // nodes: source of cell i = 2i, sink of cell i = 2i + 1 (adjacent in memory)
     int na = 0;  // arcs
     int root = 0;
     std::vector<int> tail, head;
@@ -346,8 +346,8 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
             int j = nbr[5 * i + k];
             if (j < 0) continue;
             S->arc_of[5 * i + k] = ns.na++;
-            ns.tail.push_back(i);
-            ns.head.push_back(n + j);
+            ns.tail.push_back(2 * i);  // source of cell i: node 2i, sink of cell j: node 2j + 1
+            ns.head.push_back(2 * j + 1);
             ns.cost.push_back(0);
             ns.flow.push_back(k == 0 ? S->M[i] : 0);
         }
@@ -383,21 +383,21 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
     for (int idx = 0; idx < n; ++idx) {
         int i = order[idx];
         int self = S->arc_of[5 * i];
-        int ti = n + i;
+        int ti = 2 * i + 1, si = 2 * i;
         if (idx > 0) {
             int p = par_cell[i];
-            ns.parent[ti] = p;
+            ns.parent[ti] = 2 * p;
             ns.parc[ti] = via[i];
             ns.in_tree[via[i]] = 1;
         }
         ns.in_tree[self] = 1;
         if (idx == 0) {  // root s_0; t_0 hangs below it
-            ns.parent[ti] = i;
+            ns.parent[ti] = si;
             ns.parc[ti] = self;
-            ns.root = i;
+            ns.root = si;
         } else {
-            ns.parent[i] = ti;
-            ns.parc[i] = self;
+            ns.parent[si] = ti;
+            ns.parc[si] = self;
         }
     }
     ns.build_thread();
