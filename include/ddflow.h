@@ -111,6 +111,10 @@ typedef struct dd_options {
                             budgets that sum to tol mu(X) over the partition, the
                             bound of the paper's batch stopping criterion (Section 5,
                             "Stopping criterion"); 0 (default) = tol mu(X_J) per cell */
+    double tol_gamma;    /* >= 0: with previous iteration counts it_J, the budgets above
+                            are weighted by (it_J / mean it)^tol_gamma and rescaled to
+                            sum to tol mu(X) (the same batch bound), so that slowly
+                            converging cells stop earlier and fast ones later; 0 = off */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */

@@ -254,6 +254,7 @@ void dd_default_options(dd_options* o) {
     o->eps_factor = 4.0;
     o->eps_tol = 1e-3;
     o->tol_share = 0.0;
+    o->tol_gamma = 0.0;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -285,6 +286,7 @@ void dd_destroy(dd_ctx* c) {
     for (int p = 0; p < 2; ++p) {
         DevPart& P = c->part[p];
         dfree(P.members); dfree(P.xblk); dfree(P.mJ); dfree(P.chdr); dfree(P.alpha); dfree(P.gauge);
+        dfree(P.budget);
         dfree(P.iters); dfree(P.err); dfree(P.Ecell); dfree(P.order); dfree(P.comp_b); dfree(P.comp_nu);
         dfree(c->pool[p]); dfree(c->bhdr[p]);
     }
@@ -346,7 +348,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
         c->opt.eps_levels < 0 || c->opt.eps_levels > 8 ||
         (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4) ||
-        !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0)) {
+        !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0) || !(c->opt.tol_gamma >= 0.0 && c->opt.tol_gamma <= 4.0)) {
         delete c;
         return DD_ERR_ARG;
     }
@@ -456,6 +458,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             TRY(dmalloc(&P.iters, P.ncell));
             TRY(dmalloc(&P.err, P.ncell));
             TRY(dmalloc(&P.Ecell, P.ncell));
+            TRY(dmalloc(&P.budget, P.ncell));
             TRY(dmalloc(&c->bhdr[p], (size_t)BH_N * c->nb));
         }
         if (learned) TRY(ensure_learned_buffers(c));
@@ -760,6 +763,8 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
                           c->opt.threads > 0 ? choose_threads(c, 0) : c->tune.threads[2]};
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 8, c->stream));
+    RET(launch_budget(c, part));
+    c->n_launch += 1;
     CK(cudaEventRecord(c->ev[1], c->stream));
     const bool side_used = !cls_cells[1].empty() && (!cls_cells[0].empty() || !cls_cells[2].empty());
     if (side_used) {
@@ -1011,7 +1016,8 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status + 8 * stage, 0, sizeof(int) * 8, c->stream));
     RET(launch_classify(c, part, stage));
-    c->n_launch += 1;
+    RET(launch_budget(c, part));
+    c->n_launch += 2;
     CK(cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal));
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));

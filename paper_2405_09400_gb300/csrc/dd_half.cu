@@ -217,6 +217,7 @@ struct HalfArgs {
     const double* m;
     double tol;
     double tol_share, mbar;  // stop budget tol ((1 - share) mu(X_J) + share mbar)
+    const double* budget;    // per-cell stop budgets (absolute), or null for the formula above
     float omega;  // 1: plain Sinkhorn; (1, 2): fixed over-relaxation; < 0: adaptive
     int max_iter, fixed_iters;
     float trunc;
@@ -674,7 +675,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // the error bookkeeping is FP32: it only decides when to stop, and GB300's
         // FP64 rate (1/64 of FP32) would make a per-iteration FP64 sum by every
         // thread a large share of an iteration of a big cell
-        const float tolm = (float)(A.tol * ((1.0 - A.tol_share) * A.mJ[J] + A.tol_share * A.mbar));
+        const float tolm = (float)(A.budget ? A.budget[J]
+                                            : A.tol * ((1.0 - A.tol_share) * A.mJ[J] + A.tol_share * A.mbar));
         const float eps_tolm = (float)(A.eps_tol * A.mJ[J]);
         int it = 0;
         float err = 0.f, best = 3.0e38f;
@@ -1730,6 +1732,53 @@ size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw) {
 }
 
 namespace {
+// deterministic block sum (fixed thread-to-element assignment and tree order)
+__device__ double block_sum_fixed(double x, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < nw; ++k) t += sh[k];
+        sh[32] = t;
+    }
+    __syncthreads();
+    const double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Stop budgets of the next solves (one CTA): b_J = tol ((1 - s) mu(X_J) + s mbar) w_J
+// rescaled so that sum_J b_J = tol mu(X), with w_J = (it_J / mean it)^gamma from
+// the previous iteration counts (w = 1 without them or for gamma = 0).
+__global__ void __launch_bounds__(1024) k_budget(int ncell, const double* __restrict__ mJ,
+                                                 const int32_t* __restrict__ iters, int use_iters, double tol,
+                                                 double share, double mbar, double gamma,
+                                                 double* __restrict__ budget) {
+    __shared__ double sh[33];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const bool weigh = use_iters && gamma > 0.0;
+    double si = 0.0, sm = 0.0;
+    for (int J = tid; J < ncell; J += T) {
+        if (weigh) si += (double)max(1, iters[J]);
+        sm += mJ[J];
+    }
+    const double mean_it = weigh ? block_sum_fixed(si, sh) / max(1, ncell) : 1.0;
+    const double mtot = block_sum_fixed(sm, sh);
+    double sw = 0.0;
+    for (int J = tid; J < ncell; J += T) {
+        const double base = (1.0 - share) * mJ[J] + share * mbar;
+        sw += weigh ? base * pow((double)max(1, iters[J]) / mean_it, gamma) : base;
+    }
+    const double wsum = block_sum_fixed(sw, sh);
+    const double scale = wsum > 0.0 ? tol * mtot / wsum : 0.0;
+    for (int J = tid; J < ncell; J += T) {
+        const double base = (1.0 - share) * mJ[J] + share * mbar;
+        budget[J] = scale * (weigh ? base * pow((double)max(1, iters[J]) / mean_it, gamma) : base);
+    }
+}
+
 // a <- log2 mu + f (a - log2 mu) for the stored X duals of every cell (eps change)
 __global__ void k_rescale_alpha(int ncell, int amax, int N2, const int32_t* __restrict__ xblk,
                                 const float* __restrict__ lgmu, float* __restrict__ alpha, float f) {
@@ -1746,6 +1795,14 @@ __global__ void k_rescale_alpha(int ncell, int amax, int N2, const int32_t* __re
 }
 
 }  // namespace
+
+int launch_budget(dd_ctx* c, int part) {
+    const DevPart& P = c->part[part];
+    if (P.ncell <= 0) return DD_OK;
+    k_budget<<<1, 1024, 0, c->stream>>>(P.ncell, P.mJ, P.iters, P.warm_valid ? 1 : 0, c->opt.tol, c->opt.tol_share,
+                                        P.mbar, c->opt.tol_gamma, P.budget);
+    return launch_status(__func__);
+}
 
 int launch_rescale_alpha(dd_ctx* c, int part, double f) {
     const DevPart& P = c->part[part];
@@ -1798,6 +1855,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.lnmu = c->d_lnmu; A.lnnu = c->d_lnnu; A.lnnuf = c->d_lnnuf;
     A.tol = c->opt.tol; A.max_iter = c->opt.max_iter; A.fixed_iters = c->opt.fixed_iters;
     A.tol_share = c->opt.tol_share; A.mbar = P.mbar;
+    A.budget = P.budget;
     A.omega = (float)c->opt.omega;
     A.trunc = (float)c->opt.trunc;
     A.iters = P.iters; A.err = P.err; A.Ecell = P.Ecell; A.bmom = c->d_bmom;

@@ -48,6 +48,7 @@ struct DevPart {
     int32_t* xblk = nullptr;     // ncell x XB_N
     double* mJ = nullptr;        // ncell, mu(X_J)
     double mbar = 0.0;           // mean of mu(X_J) over the partition
+    double* budget = nullptr;    // ncell: stop budget of each cell's next solve (absolute L1 X error)
     int32_t* chdr = nullptr;     // ncell x CH_N (last solve)
     float* alpha = nullptr;      // ncell x amax, centred base-2 gauge
     float* gauge = nullptr;      // ncell x 2, displacement (cell centre - box centre) in pixels
@@ -231,6 +232,8 @@ inline bool mlp_keeps_old(const dd_ctx* c) {
 // unpack the current pool into c->d_plan64
 int launch_pack_plan(dd_ctx* c, int dst, bool validate);
 int launch_unpack_plan(dd_ctx* c);
+// per-cell stop budgets of the next solves of `part` into P.budget (dd_options tol_share, tol_gamma)
+int launch_budget(dd_ctx* c, int part);
 // stored X duals of a partition: a <- log2 mu + f (a - log2 mu) (eps change by 1 / f)
 int launch_rescale_alpha(dd_ctx* c, int part, double f);
 int half_occupancy(int threads, size_t smem);

@@ -180,18 +180,20 @@ def test_tolerance_mode_marginal_errors(dd, workload, N, init, levels):
     g.close()
 
 
-@pytest.mark.parametrize("share,omega", [(1.0, 1.0), (0.5, 1.4)])
-def test_tolerance_mode_batch_budget(dd, share, omega):
+@pytest.mark.parametrize("share,omega,gamma", [(1.0, 1.0, 0.0), (0.5, 1.4, 0.0), (1.0, 1.4, 1.0)])
+def test_tolerance_mode_batch_budget(dd, share, omega, gamma):
     """dd_options.tol_share = s: cell J stops at L1 X error <= tol ((1 - s) m_J +
     s mean(m)), budgets that sum to tol |mu| (the paper's batch criterion over
     all cells of the half-iteration). FP64 re-evaluation of the exported duals:
     each cell within its budget (+ the FP32 slack of the per-cell test), the
-    kernel's own total within tol; with over-relaxation (omega) the same holds."""
+    kernel's own total within tol; with over-relaxation (omega) the same holds.
+    tol_gamma > 0 reweights the budgets by the previous iteration counts (still
+    summing to tol |mu|): the per-cell bound is then the total one."""
     mu, nu, eps, p = synth.workload("dd256", 0, N=64)
     tol = 1e-5
     boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
     g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000, eps_levels=2, eps_factor=4.0,
-                  tol_share=share, omega=omega)
+                  tol_share=share, omega=omega, tol_gamma=gamma)
     geom = Geometry(64, 64, 4)
     m = geom.basic_masses(mu)
     for part in (0, 1, 0):
@@ -199,10 +201,13 @@ def test_tolerance_mode_batch_budget(dd, share, omega):
         assert st["n_maxiter"] == 0 and st["n_stalled"] == 0
         parts = geom.partition(part)
         mJ = np.array([m[c].sum() for c in parts])
-        budget = tol * ((1 - share) * mJ + share * mJ.mean())
+        budget = tol * ((1 - share) * mJ + share * mJ.mean()) if gamma == 0 else np.full(len(mJ), tol * mJ.sum())
+        total = 0.0
         for J, xe, ye in gpu_cell_errors(g, part, mu, nu, eps, geom):
             assert xe * mJ[J] <= budget[J] + 3e-5 * mJ[J], (J, xe * mJ[J], budget[J])
             assert ye <= 3e-5
+            total += xe * mJ[J]
+        assert total <= tol * mJ.sum() + 3e-5 * mJ.sum()
         assert st["l1_x"] <= tol * mJ.sum() + 1e-12
     g.close()
 
