@@ -47,8 +47,9 @@ def _flow_instance(N, s, seed):
     return nbr, cbar, m / m.sum()
 
 
-@pytest.mark.parametrize("N,s,seed", [(8, 2, 0), (16, 2, 1), (32, 2, 2), (64, 2, 3), (64, 4, 4)])
+@pytest.mark.parametrize("N,s,seed", [(8, 2, 0), (16, 2, 1), (32, 2, 2), (64, 2, 3), (64, 4, 4), (256, 2, 5)])
 def test_host_min_cost_flow_matches_oracle_lp(lib, N, s, seed):
+    # (256, 2): 16384 basic cells, 81920 arcs, a pricing list longer than the minimum
     nbr, cbar, m = _flow_instance(N, s, seed)
     w, val, piv = lib.dd_min_cost_flow(nbr, cbar, m)
     _, ref, _ = oracle_mcf(nbr, cbar, m)
