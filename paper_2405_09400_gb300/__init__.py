@@ -233,7 +233,11 @@ def dd_step(ctx, n=1, stats=True):
     else:
         rc = load().dd_step(ctx, int(n), None, None, None)
     _check(rc, "dd_step", ok=(DD_OK, DD_ERR_MAXITER, DD_ERR_FLOW))
-    return (sa.as_dict(), sb.as_dict(), sf.as_dict()) if stats else rc
+    if not stats:
+        return rc
+    fd = sf.as_dict()
+    fd["status"] = rc  # DD_ERR_MAXITER: some cell capped; DD_ERR_FLOW: stationary flow kept
+    return sa.as_dict(), sb.as_dict(), fd
 
 
 def _boxes_call(fn, ctx, nhdr, *lead, out=None):

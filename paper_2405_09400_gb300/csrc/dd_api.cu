@@ -1178,26 +1178,30 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     }
     c->part[0].warm_valid = c->part[0].solved = true;
     c->part[0].pred_old_valid = mlp_keeps_old(c);
-    {
-        int r = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
-        if (r != DD_OK && r != DD_ERR_MAXITER) return r;
-    }
+    // capped cells of the stages that ran in the graph stay in the returned status
+    auto merge = [](int r_graph, int r_eager) {
+        if (r_eager != DD_OK && r_eager != DD_ERR_MAXITER && r_eager != DD_ERR_FLOW) return r_eager;
+        return r_eager == DD_ERR_FLOW ? r_eager : (r_graph != DD_OK ? r_graph : r_eager);
+    };
+    int rg = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
+    if (rg != DD_OK && rg != DD_ERR_MAXITER) return rg;
     if (guard == 2) {
         c->cur = 1 - parity;
         c->last_part = 0;
         c->flow_ready = true;
-        return step_eager(c, sa, sb, sf, 1);
+        return merge(rg, step_eager(c, sa, sb, sf, 1));
     }
     c->part[1].warm_valid = c->part[1].solved = true;
     c->part[1].pred_old_valid = mlp_keeps_old(c);
     {
         int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);  // B ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
+        if (r != DD_OK) rg = r;
     }
     c->cur = parity;
     c->last_part = 1;
     c->flow_ready = true;
-    return step_eager(c, sa, sb, sf, 2);
+    return merge(rg, step_eager(c, sa, sb, sf, 2));
 }
 
 }  // namespace
@@ -1216,8 +1220,10 @@ int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
         if (r != DD_OK) rc = r;
         if (used_graph) {
             // statistics of the replayed iteration (objective / errors always, for
-            // dd_get_objective)
-            RET(fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]));
+            // dd_get_objective); capped cells (DD_ERR_MAXITER, already in r)
+            // neither end the statistics nor the remaining iterations
+            int r1 = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);
+            if (r1 != DD_OK && r1 != DD_ERR_MAXITER) return r1;
             int r2 = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);
             if (r2 != DD_OK && r2 != DD_ERR_MAXITER) return r2;
             flow_stats(c, c->g_value, c->g_piv, c->g_ms_solve, c->gev + 6, sf);

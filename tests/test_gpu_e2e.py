@@ -220,6 +220,37 @@ def test_graph_step_is_bit_identical_to_step_by_step(dd, margin):
     e.close()
 
 
+def test_graph_step_with_capped_cells(dd):
+    """Cells that stop at max_iter (DD_ERR_MAXITER) end neither a replayed
+    iteration's statistics nor dd_step(n > 1): B's and the flow's statistics
+    are those of the step-by-step path, and n iterations run."""
+    mu, nu, eps, p = synth.workload("dd256", 0, N=64)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    kw = dict(boxes=boxes, tol=1e-12, max_iter=15)  # every cell caps at 15 iterations
+    g = dd.DomDec(mu, nu, eps, 4, **kw)
+    e = dd.DomDec(mu, nu, eps, 4, flags=dd.DD_FLAG_NO_GRAPH, **kw)
+    g.step(1)
+    e.step(1)
+    for it in range(2):
+        sg, se = g.step(1), e.step(1)
+        assert sg[2]["status"] == se[2]["status"] == dd.DD_ERR_MAXITER
+        for k in (0, 1):
+            assert sg[k]["n_maxiter"] == se[k]["n_maxiter"] == g.ncell[k], (it, k)
+            assert sg[k]["iters_max"] == 15 and sg[k]["objective"] == se[k]["objective"], (it, k)
+        assert sg[2]["pivots"] == se[2]["pivots"] and sg[2]["value"] == se[2]["value"], it
+        assert sg[2]["ms_solve"] > 0.0 and sg[2]["nonzero"] == se[2]["nonzero"], it
+    r0 = g.graph_counters()["replays"]
+    assert r0 >= 1
+    assert dd.dd_step(g.ctx, 2, stats=False) == dd.DD_ERR_MAXITER
+    assert dd.dd_step(e.ctx, 2, stats=False) == dd.DD_ERR_MAXITER
+    assert g.graph_counters()["replays"] - r0 + g.graph_counters()["fallbacks"] >= 2
+    for (a1, a2, a), (b1, b2, b) in zip(_state(g), _state(e)):
+        assert (a1, a2) == (b1, b2) and np.array_equal(a, b)
+    assert g.objective()[:2] == e.objective()[:2]
+    g.close()
+    e.close()
+
+
 def test_autotune_restores_state_and_caches(dd, tmp_path):
     """The autotuner's trials leave the state and warm starts as they were: the
     next half-iterations equal those of a context given the chosen
