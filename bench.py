@@ -273,7 +273,7 @@ def run_ours(args):
         micro = {"iterations_per_cell": K, "half_iterations": len(rs), "ms_per_half_iteration": round(ms / len(rs), 4),
                  "us_per_sinkhorn_iteration_all_cells": round(1e3 * ms / len(rs) / K, 3),
                  "achieved_texp2_s": round(ach / 1e12, 4), "peak_texp2_s": round(ex2_peak / 1e12, 4),
-                 "frac": round(ach / ex2_peak, 5)}
+                 "frac": round(ach / ex2_peak, 5), "box_sweep": box_sweep(tune, ex2_peak)}
 
     # end to end through the C ABI with host buffers: H2D of the plan, one
     # hybrid iteration (graph replay), D2H of the plan, every step (pinned host memory)
@@ -441,6 +441,36 @@ def run_reference(args):
             "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(time.perf_counter() - t0, 2)}
     print(json.dumps(line), flush=True)
+
+
+def box_sweep(tune, ex2_peak, K=50):
+    """Cell-LSE throughput per box size: (2048/m)^2 independent cells with 8 x 8 X
+    blocks and m x m boxes (synth.cell_lse_sweep), K fixed iterations from a cold
+    start, A half-iterations only; two timed half-iterations per size, the plan
+    reset before each."""
+    import paper_2405_09400_gb300 as dd
+    import synth
+
+    rows = []
+    for m in synth.cellbench.SIDES:
+        mu, nu, eps, s, (hdr, data) = synth.cell_lse_sweep(m, 0)
+        g = dd.DomDec(mu, nu, eps, s, boxes=(hdr, data), fixed_iters=K, warm=dd.DD_WARM_COLD,
+                      flags=dd.DD_FLAG_NO_GRAPH)
+        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        g.iterate(0)  # sizes, allocation
+        terms = ms = 0.0
+        for _ in range(2):
+            g.set_plan((hdr, data))
+            st = g.iterate(0)
+            terms += st["lse_terms"]
+            ms += st["ms_cells"]
+        ncell = st["ncell"]
+        g.close()
+        ach = terms / (ms * 1e-3)
+        rows.append({"box": m, "cells": ncell, "ms_per_half_iteration": round(ms / 2, 4),
+                     "us_per_sinkhorn_iteration_all_cells": round(1e3 * ms / 2 / K, 3),
+                     "achieved_texp2_s": round(ach / 1e12, 4), "frac": round(ach / ex2_peak, 5)})
+    return rows
 
 
 def main():

@@ -23,3 +23,4 @@ from .couplings import (  # noqa: F401
     boxes_from_coupling,
     rotation_coupling,
 )
+from .cellbench import cell_lse_sweep  # noqa: F401
