@@ -294,7 +294,7 @@ int dd_get_counters(dd_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t*
  *            (shared memory, many CTAs per SM),
  *   class 0: other boxes that fit shared memory,
  *   class 2: boxes beyond shared memory (their arrays in global scratch).
- * threads[k] is the CTA size of class k (128, 256 or 512).
+ * threads[k] is the CTA size of class k (64, 128, 256 or 512).
  */
 typedef struct dd_tuning {
     int32_t threads[3];

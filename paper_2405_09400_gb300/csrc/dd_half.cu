@@ -1827,7 +1827,8 @@ bool g_attr_set = false;
 int set_attrs() {
     if (g_attr_set) return DD_OK;
     const int mx = half_kernel_max_smem();
-    if (cudaFuncSetAttribute(k_sink<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+    if (cudaFuncSetAttribute(k_sink<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sink<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_sink<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_sink<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_sink<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
@@ -1894,7 +1895,9 @@ int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* 
     return launch_status(__func__);
 }
 
-int half_threads(int requested) { return requested <= 128 ? 128 : (requested <= 256 ? 256 : 512); }
+int half_threads(int requested) {
+    return requested <= 64 ? 64 : (requested <= 128 ? 128 : (requested <= 256 ? 256 : 512));
+}
 
 int launch_classify(dd_ctx* c, int part, int stage) {
     const DevPart& P = c->part[part];
@@ -1921,6 +1924,7 @@ int launch_half(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue
     A.smaxH = (int)dims[1];
     A.smaxW = (int)dims[2];
     switch (half_threads(threads)) {
+        case 64: k_sink<64, 1><<<grid, 64, smem, stream>>>(A); break;
         case 128: k_sink<128, 1><<<grid, 128, smem, stream>>>(A); break;
         case 256: k_sink<256, 1><<<grid, 256, smem, stream>>>(A); break;
         default: k_sink<512, 1><<<grid, 512, smem, stream>>>(A); break;
@@ -1982,6 +1986,7 @@ int half_occupancy(int threads, size_t smem) {
     if (set_attrs() != DD_OK) return 0;
     int nb = 0;
     switch (half_threads(threads)) {
+        case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<64, 1>, 64, smem); break;
         case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<128, 1>, 128, smem); break;
         case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<256, 1>, 256, smem); break;
         default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sink<512, 1>, 512, smem); break;

@@ -129,7 +129,7 @@ void cache_store(const char* path, const std::string& key, const dd_tuning& t) {
     std::fclose(f);
 }
 
-bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
+bool valid_threads(int t) { return t == 64 || t == 128 || t == 256 || t == 512; }
 
 // cell-kernel time of one configuration: both partitions, best of two runs
 int trial(dd_ctx* c, const dd_tuning& t, Saved* saved, double* ms) {
@@ -207,7 +207,7 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
     const int sides[3][2] = {{768, 48}, {1536, 64}, {3072, 96}};
     std::vector<std::pair<double, dd_tuning>> one_cta;  // phase 1 results
     if (r == DD_OK) one_cta.push_back({def_ms, defaults});
-    for (int t1 : {128, 256}) {
+    for (int t1 : {64, 128, 256}) {
         for (int t0 : {256, 512}) {
             for (const auto& sd : sides) {
                 if (r != DD_OK) break;

@@ -240,11 +240,12 @@ def test_flow_update_matches_oracle_on_gpu_state(dd):
     g.close()
 
 
-@pytest.mark.parametrize("m", [8, 32, 128])
-def test_cell_lse_box_sweep_cells_match_oracle(dd, m):
+@pytest.mark.parametrize("m,small_threads", [(8, 64), (32, 64), (32, None), (128, None)])
+def test_cell_lse_box_sweep_cells_match_oracle(dd, m, small_threads):
     """The cell-LSE microbenchmark's inputs (synth.cell_lse_sweep: (2048/m)^2
     cells, 8 x 8 X blocks, m x m Gaussian boxes, cold start, 30 fixed iterations):
-    sampled cells' pre-balance basic marginals and D_i against the FP64 oracle.
+    sampled cells' pre-balance basic marginals and D_i against the FP64 oracle,
+    with the default launch configuration or the small-box class on 64-thread CTAs.
     Bound 1e-5 (L1 per unit basic mass, relative D_i), the fixed-iteration bound
     above; measured <= 7.8e-7 at every box size from 8 to 128."""
     from oracle.domdec import composite_to_basic, solve_cell
@@ -253,9 +254,13 @@ def test_cell_lse_box_sweep_cells_match_oracle(dd, m):
     mu, nu, eps, s, (hdr, data) = synth.cell_lse_sweep(m, 0)
     N = mu.shape[0]
     g = dd.DomDec(mu, nu, eps, s, boxes=(hdr, data), fixed_iters=K, warm=dd.DD_WARM_COLD,
-                  flags=dd.DD_FLAG_NO_GRAPH | dd.DD_FLAG_KEEP_PREBALANCE)
+                  flags=dd.DD_FLAG_NO_GRAPH | dd.DD_FLAG_KEEP_PREBALANCE | dd.DD_FLAG_TRACE)
+    if small_threads:
+        g.set_tuning([512, small_threads, 512], 3072, 96, cl_size=1, cl_cells=0)
     st = g.iterate(0)
     assert st["ncell"] == (2048 // m) ** 2 and st["iters_max"] == K
+    if small_threads:
+        assert (g.trace(0)[:, 3] == small_threads).all()  # every cell ran on the small class
     pre = g.prebalance()
     D = g.basic_moments()["D"]
     g.close()
