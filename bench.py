@@ -199,7 +199,9 @@ def run_ours(args):
     weights, _ = ws.load_params()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     arms = set(args.arms.split(","))
-    # autotune the cell-kernel launch configuration on this GPU and workload
+    # autotune the cell-kernel launch configuration on this GPU and workload, on
+    # the state in the middle of the timed trajectory (the composite boxes widen
+    # and the slowest cells grow along it)
     tune = None
     if args.tuning:
         t = [int(x) for x in args.tuning.split(",")]
@@ -209,7 +211,7 @@ def run_ours(args):
     elif not args.no_tune:
         tctx = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
                          weights=weights, **SOLVER)
-        tctx.step(2, stats=False)
+        tctx.step(args.warmup + args.steps // 2, stats=False)
         tune = tctx.autotune()
         tctx.close()
     if world > 1:

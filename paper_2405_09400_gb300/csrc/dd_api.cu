@@ -311,8 +311,10 @@ void dd_destroy(dd_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->side2) cudaStreamDestroy(c->side2);
+    if (c->side3) cudaStreamDestroy(c->side3);
     delete c;
 }
 
@@ -496,17 +498,21 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         for (auto& e : c->gev)
             if (cudaEventCreate(&e) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
-        // the large-box cells run on a high-priority stream: their CTAs are placed
-        // before the small-box kernel's persistent grid fills the SMs, so the
-        // longest solves start first (in graphs too: node priorities)
+        // the large-box and cluster cells run on high-priority streams: released
+        // together with the small-box class (all three wait on one fork event, or
+        // in graphs on one node), their CTAs are placed before the small-box
+        // kernel's persistent grid fills the SMs, so the longest solves start
+        // first (in graphs: node priorities)
         int prio_lo = 0, prio_hi = 0;
         cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side3, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
             rc = DD_ERR_CUDA;
             goto fail;
         }
@@ -766,10 +772,16 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     RET(launch_budget(c, part));
     c->n_launch += 1;
     CK(cudaEventRecord(c->ev[1], c->stream));
+    // with both size classes, each waits on the same fork event (the small class
+    // on its own stream): released together, the high-priority large class is
+    // placed first, as in a captured graph. Stream-ordered after the budget
+    // kernel, the small class would be released first and its persistent grid
+    // would take every SM before the large cells could start.
     const bool side_used = !cls_cells[1].empty() && (!cls_cells[0].empty() || !cls_cells[2].empty());
     if (side_used) {
         CK(cudaEventRecord(c->ev_fork, c->stream));
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        CK(cudaStreamWaitEvent(c->side3, c->ev_fork, 0));
     }
     if (!cls_cells[3].empty()) {  // clusters first, on their own high-priority stream
         CK(cudaEventRecord(c->ev_fork, c->stream));
@@ -786,7 +798,7 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         const int n = (int)cls_cells[k].size();
         int occ = std::max(1, half_occupancy(thr_c[k], smem_c[k]));
         int grid = std::max(1, std::min(n, c->nsm * occ));
-        cudaStream_t st = (k != 1 && side_used) ? c->side : c->stream;
+        cudaStream_t st = !side_used ? c->stream : (k != 1 ? c->side : c->side3);
         // the global-scratch class keeps no box array in shared memory: its carve
         // must see area 0, as its shared-memory size was computed with area 0
         const long long kd[3] = {k == 2 ? 0 : dims[k][0], dims[k][1], dims[k][2]};
@@ -797,6 +809,8 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     if (side_used) {
         CK(cudaEventRecord(c->ev_join, c->side));
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        CK(cudaEventRecord(c->ev_join3, c->side3));
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join3, 0));
     }
     if (!cls_cells[3].empty()) CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
     if (mlp_keeps_old(c) && with_c2b)

@@ -137,7 +137,8 @@ struct dd_ctx {
     cudaEvent_t ev[8] = {};
     cudaStream_t side = nullptr;  // second stream: the large-box class of cells
     cudaStream_t side2 = nullptr;  // third stream: the cells solved by clusters
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    cudaStream_t side3 = nullptr;  // step by step: the small-box class (normal priority)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
     long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
 
