@@ -264,7 +264,9 @@ def test_autotune_restores_state_and_caches(dd, tmp_path):
     a.step(1)
     b.step(1)
     t = a.autotune(cache)
-    assert t["trials"] >= 2 and 0 < t["ms_best"] <= t["ms_default"]
+    # ms_best is a fresh timing of the chosen configuration, ms_default the
+    # default's first one: both are noisy
+    assert t["trials"] >= 2 and 0 < t["ms_best"] <= 1.1 * t["ms_default"]
     b.set_tuning(t["threads"], t["small_area"], t["small_side"], t["cl_size"], t["cl_cells"])
     for part in (0, 1, 0):
         sa, sb = a.iterate(part), b.iterate(part)
