@@ -1766,17 +1766,23 @@ __global__ void __launch_bounds__(1024) k_budget(int ncell, const double* __rest
     }
     const double mean_it = weigh ? block_sum_fixed(si, sh) / max(1, ncell) : 1.0;
     const double mtot = block_sum_fixed(sm, sh);
+    // the weights are a heuristic: FP32 (an FP64 pow per cell on one SM took
+    // ~70 us at GB300's FP64 rate); their sum and the rescale stay FP64, so the
+    // budgets still add up to tol mu(X)
+    const float inv_mean = (float)(1.0 / mean_it), gf = (float)gamma;
     double sw = 0.0;
     for (int J = tid; J < ncell; J += T) {
-        const double base = (1.0 - share) * mJ[J] + share * mbar;
-        sw += weigh ? base * pow((double)max(1, iters[J]) / mean_it, gamma) : base;
+        double wj = (1.0 - share) * mJ[J] + share * mbar;
+        if (weigh) {
+            const float r = (float)max(1, iters[J]) * inv_mean;
+            wj *= (double)(gf == 1.f ? r : exp2f(gf * __log2f(r)));
+        }
+        budget[J] = wj;
+        sw += wj;
     }
     const double wsum = block_sum_fixed(sw, sh);
     const double scale = wsum > 0.0 ? tol * mtot / wsum : 0.0;
-    for (int J = tid; J < ncell; J += T) {
-        const double base = (1.0 - share) * mJ[J] + share * mbar;
-        budget[J] = scale * (weigh ? base * pow((double)max(1, iters[J]) / mean_it, gamma) : base);
-    }
+    for (int J = tid; J < ncell; J += T) budget[J] *= scale;
 }
 
 // a <- log2 mu + f (a - log2 mu) for the stored X duals of every cell (eps change)
