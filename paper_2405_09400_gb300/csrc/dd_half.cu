@@ -1525,7 +1525,7 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
         const int v1 = v / w, v2 = v - v1 * w;
         const float* tb = S.tab1 + v1;
         const float nuv = A.comp_nu[comp + (long long)v1 * stride + v2];
-        float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};
+        float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};  // ew: sum_u pi(u, v) E_i(v)
         if (nuv > 0.f) {
             float mx = DD_NEG;
             for (int cg = 0; cg < ncg; ++cg)
@@ -1546,19 +1546,22 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
                     ek += wt * (dd * dd + Mc[u1 * w]);
                 }
                 num[k] = nk;
-                ew[k] = nk > 0.f ? ek / nk : 0.f;
+                ew[k] = ek;
                 den += nk;
             }
             const float sc = den > 0.f ? nuv / den : 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) num[k] *= sc;
+            for (int k = 0; k < 4; ++k) {
+                num[k] *= sc;
+                ew[k] *= sc;  // nu_i(v) E_i(v), without dividing by the member's share
+            }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (k >= nmem) break;
             A.pool_out[slot0 + k * area + (long long)v1 * stride + v2] = num[k];
             accm[k] += num[k];
-            accd[k] += num[k] * ew[k];
+            accd[k] += ew[k];
         }
     }
     double red8[8];
