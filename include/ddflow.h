@@ -319,12 +319,15 @@ int dd_get_tuning(dd_ctx* ctx, dd_tuning* t);
 int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
 
 /*
- * Autotuner: times every candidate configuration (threads of the small and
- * large classes, the small-class limit) on the context's current state, both
- * partitions, every cell solved to the context's tolerance from the current
- * warm start (restored before each trial and after the last, so every
- * configuration does the same solves and the state and next solve are
- * unchanged), and keeps the fastest. With cache_path not NULL the
+ * Autotuner: times every candidate configuration (threads of the small class
+ * 64 / 128 / 256 and of the large class 256 / 512, the small-class limit, then
+ * clusters of 2 or 4 CTAs for 16, 32 or 48 cells on the two fastest) on the
+ * context's current state, both partitions, every cell solved to the
+ * context's tolerance from the current warm start (restored before each trial
+ * and after the last, so every configuration does the same solves and the
+ * state and next solve are unchanged), best of two runs each; the three
+ * fastest are timed again (best of four fresh runs) and the fastest of those is
+ * kept (ms_best is that fresh time). With cache_path not NULL the
  * result is looked up in / appended to that text file, keyed by GPU name, SM
  * count, grid, cell size, eps / h^2 and the median / largest box area of the
  * state. The chosen configuration is in *out (may be NULL).
