@@ -118,35 +118,35 @@ struct NetworkSimplex {
         }
         const int join = x;
         // cycle join -> u, a, v -> join: on the u path arcs pointing up are
-        // backward, on the v path arcs pointing down
+        // backward (blocking), on the v path arcs pointing down. theta is the
+        // least flow on a blocking arc, and the leaving arc the last blocking arc
+        // with that flow in cycle order from the join (keeps the basis strongly
+        // feasible, no cycling): one walk in reverse cycle order (the v path from
+        // the join down, then the u path from u up) keeping the first minimum
         int64_t theta = INT64_MAX;
-        for (int z : pu) {
-            int e = parc[z];
-            if (tail[e] == z) theta = std::min(theta, flow[e]);
+        int q = -1;
+        bool on_v = false;
+        for (int k = (int)pv.size() - 1; k >= 0; --k) {
+            const int z = pv[k], e = parc[z];
+            if (head[e] == z && flow[e] < theta) {
+                theta = flow[e];
+                q = z;
+                on_v = true;
+            }
         }
-        for (int z : pv) {
-            int e = parc[z];
-            if (head[e] == z) theta = std::min(theta, flow[e]);
+        for (int k = 0; k < (int)pu.size(); ++k) {
+            const int z = pu[k], e = parc[z];
+            if (tail[e] == z && flow[e] < theta) {
+                theta = flow[e];
+                q = z;
+                on_v = false;
+            }
         }
         if (theta == INT64_MAX) return false;  // unbounded (cannot happen here)
 #ifdef MCF_STATS
         st_path += pu.size() + pv.size();
         if (theta == 0) ++st_degenerate;
 #endif
-        // leaving arc: the last blocking arc of the cycle from the join (keeps the
-        // basis strongly feasible, no cycling)
-        int q = -1;
-        bool on_v = false;
-        for (int k = (int)pv.size() - 1; k >= 0; --k) {
-            int z = pv[k], e = parc[z];
-            if (head[e] == z && flow[e] == theta) { q = z; on_v = true; break; }
-        }
-        if (q < 0) {
-            for (int k = 0; k < (int)pu.size(); ++k) {
-                int z = pu[k], e = parc[z];
-                if (tail[e] == z && flow[e] == theta) { q = z; break; }
-            }
-        }
         if (q < 0) return false;
         if (theta > 0) {
             for (int z : pu) {
