@@ -255,15 +255,18 @@ struct NetworkSimplex {
         const int64_t* cst = cost.data();
         const int* tl = tail.data();
         const int* hd = head.data();
+        // the list lives in cl[0, nc); a block may overfill it by up to block - 1
+        if ((int)cand.size() < kCand + block) cand.resize(kCand + block);
+        int* cl = cand.data();
+        int nc = 0;
         while (true) {
             int best = -1;
             int64_t best_rc = 0;
-            for (size_t k = 0; k < cand.size();) {  // minor pass
-                const int e = cand[k];
+            for (int k = 0; k < nc;) {  // minor pass
+                const int e = cl[k];
                 const int64_t r = rc(e);
                 if (r >= 0) {
-                    cand[k] = cand.back();
-                    cand.pop_back();
+                    cl[k] = cl[--nc];
                     continue;
                 }
                 if (r < best_rc) {
@@ -273,23 +276,30 @@ struct NetworkSimplex {
                 ++k;
             }
             if (best < 0) {  // major pass
-                cand.clear();
+                nc = 0;
                 const int64_t* pt = pot.data();
                 int scanned = 0;
-                while (scanned < na && (int)cand.size() < kCand) {
+                while (scanned < na && nc < kCand) {
                     const int lim = std::min(block, na - scanned);
-                    for (int t = 0; t < lim; ++t) {
-                        const int e = next;
-                        next = (next + 1 == na) ? 0 : next + 1;
-                        const int64_t r = cst[e] + pt[tl[e]] - pt[hd[e]];
-                        if (r < 0) {
-                            cand.push_back(e);
-                            if (r < best_rc) {
-                                best_rc = r;
-                                best = e;
+                    // arcs next, next + 1, ... (lim of them, wrapping at na): at most
+                    // two contiguous ranges
+                    int e = next, left = lim;
+                    while (left > 0) {
+                        const int stop = std::min(na, e + left);
+                        left -= stop - e;
+                        for (; e < stop; ++e) {
+                            const int64_t r = cst[e] + pt[tl[e]] - pt[hd[e]];
+                            if (r < 0) {
+                                cl[nc++] = e;
+                                if (r < best_rc) {
+                                    best_rc = r;
+                                    best = e;
+                                }
                             }
                         }
+                        if (e == na) e = 0;
                     }
+                    next = e;
 #ifdef MCF_STATS
                     st_scan += lim;
 #endif
