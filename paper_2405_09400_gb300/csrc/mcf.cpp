@@ -44,7 +44,6 @@ struct NetworkSimplex {
     std::vector<int64_t> cost, flow;
     std::vector<int> parent, parc, thread, rev_thread, succ, last;
     std::vector<int64_t> pot;
-    std::vector<char> in_tree;
     std::vector<int> pu, pv, stem, seg;
     int64_t pivots = 0;
 #ifdef MCF_STATS
@@ -166,8 +165,6 @@ struct NetworkSimplex {
         const int64_t delta = on_v ? rc(a) : -rc(a);
         const int p_out = parent[q];
         const int nS = succ[q];
-        in_tree[parc[q]] = 0;
-        in_tree[a] = 1;
         // stem u_in = w0, w1, ..., wk = q (old ancestors of u_in inside S)
         stem.clear();
         for (int z = u_in; z != q; z = parent[z]) stem.push_back(z);
@@ -368,7 +365,6 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
     ns.parent.assign(nn, -1);
     ns.parc.assign(nn, -1);
     ns.pot.assign(nn, 0);
-    ns.in_tree.assign(ns.na, 0);
     // spanning tree of the cell grid by breadth-first search from cell 0, over
     // neighbour arcs; tree: s_root; t_i under s_p(i) (zero flow), s_i under t_i.
     std::vector<int> order;
@@ -401,9 +397,7 @@ int mcf_create(int32_t n, const int32_t* nbr, const double* m, McfSolver** out) 
             int p = par_cell[i];
             ns.parent[ti] = 2 * p;
             ns.parc[ti] = via[i];
-            ns.in_tree[via[i]] = 1;
         }
-        ns.in_tree[self] = 1;
         if (idx == 0) {  // root s_0; t_0 hangs below it
             ns.parent[ti] = si;
             ns.parc[ti] = self;
