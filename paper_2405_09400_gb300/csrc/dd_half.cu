@@ -488,7 +488,6 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
     const int ncell = A.count ? *A.count : A.ncell;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
-    const int s = A.s;
     int crank = 0;
     if constexpr (CL > 1) crank = (int)cg::this_cluster().block_rank();
     const bool lead = crank == 0;  // writes the per-cell results
