@@ -217,7 +217,10 @@ int dd_flow_update(dd_ctx* ctx, dd_flow_stats* st);
  * finished step by step (same results), after which the graph is captured
  * again. DD_FLAG_NO_GRAPH disables the graph. Any of the stats pointers may be
  * NULL; when given they receive the values of the LAST iteration (in graph
- * mode stored_entries is that of the state after the flow update).
+ * mode stored_entries is that of the state after the flow update). All n
+ * iterations run; the status is DD_ERR_FLOW if a flow solve failed (the
+ * stationary flow was kept), else DD_ERR_MAXITER if some cell reached max_iter
+ * (the state is still updated), else DD_OK; other errors stop at once.
  */
 int dd_step(dd_ctx* ctx, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf);
 

@@ -1231,7 +1231,7 @@ int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
         bool used_graph = false;
         int r = can_graph ? step_graph(c, sa, sb, sf, &used_graph) : step_eager(c, sa, sb, sf);
         if (r != DD_OK && r != DD_ERR_MAXITER && r != DD_ERR_FLOW) return r;
-        if (r != DD_OK) rc = r;
+        if (r == DD_ERR_FLOW || (r == DD_ERR_MAXITER && rc == DD_OK)) rc = r;  // a failed flow solve first
         if (used_graph) {
             // statistics of the replayed iteration (objective / errors always, for
             // dd_get_objective); capped cells (DD_ERR_MAXITER, already in r)
