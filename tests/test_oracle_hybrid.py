@@ -67,3 +67,31 @@ def test_golden_dd32_trajectory_regenerates():
     a = o.iterate(0)
     assert a["E"] == pytest.approx(gold["steps"][0]["E"], rel=1e-12)
     assert max(a["iters"]) == gold["steps"][0]["iters_max"]
+
+
+def test_flow_updates_unfreeze_the_rotation():
+    """Section 5.2: mu = nu with four symmetric bumps, initial plan rotated by a
+    quarter turn, eps = (h/2)^2, small cells (s = 2). Domain decomposition alone
+    removes the rotation only slowly; with a flow update after every B
+    half-iteration (Alg. 3) the objective falls markedly faster. The oracle,
+    measured after 12 iterations at 16 x 16: 7.1e-3 with flow updates, 1.39e-2
+    without; asserted ratio <= 0.6, and each run's objective never increases."""
+    N, s = 16, 2
+    mu = synth.four_bumps(N)
+    eps = (0.5 / N) ** 2
+    boxes = synth.boxes_from_coupling(mu.shape, s, *synth.rotation_coupling(mu))
+    last = {}
+    for flow in (False, True):
+        o = OracleDD(mu, mu, eps, s, boxes=boxes, tol=1e-8)
+        prev = np.inf
+        for _ in range(12):
+            if flow:
+                a, b, f = o.step()
+                assert f["value"] <= 1e-16
+            else:
+                a = o.iterate(0)
+                b = o.iterate(1)
+            assert a["E"] <= prev + 1e-13 and b["E"] <= a["E"] + 1e-13
+            prev = b["E"]
+        last[flow] = prev
+    assert last[True] <= 0.6 * last[False], last
