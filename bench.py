@@ -35,27 +35,31 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-5 L1 marginal err (plain vs warm-start), cell-LSE HBM GB/s"
 WORKLOAD = "dd256"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# GB300 unit counts and clock used for the exp-throughput peak of the cell kernel
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-EX2_PER_CLK_SM = 32  # MUFU ex2 issue rate per SM per clock (see the design notes)
+# exp-throughput peak of the cell kernel: #SM (read from the device) x ex2 per SM
+# per clock x the SM clock. GB300's SMs issue 32 MUFU ex2 per clock (twice the
+# 16 of earlier generations); the library's dd_probe_ex2_rate measures the rate
+# in the same run and the line reports both
+EX2_PER_CLK_SM = 32
+SM_MAX_MHZ_DEFAULT = 2070.0
 # cell solver of every arm: eps-scaling inside each solve (eps 16, 4, 1 x the
-# target; the stop and the solution are those of the target eps), a fixed
-# over-relaxation of the X-update (same fixed point, same stop) and the batch
-# error budget (cell budgets ~ 1e-5 mu(X) / #cells, weighted by the cell's previous
-# iteration count relative to the mean and rescaled to sum to 1e-5 mu(X), so the
-# half-iteration's total L1 X error stays <= 1e-5 mu(X), the paper's batch criterion);
-# the line reports how many cell solves ended stalled or at the iteration cap
-SOLVER = dict(eps_levels=2, eps_factor=4.0, eps_tol=1e-3, omega=1.4, tol_share=1.0, tol_gamma=1.0)
+# target; the stop and the solution are those of the target eps), Anderson
+# acceleration of the X-dual iteration (memory 4; same fixed point, same stop)
+# and the batch error budget (cell budgets ~ 1e-5 mu(X) / #cells, weighted by
+# the cell's previous iteration count relative to the mean and rescaled to sum
+# to 1e-5 mu(X), so the half-iteration's total L1 X error stays <= 1e-5 mu(X),
+# the paper's batch criterion); the line reports how many cell solves ended on a
+# plateau or at the iteration cap
+SOLVER = dict(eps_levels=2, eps_factor=4.0, eps_tol=1e-3, tol_share=1.0, tol_gamma=1.0, anderson=4)
 
 
 def peaks():
     try:
         with open(MEASURED) as fh:
             d = json.load(fh)
-        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured")
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", SM_MAX_MHZ_DEFAULT)),
+                    src="measured")
     except Exception:
-        return dict(hbm_gbs=6800.0, src="fallback")
+        return dict(hbm_gbs=6800.0, sm_max_mhz=SM_MAX_MHZ_DEFAULT, src="fallback")
 
 
 def dist_env():
@@ -244,7 +248,11 @@ def run_ours(args):
     k_ms = sum(warm["cell_ms"]) / len(warm["cell_ms"])
     k_terms = sum(warm["terms"]) / len(warm["terms"])
     pk = peaks()
-    ex2_peak = N_SM * EX2_PER_CLK_SM * SM_MAX_MHZ * 1e6  # terms (ex2) per second
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or pk.get("sm_max_mhz") or SM_MAX_MHZ_DEFAULT
+    ex2_peak = n_sm * EX2_PER_CLK_SM * sm_max * 1e6  # terms (ex2) per second
+    ex2_meas, ex2_ms = dd.dd_probe_ex2_rate()
     achieved = k_terms / (k_ms * 1e-3)
     hbm_gbs = (sum(warm["hbm_bytes"]) / len(warm["hbm_bytes"])) / (k_ms * 1e-3) / 1e9
 
@@ -316,7 +324,6 @@ def run_ours(args):
         cpu = cpu_baseline(args, mu, nu, eps, p, boxes)
     if rank != 0:
         return
-    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(ms_warm, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_warm, 4), "higher_is_better": False,
@@ -338,6 +345,9 @@ def run_ours(args):
         "sinkhorn_iters_mean": {k: round(float(np.mean(x["iters_mean"])), 2) for k, x in arm_map.items()},
         "sinkhorn_iters_max_mean": {k: round(float(np.mean(x["iters_max"])), 1) for k, x in arm_map.items()},
         "cell_solves_stalled_or_capped": {k: x["stalled"] + x["maxiter"] for k, x in arm_map.items()},
+        "cell_solves_on_plateau": {k: x["stalled"] for k, x in arm_map.items()},
+        "cell_solves_capped": {k: x["maxiter"] for k, x in arm_map.items()},
+        "cell_solves": {k: x["cells"] for k, x in arm_map.items()},
         "step_breakdown_ms": {"cell_kernels_A_plus_B": round(2 * k_ms, 3),
                               "min_cost_flow_host": round(float(np.mean(warm["mcf_ms"])), 3),
                               "rest": round(ms_warm - 2 * k_ms - float(np.mean(warm["mcf_ms"])), 3),
@@ -351,7 +361,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_sink (persistent cell Sinkhorn, + k_c2b)",
                      "achieved": round(achieved / 1e12, 4), "peak": round(ex2_peak / 1e12, 4), "unit": "Texp2/s",
                      "frac": round(achieved / ex2_peak, 5), "traffic": None, "kernel_ms_mean": round(k_ms, 4),
-                     "work_per_launch": k_terms},
+                     "work_per_launch": k_terms,
+                     "peak_src": f"{n_sm} SMs x {EX2_PER_CLK_SM} ex2/clk x {sm_max:.0f} MHz"},
+        "ex2_probe": {"measured_tex2_s": round(ex2_meas / 1e12, 4), "ms": round(ex2_ms, 4),
+                      "ex2_per_clk_sm_at_max_clock": round(ex2_meas / (n_sm * sm_max * 1e6), 2)},
         "cell_lse_fixed_iterations": micro,
         "clocks": clocks,
         "gpu_launches": int(warm["launches"]),

@@ -115,6 +115,13 @@ typedef struct dd_options {
                             are weighted by (it_J / mean it)^tol_gamma and rescaled to
                             sum to tol mu(X) (the same batch bound), so that slowly
                             converging cells stop earlier and fast ones later; 0 = off */
+    int32_t anderson;    /* 0 (default): plain Sinkhorn updates of the X dual. 1..4:
+                            Anderson acceleration of the X-dual fixed-point iteration
+                            (tolerance mode): the next X dual combines the last
+                            anderson + 1 iterates and their plain updates by
+                            mu-weighted least squares on the residuals, restarted
+                            when the L1 X error more than doubles; same fixed point,
+                            same stopping pair (alpha_old, beta); omega is ignored */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */
@@ -342,6 +349,18 @@ int dd_autotune(dd_ctx* ctx, const char* cache_path, dd_tuning* out);
  * timer), the SM it ran on, its CTA size. */
 int dd_get_trace(dd_ctx* ctx, int part, int64_t* trace);
 
+/*
+ * Measured throughput of the base-2 exponential (ex2.approx, the MUFU unit) on
+ * the current device, in ex2 per second (best of five timed launches of a
+ * persistent grid of independent ex2 chains, 4 CTAs of 512 threads per SM).
+ * Every log-sum-exp term of the cell Sinkhorn kernel is one ex2, so this rate
+ * calibrates the kernel's roofline (Section A.1 "Custom CUDA Sinkhorn" is the
+ * step it bounds). Allocates a small device buffer; synchronises `stream`.
+ * *ms (may be NULL) receives the best launch time. Errors: DD_ERR_ARG,
+ * DD_ERR_OOM, DD_ERR_CUDA.
+ */
+int dd_probe_ex2_rate(void* stream, double* ex2_per_s, double* ms);
+
 /* dd_step graph counters since dd_init: graphs captured, iterations replayed
  * from a graph, replays finished step by step after a capacity overflow. */
 int dd_get_graph_counters(dd_ctx* ctx, int64_t* captures, int64_t* replays, int64_t* fallbacks);
@@ -349,22 +368,23 @@ int dd_get_graph_counters(dd_ctx* ctx, int64_t* captures, int64_t* replays, int6
 /*
  * Allocation-free variant of the L1 Y-marginal error of dd_get_objective (the
  * paper has no counterpart; this is a library facility). For callers that
- * cannot allocate device memory: code running inside CUDA stream capture
- * (cudaMalloc cannot be captured), real-time pipelines that reserve all device
- * memory up front, hosts whose own allocator owns the GPU. It computes
+ * cannot allocate device memory: real-time pipelines that reserve all device
+ * memory up front and forbid allocation afterwards, and host frameworks whose
+ * own caching allocator owns the GPU's memory. It computes
  *     *l1_out = sum_y | sum_i nu_i(y) - nu(y) |
  * with scratch memory taken from a fixed __device__ array inside the library,
  * never from cudaMalloc.
  *  - All pointers are DEVICE pointers on the current device: hdr (nbasic x 4
  *    int32 box headers o1, o2, h, w), data (float32 box contents packed in cell
  *    order, each h x w row-major, no padding), nu (N1 * N2 float64), l1_out (one
- *    float64, overwritten). Entries of a box outside the grid are ignored.
+ *    float64, overwritten). Entries of a box outside the grid are ignored; a
+ *    box with h <= 0 or w <= 0 is empty. data must hold sum_i h_i w_i entries.
  *  - Limits: N1 * N2 <= DD_STATIC_MAX_PIXELS and nbasic <= DD_STATIC_MAX_CELLS;
  *    larger problems return DD_ERR_ARG without touching the GPU. The array
  *    (about 8.5 MB) is held by every GPU that loads the library until exit.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture. Host threads may make it concurrently.
  *  - Every call shares the array: calls that overlap on the GPU (other streams,
  *    other host threads on the same device) race. Calls ordered on one stream are
  *    safe; each call clears the accumulator it uses.

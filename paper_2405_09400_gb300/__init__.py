@@ -28,6 +28,7 @@ DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
 DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
 DD_FLAG_MLP_EVERY_SOLVE = 16
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
+DD_STATIC_MAX_PIXELS, DD_STATIC_MAX_CELLS = 1024 * 1024, 65536
 
 EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_set_eps", "dd_iterate", "dd_flow_update", "dd_step",
@@ -36,7 +37,7 @@ EXPORTS = [
     "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
     "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
-    "dd_get_tuning", "dd_set_tuning", "dd_autotune", "dd_get_trace",
+    "dd_get_tuning", "dd_set_tuning", "dd_autotune", "dd_get_trace", "dd_probe_ex2_rate",
 ]
 
 
@@ -49,7 +50,7 @@ class dd_options(C.Structure):
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
                 ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double),
                 ("eps_levels", C.c_int32), ("eps_factor", C.c_double), ("eps_tol", C.c_double),
-                ("tol_share", C.c_double), ("tol_gamma", C.c_double)]
+                ("tol_share", C.c_double), ("tol_gamma", C.c_double), ("anderson", C.c_int32)]
 
 
 class dd_stats(C.Structure):
@@ -131,6 +132,7 @@ def load():
         "dd_set_tuning": (C.c_int, [vp, P(dd_tuning)]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, P(dd_tuning)]),
         "dd_get_trace": (C.c_int, [vp, C.c_int, P(C.c_int64)]),
+        "dd_probe_ex2_rate": (C.c_int, [vp, _f64p, _f64p]),
         "dd_debug_cell": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), _i32p]),
         "dd_l1_y_error_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp]),
         "dd_destroy": (None, [vp]),
@@ -399,6 +401,14 @@ def dd_l1_y_error_static(N1, N2, nbasic, hdr_ptr, data_ptr, nu_ptr, out_ptr, str
     return load().dd_l1_y_error_static(int(N1), int(N2), int(nbasic), C.c_void_p(hdr_ptr), C.c_void_p(data_ptr),
                                        C.c_void_p(nu_ptr), C.c_void_p(out_ptr),
                                        stream if stream is not None else current_stream())
+
+
+def dd_probe_ex2_rate(stream=None):
+    """Measured ex2.approx throughput of the current device: (ex2 per second, ms)."""
+    r, ms = C.c_double(), C.c_double()
+    _check(load().dd_probe_ex2_rate(stream if stream is not None else current_stream(), C.byref(r), C.byref(ms)),
+           "dd_probe_ex2_rate")
+    return r.value, ms.value
 
 
 def dd_destroy(ctx):

@@ -255,6 +255,7 @@ void dd_default_options(dd_options* o) {
     o->eps_tol = 1e-3;
     o->tol_share = 0.0;
     o->tol_gamma = 0.0;
+    o->anderson = 0;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -350,7 +351,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
         c->opt.eps_levels < 0 || c->opt.eps_levels > 8 ||
         (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4) ||
-        !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0) || !(c->opt.tol_gamma >= 0.0 && c->opt.tol_gamma <= 4.0)) {
+        !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0) || !(c->opt.tol_gamma >= 0.0 && c->opt.tol_gamma <= 4.0) ||
+        c->opt.anderson < 0 || c->opt.anderson > 4) {
         delete c;
         return DD_ERR_ARG;
     }

@@ -236,6 +236,8 @@ struct HalfArgs {
     const float* pred;  // ncell x DD_MLP_NOUT network outputs (first 64: predicted r), or null
     const float* pred_old;  // the outputs of the previous solve of this partition, or null
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
+    // Anderson acceleration of the X-dual iteration (tolerance mode): memory, 0 = off
+    int aa_m;
     // eps-scaling inside each solve (tolerance mode only): levels eps f^L .. eps
     int eps_levels;
     float eps_factor;
@@ -267,10 +269,19 @@ struct Smem {
     double* clx;  // 16: per-CTA sums exchanged within a cluster
     float* pm;    // 8 * amax: partial X-update log-sums of every rank of a cluster
                   // ([buffer][rank][u], two buffers, up to 4 ranks), written by the ranks
+    float* aa;    // Anderson history (aa_m > 0): residual differences dG[aa_m][amax],
+                  // iterate differences dX[aa_m][amax], last residual g[amax], last
+                  // iterate x[amax], Gram matrix of dG (kAAMax x kAAMax)
     float* coef;  // 16
     int* ctl;     // 32
     long long end;  // bytes used
 };
+
+constexpr int kAAMax = 4;  // largest Anderson memory
+// floats of the Anderson history for memory m and X blocks of amax pixels
+__host__ __device__ __forceinline__ int aa_floats(int m, int amax) {
+    return m > 0 ? (2 * m + 2) * amax + kAAMax * kAAMax : 0;
+}
 
 __device__ Smem carve(char* base, const HalfArgs& A) {
     Smem S;
@@ -300,6 +311,7 @@ __device__ Smem carve(char* base, const HalfArgs& A) {
     S.lgm = f; f += A.amax;
     S.muxf = f; f += A.amax;
     S.pm = f; f += 8 * A.amax;
+    S.aa = f; f += aa_floats(A.aa_m, A.amax);
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     S.end = reinterpret_cast<char*>(f + 32) - base;
@@ -463,6 +475,163 @@ __device__ void cluster_sum_d(double (&v)[N], double* clx, int slot) {
         double x = 0.0;
         for (unsigned r = 0; r < nr; ++r) x += cl.map_shared_rank(clx, r)[slot + k];
         v[k] = x;
+    }
+}
+
+// One Anderson step on the X dual (type II, memory m <= kAAMax), run by one warp
+// (every lane computes the same coefficients). x = aC is the current iterate and
+// aN holds its plain Sinkhorn update F(x); g = F(x) - x. With the columns
+// dG_j = g_j - g_(j-1) and dX_j = x_j - x_(j-1) of the last q <= m iterations,
+//   gamma = argmin sum_u w(u) (g(u) - sum_j gamma_j dG_j(u))^2   (w = mu / mu(X_J)),
+// solved from the normal equations with a Tikhonov term (1e-4 trace / q, at
+// least the squared FP32 resolution of the duals) by a Cholesky factorisation,
+// and the next iterate
+//   x' = x + g - sum_j gamma_j (dX_j + dG_j)
+// overwrites aN. q = 0 (first iteration, after a restart) leaves the plain update.
+// The history ring holds the columns in slots [0, q); `head` is the slot the new
+// column goes to. Coefficients that are not finite or very large keep the plain
+// update and restart the history, as does an error more than twice the last one.
+__device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err, float err_last,
+                              const float* __restrict__ aC, float* __restrict__ aN) {
+    const int lane = threadIdx.x & 31;
+    // history state in shared memory: ctl[8] = count | head << 4 | prev << 8, ctl[9] = 1 / mu(X_J)
+    const int st = S.ctl[8];
+    const float wnorm = __int_as_float(S.ctl[9]);
+    int cnt = st & 15, head = (st >> 4) & 15;
+    bool prev = (st >> 8) & 1;
+    if (prev && err > 2.f * err_last) {  // restart when the error more than doubled
+        cnt = head = 0;
+        prev = false;
+    }
+    __syncwarp();
+    auto store_state = [&](int c, int hd, bool pv) {
+        if (lane == 0) S.ctl[8] = c | (hd << 4) | ((pv ? 1 : 0) << 8);
+    };
+    float* const dG = S.aa;
+    float* const dX = dG + m * amax;
+    float* const gp = dX + m * amax;
+    float* const xp = gp + amax;
+    float* const Mg = xp + amax;  // kAAMax x kAAMax
+    for (int u = lane; u < nx; u += 32) {
+        const bool live = S.lgm[u] > 0.5f * DD_NEG;
+        const float g = live ? aN[u] - aC[u] : 0.f;
+        const float x = live ? aC[u] : 0.f;
+        if (prev) {
+            dG[head * amax + u] = g - gp[u];
+            dX[head * amax + u] = x - xp[u];
+        }
+        gp[u] = g;
+        xp[u] = x;
+    }
+    __syncwarp();
+    const int q = prev ? min(cnt + 1, m) : cnt;
+    const int head_next = prev ? (head + 1 == m ? 0 : head + 1) : head;
+    if (q == 0) {  // the plain update stays in aN
+        store_state(0, 0, true);
+        return;
+    }
+    float pm[kAAMax], pr[kAAMax];
+#pragma unroll
+    for (int j = 0; j < kAAMax; ++j) pm[j] = pr[j] = 0.f;
+    for (int u = lane; u < nx; u += 32) {
+        const float w = S.muxf[u] * wnorm;
+        const float g = gp[u];
+        const float gn = prev ? dG[head * amax + u] : 0.f;
+#pragma unroll
+        for (int j = 0; j < kAAMax; ++j) {
+            if (j < q) {
+                const float dj = w * dG[j * amax + u];
+                pm[j] += dj * gn;
+                pr[j] += dj * g;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kAAMax; ++j) {
+        for (int o = 16; o > 0; o >>= 1) {
+            pm[j] += __shfl_xor_sync(0xffffffffu, pm[j], o);
+            pr[j] += __shfl_xor_sync(0xffffffffu, pr[j], o);
+        }
+    }
+    if (prev && lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kAAMax; ++j)
+            if (j < q) {
+                Mg[head * kAAMax + j] = pm[j];
+                Mg[j * kAAMax + head] = pm[j];
+            }
+    }
+    __syncwarp();
+    // Cholesky of M + lam I (q x q, lower factor L in registers), every lane alike
+    float L[kAAMax][kAAMax];
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < kAAMax; ++i) {
+#pragma unroll
+        for (int j = 0; j < kAAMax; ++j) L[i][j] = (i < q && j < q) ? Mg[i * kAAMax + j] : 0.f;
+        if (i < q) tr += L[i][i];
+    }
+    // Tikhonov term: relative to the Gram trace, and at least the squared FP32
+    // resolution of the dual differences (8e-6 in base-2 units), so that
+    // columns made of rounding noise get no weight
+    const float lam = fmaxf(1e-4f * tr / (float)q, 6.4e-11f);
+    bool ok = tr > 0.f && isfinite(tr);
+#pragma unroll
+    for (int j = 0; j < kAAMax; ++j) {
+        if (j < q) {
+            float d = L[j][j] + lam;
+#pragma unroll
+            for (int k = 0; k < kAAMax; ++k)
+                if (k < j) d -= L[j][k] * L[j][k];
+            ok = ok && d > 0.f;
+            const float dj = sqrtf(fmaxf(d, 1e-30f));
+            L[j][j] = dj;
+#pragma unroll
+            for (int i = 0; i < kAAMax; ++i) {
+                if (i > j && i < q) {
+                    float v = L[i][j];
+#pragma unroll
+                    for (int k = 0; k < kAAMax; ++k)
+                        if (k < j) v -= L[i][k] * L[j][k];
+                    L[i][j] = v / dj;
+                }
+            }
+        }
+    }
+    float gam[kAAMax];
+#pragma unroll
+    for (int i = 0; i < kAAMax; ++i) {  // L y = r
+        float v = pr[i];
+#pragma unroll
+        for (int k = 0; k < kAAMax; ++k)
+            if (k < i) v -= L[i][k] * gam[k];
+        gam[i] = i < q ? v / L[i][i] : 0.f;
+    }
+#pragma unroll
+    for (int i = kAAMax - 1; i >= 0; --i) {  // L^T gamma = y
+        if (i < q) {
+            float v = gam[i];
+#pragma unroll
+            for (int k = 0; k < kAAMax; ++k)
+                if (k > i && k < q) v -= L[k][i] * gam[k];
+            gam[i] = v / L[i][i];
+        }
+    }
+    float gs = 0.f;
+#pragma unroll
+    for (int j = 0; j < kAAMax; ++j) gs += fabsf(gam[j]);
+    if (!ok || !(gs <= 1e3f)) {  // keep the plain update; restart the history
+        store_state(0, 0, false);
+        return;
+    }
+    store_state(q, head_next, true);
+    for (int u = lane; u < nx; u += 32) {
+        if (!(S.lgm[u] > 0.5f * DD_NEG)) continue;
+        float xn = xp[u] + gp[u];
+#pragma unroll
+        for (int j = 0; j < kAAMax; ++j)
+            if (j < q) xn -= gam[j] * (dX[j * amax + u] + dG[j * amax + u]);
+        aN[u] = xn;
     }
 }
 
@@ -664,6 +833,10 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             const float shift = (float)(cm[0] / gm[5]);
             for (int u = tid; u < nx; u += NT)
                 if (aC[u] > 0.5f * DD_NEG) aC[u] -= shift;
+            if (tid == 0) {  // empty Anderson history; its weights mu / mu(X_J)
+                S.ctl[8] = 0;
+                S.ctl[9] = __float_as_int((float)(1.0 / gm[5]));
+            }
         }
         __syncthreads();
 
@@ -684,9 +857,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // over-relaxation of the X-update (same fixed point): a <- a + w (X(b) - a).
         // Adaptive: plain for the first iterations, then w from the observed
         // contraction r of the error, w = 2 / (1 + sqrt(1 - r)) (Young's rule).
-        float om = A.omega > 1.f ? A.omega : 1.f;
+        // Anderson acceleration replaces the over-relaxation when it is on
+        const bool aa_on = A.aa_m > 0 && A.fixed_iters <= 0;
+        float om = (A.omega > 1.f && !aa_on) ? A.omega : 1.f;
         float err_prev = 0.f, err_mark = 0.f;
         int om_start = 5;
+
         // threads per line of the X-update stage 2 (a power of two, lanes adjacent)
         int P2 = 1;
         while (P2 * 2 * nx <= NT && P2 < 16) P2 *= 2;
@@ -1057,7 +1233,14 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             // 50 tol (the FP32 rounding floor of this cell has been reached)
             if (err < 0.99f * best) { best = err; since = 0; } else ++since;
             stalled = A.fixed_iters <= 0 && since >= 64 && err <= 50.f * tolm;
-            if (A.omega < 0.f) {
+            // the next iterate from the Anderson history (warp 0; every thread passes the barrier)
+            const float err_last = err_prev;
+            auto aa_update = [&]() {
+                if (!aa_on) return;
+                if (wid == 0) anderson_step(S, nx, A.amax, A.aa_m, err, err_last, aC, aN);
+                __syncthreads();
+            };
+            if (A.omega < 0.f && !aa_on) {
                 if (om > 1.f && err > 1.5f * err_prev) {  // diverging: back to plain steps
                     om = 1.f;
                     om_start = it + 5;
@@ -1092,9 +1275,11 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     best = 3.0e38f;
                     since = 0;
                     stalled = false;
+                    if (tid == 0) S.ctl[8] = 0;  // Anderson history restarts at the new level
                     __syncthreads();
                     continue;
                 }
+                aa_update();
                 float* tmp = aC;
                 aC = aN;
                 aN = tmp;
@@ -1103,6 +1288,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             const bool done = (A.fixed_iters > 0) ? (it >= A.fixed_iters)
                                                   : (err <= tolm || it >= A.max_iter || stalled);
             if (done) break;
+            aa_update();
             float* tmp = aC;
             aC = aN;
             aN = tmp;
@@ -1723,7 +1909,8 @@ size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long m
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
     maxarea = (maxarea + 3) & ~3LL;  // as in carve()
     size_t bytes = sizeof(double) * ((size_t)c->amax + 32 * 16 + 16 + (size_t)maxh + BS + 16) + 16;
-    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 12 * (size_t)c->amax + 16 + 32;
+    size_t fl = 2 * (size_t)maxarea + s2 * BS + 2 * (size_t)maxh * s2 + BS * s2 + 12 * (size_t)c->amax + 16 + 32 +
+                (size_t)aa_floats(c->opt.fixed_iters > 0 ? 0 : c->opt.anderson, c->amax);
     return bytes + sizeof(float) * fl;
 }
 
@@ -1873,6 +2060,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.guard = c->capturing ? c->d_guard : nullptr;
     A.count = nullptr;
     A.trace = (c->opt.flags & DD_FLAG_TRACE) ? c->d_trace[part] : nullptr;
+    A.aa_m = c->opt.fixed_iters > 0 ? 0 : c->opt.anderson;
     A.eps_levels = c->opt.eps_levels;
     A.eps_factor = (float)c->opt.eps_factor;
     A.eps_tol = c->opt.eps_tol;

@@ -1,10 +1,10 @@
 // dd_l1_y_error_static: the L1 Y-marginal error of a basic-cell box state,
 // computed without allocating any device memory.
 //
-// Some callers cannot allocate: code that runs while a CUDA stream is being
-// captured into a graph (cudaMalloc is not capturable), real-time or embedded
-// pipelines that reserve all device memory up front and forbid allocation
-// afterwards, and host frameworks whose own allocator owns the device. For them
+// Some callers cannot allocate: real-time or embedded pipelines that reserve all
+// device memory up front and forbid allocation afterwards, and host frameworks
+// whose own caching allocator owns the device memory (a cudaMalloc behind its
+// back can fail or fragment its pool). For them
 // this entry point uses a fixed scratch area that lives in a file-scope
 // __device__ array instead of memory from cudaMalloc. The caller passes inputs
 // and the output in device memory, as for dd_get_objective's Y error.
@@ -16,6 +16,7 @@
 // device) race; calls ordered on one stream are safe.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/ddflow.h"
@@ -33,8 +34,16 @@ struct StaticScratch {
 };
 static __device__ __align__(256) StaticScratch g_scratch;
 
-// host-side device address of g_scratch, looked up once per device
-StaticScratch* g_addr[kMaxDevices] = {};
+// host-side device address of g_scratch, looked up once per device; host threads
+// making their first call on one device at the same time may both look it up and
+// store the same value
+std::atomic<StaticScratch*> g_addr[kMaxDevices] = {};
+
+// entries of a box: h * w, or 0 for a box with a non-positive extent
+__device__ __forceinline__ long long box_size(const int32_t* __restrict__ hdr, int i) {
+    const int h = hdr[4 * i + 2], w = hdr[4 * i + 3];
+    return (h > 0 && w > 0) ? (long long)h * w : 0LL;
+}
 
 __global__ void k_offsets(int nb, const int32_t* __restrict__ hdr, StaticScratch* __restrict__ S) {
     // one CTA: exclusive prefix sum of the box sizes h * w (packed, unpadded boxes)
@@ -42,7 +51,7 @@ __global__ void k_offsets(int nb, const int32_t* __restrict__ hdr, StaticScratch
     const int T = blockDim.x, per = (nb + T - 1) / T;
     const int c0 = min(nb, (int)threadIdx.x * per), c1 = min(nb, c0 + per);
     long long s = 0;
-    for (int i = c0; i < c1; ++i) s += (long long)hdr[4 * i + 2] * hdr[4 * i + 3];
+    for (int i = c0; i < c1; ++i) s += box_size(hdr, i);
     part[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -58,7 +67,7 @@ __global__ void k_offsets(int nb, const int32_t* __restrict__ hdr, StaticScratch
     long long run = part[threadIdx.x];
     for (int i = c0; i < c1; ++i) {
         S->offset[i] = run;
-        run += (long long)hdr[4 * i + 2] * hdr[4 * i + 3];
+        run += box_size(hdr, i);
     }
 }
 
@@ -73,10 +82,10 @@ __global__ void k_scatter(int N1, int N2, const int32_t* __restrict__ hdr, const
     const int i = blockIdx.x;
     const int o1 = hdr[4 * i], o2 = hdr[4 * i + 1], h = hdr[4 * i + 2], w = hdr[4 * i + 3];
     if (h <= 0 || w <= 0) return;
-    const long long base = S->offset[i];
-    for (int v = threadIdx.x; v < h * w; v += blockDim.x) {
-        const int v1 = v / w, v2 = v - v1 * w;
-        const int y1 = o1 + v1, y2 = o2 + v2;
+    const long long base = S->offset[i], n = (long long)h * w;
+    for (long long v = threadIdx.x; v < n; v += blockDim.x) {
+        const long long v1 = v / w, v2 = v - v1 * w;
+        const long long y1 = o1 + v1, y2 = o2 + v2;
         if (y1 < 0 || y1 >= N1 || y2 < 0 || y2 >= N2) continue;  // outside the grid: ignored
         const float val = data[base + v];
         if (val != 0.f) atomicAdd(&S->acc[(long long)y1 * N2 + y2], (double)val);
@@ -108,14 +117,15 @@ extern "C" int dd_l1_y_error_static(int32_t N1, int32_t N2, int32_t nbasic, cons
     if (np > kMaxPixels || nbasic > kMaxCells) return DD_ERR_ARG;  // beyond the static scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DD_ERR_CUDA;
-    if (!g_addr[dev]) {
+    StaticScratch* S = g_addr[dev].load(std::memory_order_acquire);
+    if (!S) {
         // first call on this device: the host-side name g_scratch is not a device
         // address; ask the runtime for it (with this device current)
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return DD_ERR_CUDA;
-        g_addr[dev] = static_cast<StaticScratch*>(p);
+        S = static_cast<StaticScratch*>(p);
+        g_addr[dev].store(S, std::memory_order_release);
     }
-    StaticScratch* S = g_addr[dev];
     cudaStream_t st = (cudaStream_t)stream;
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DD_ERR_CUDA;

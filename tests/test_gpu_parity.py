@@ -1,6 +1,6 @@
 """GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
 
-Tolerances (derived from the arithmetic; see the design notes):
+Tolerances (each derived below from the FP32 and FP64 arithmetic of the two sides):
 * indexing (partitions, neighbours, box headers given identical values): bit-exact;
 * fixed Sinkhorn iteration counts, same start: both sides run the same
   iteration; the GPU's FP32 log-sum-exp carries relative errors of a few 1e-7 per
@@ -158,15 +158,20 @@ def test_composite_to_basic_D_and_balancing_from_gpu_duals(dd):
     g.close()
 
 
-@pytest.mark.parametrize("workload,N,init,levels", [("dd32", 32, "product", 0), ("dd256", 64, "kr", 0),
-                                                     ("dd32", 32, "product", 2), ("dd256", 64, "kr", 2)])
-def test_tolerance_mode_marginal_errors(dd, workload, N, init, levels):
-    """levels > 0: eps-scaling inside each solve (coarser eps first); the stop
-    and the solution are those of the target eps, so the same bounds hold."""
+@pytest.mark.parametrize("workload,N,init,levels,aa", [("dd32", 32, "product", 0, 0), ("dd256", 64, "kr", 0, 0),
+                                                        ("dd32", 32, "product", 2, 0), ("dd256", 64, "kr", 2, 0),
+                                                        ("dd32", 32, "product", 0, 4), ("dd256", 64, "kr", 2, 4),
+                                                        ("dd256", 64, "kr", 2, 1)])
+def test_tolerance_mode_marginal_errors(dd, workload, N, init, levels, aa):
+    """levels > 0: eps-scaling inside each solve (coarser eps first); aa > 0:
+    Anderson acceleration of the X-dual iteration. The stop and the solution are
+    those of the target eps and of plain Sinkhorn (same fixed point, same
+    stopping pair), so the same bounds hold."""
     mu, nu, eps, p = synth.workload(workload, 0, N=N)
     tol = 1e-5
     boxes = None if init == "product" else synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
-    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000, eps_levels=levels, eps_factor=4.0)
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000, eps_levels=levels, eps_factor=4.0,
+                  anderson=aa)
     geom = Geometry(N, N, 4)
     for part in (0, 1, 0):
         st = g.iterate(part)
@@ -180,20 +185,22 @@ def test_tolerance_mode_marginal_errors(dd, workload, N, init, levels):
     g.close()
 
 
-@pytest.mark.parametrize("share,omega,gamma", [(1.0, 1.0, 0.0), (0.5, 1.4, 0.0), (1.0, 1.4, 1.0)])
-def test_tolerance_mode_batch_budget(dd, share, omega, gamma):
+@pytest.mark.parametrize("share,omega,gamma,aa", [(1.0, 1.0, 0.0, 0), (0.5, 1.4, 0.0, 0), (1.0, 1.4, 1.0, 0),
+                                                   (1.0, 1.0, 1.0, 4)])
+def test_tolerance_mode_batch_budget(dd, share, omega, gamma, aa):
     """dd_options.tol_share = s: cell J stops at L1 X error <= tol ((1 - s) m_J +
     s mean(m)), budgets that sum to tol |mu| (the paper's batch criterion over
     all cells of the half-iteration). FP64 re-evaluation of the exported duals:
     each cell within its budget (+ the FP32 slack of the per-cell test), the
-    kernel's own total within tol; with over-relaxation (omega) the same holds.
+    kernel's own total within tol; with over-relaxation (omega) or Anderson
+    acceleration (aa) the same holds.
     tol_gamma > 0 reweights the budgets by the previous iteration counts (still
     summing to tol |mu|): the per-cell bound is then the total one."""
     mu, nu, eps, p = synth.workload("dd256", 0, N=64)
     tol = 1e-5
     boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
     g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=tol, max_iter=20000, eps_levels=2, eps_factor=4.0,
-                  tol_share=share, omega=omega, tol_gamma=gamma)
+                  tol_share=share, omega=omega, tol_gamma=gamma, anderson=aa)
     geom = Geometry(64, 64, 4)
     m = geom.basic_masses(mu)
     for part in (0, 1, 0):
