@@ -38,6 +38,16 @@ class OracleDD:
         self.k = 0
         self.history = []
 
+    def set_eps(self, eps):
+        """Change eps between hybrid iterations: the eps schedule of the paper's
+        solvers (Section 5, "Multi-scale and eps-scaling"; here without the
+        multiscale layers). The plan is kept, and so are the dual potentials
+        alpha of both partitions in cost units: they only warm-start the next
+        cell solves, which then solve the cell problems at the new eps."""
+        if not (eps > 0.0 and np.isfinite(eps)):
+            raise ValueError("eps must be positive and finite")
+        self.eps = float(eps)
+
     def iterate(self, part: int, keep_plans=False):
         self.boxes, info = half_iteration(
             self.geom, self.mu, self.nu, self.eps, self.hgrid, self.boxes, part,

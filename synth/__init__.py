@@ -22,5 +22,6 @@ from .couplings import (  # noqa: F401
     product_coupling,
     boxes_from_coupling,
     rotation_coupling,
+    rotation_contraction_coupling,
 )
 from .cellbench import cell_lse_sweep  # noqa: F401

@@ -72,6 +72,45 @@ def rotation_coupling(mu: np.ndarray):
     return (p * N + q).reshape(-1), y.reshape(-1), mu.reshape(-1).copy()
 
 
+def rotation_contraction_coupling(mu: np.ndarray, theta_deg: float):
+    """(id, T)_# mu for T(x) = c R_theta x on [-1, 1]^2, with the contraction
+    c = 1 / (cos theta + sin theta) that makes the rotated square fit into
+    [-1, 1]^2 (the initial plan and target of Section 5.3). On the pixel grid
+    each pixel's mass goes to the four pixels around T(its centre) with bilinear
+    weights (indices clipped to the grid), so nu is by construction the exact
+    second marginal of the returned coupling.
+
+    Returns (x index, y index, mass, nu) with nu an (N, N) array summing to 1.
+    """
+    N = mu.shape[0]
+    th = np.deg2rad(theta_deg)
+    c = 1.0 / (abs(np.cos(th)) + abs(np.sin(th)))
+    t = 2.0 * (np.arange(N) + 0.5) / N - 1.0
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    Y1 = c * (np.cos(th) * X1 - np.sin(th) * X2)
+    Y2 = c * (np.sin(th) * X1 + np.cos(th) * X2)
+    # continuous pixel coordinates of the image points
+    q1 = (Y1 + 1.0) * N / 2.0 - 0.5
+    q2 = (Y2 + 1.0) * N / 2.0 - 0.5
+    f1, f2 = np.floor(q1), np.floor(q2)
+    w1, w2 = q1 - f1, q2 - f2
+    xs, ys, ms = [], [], []
+    xi = (np.arange(N)[:, None] * N + np.arange(N)[None, :]).reshape(-1)
+    m = mu.reshape(-1)
+    for d1, a1 in ((0, 1.0 - w1), (1, w1)):
+        for d2, a2 in ((0, 1.0 - w2), (1, w2)):
+            r = np.clip(f1 + d1, 0, N - 1).astype(np.int64).reshape(-1)
+            k = np.clip(f2 + d2, 0, N - 1).astype(np.int64).reshape(-1)
+            wt = (a1 * a2).reshape(-1) * m
+            ok = wt > 0
+            xs.append(xi[ok])
+            ys.append((r * N + k)[ok])
+            ms.append(wt[ok])
+    x, y, mass = np.concatenate(xs), np.concatenate(ys), np.concatenate(ms)
+    nu = np.bincount(y, weights=mass, minlength=N * N).reshape(N, N)
+    return x, y, mass, nu
+
+
 def boxes_from_coupling(shape, s: int, x, y, mass):
     """Basic-cell Y-marginals of a sparse coupling, on their bounding boxes."""
     N1, N2 = shape

@@ -29,6 +29,7 @@ import pytest
 import synth
 from oracle.domdec import Box, basic_to_composite, composite_to_basic, solve_cell
 from oracle.geometry import Geometry
+from oracle.hybrid import OracleDD
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "dd32_k0.json")
@@ -398,6 +399,38 @@ def test_four_bumps_hybrid_matches_oracle(dd):
     g.close()
 
 
+@pytest.mark.parametrize("theta", [5.0, 20.0])
+def test_rotated_contracted_target_hybrid_matches_oracle(dd, theta):
+    """Section 5.3's workload (nu = (c R_theta)_# mu for the four-bumps mu, initial
+    plan (id, c R_theta)_# mu) at 16 x 16, s = 2, eps = (h/2)^2: three hybrid
+    iterations against the FP64 oracle, objectives within 1e-6 relative and flow
+    values within the bound of the trajectory test."""
+    N, s = 16, 2
+    mu = synth.four_bumps(N)
+    eps = (0.5 / N) ** 2
+    x, y, mass, nu = synth.rotation_contraction_coupling(mu, theta)
+    boxes = synth.boxes_from_coupling(mu.shape, s, x, y, mass)
+    g = dd.DomDec(mu, nu, eps, s, boxes=boxes, tol=1e-6, max_iter=50000)
+    o = OracleDD(mu, nu, eps, s, boxes=[Box(o1, o2, np.asarray(a)) for o1, o2, a in boxes], tol=1e-8)
+    m = Geometry(N, N, s).basic_masses(mu)
+    for it in range(3):
+        for part in (0, 1):
+            st = g.iterate(part)
+            ref = o.iterate(part)
+            assert abs(st["objective"] - ref["E"]) <= 1e-6 * abs(ref["E"]), (it, part)
+            assert st["n_maxiter"] == 0
+        t = np.max(np.abs(g.basic_moments()["D"]) / m)
+        f = g.flow_update()
+        fo = o.flow_update()
+        bound = 2 * (1e-6 + 1e-8) * t * max(f["moved"], 1e-300) + 1e-15
+        assert abs(f["value"] - fo["value"]) <= bound, (it, f["value"], fo["value"], bound)
+        if theta == 20.0 and it == 0:
+            assert f["value"] < 0
+    _, l1x, l1y = g.objective()
+    assert l1y <= 1e-6
+    g.close()
+
+
 def test_set_eps_keeps_dual_potentials(dd):
     """dd_set_eps rescales the stored X duals so that the dual potentials alpha
     (cost units) are unchanged: in a cell's gauge a - log2 mu scales as 1/eps
@@ -445,6 +478,34 @@ def test_eps_schedule_across_hybrid_iterations(dd):
     Es, its = run([(4 * eps, 4), (2 * eps, 4), (eps, 12)])
     assert abs(Ed - Eref) <= 2e-4 * Eref and abs(Es - Eref) <= 2e-4 * Eref, (Ed, Es, Eref)
     assert its <= 0.8 * itd, (its, itd)
+
+
+def test_eps_schedule_matches_oracle(dd):
+    """The eps schedule 4 eps, 2 eps, eps across hybrid iterations on the 32 x 32
+    workload, GPU (dd_set_eps: stored X duals rescaled so that the potentials
+    in cost units stay) against the oracle (OracleDD.set_eps: potentials kept),
+    per half-iteration: objectives within 1e-6 relative, flow values within the
+    bound of the stored-trajectory test (GPU tol 1e-6 in FP32, oracle 1e-7 in
+    FP64)."""
+    mu, nu, eps, p = synth.workload("dd32", 0)
+    g = dd.DomDec(mu, nu, 4 * eps, p["s"], tol=1e-6, max_iter=50000)
+    o = OracleDD(mu, nu, 4 * eps, p["s"], tol=1e-7)
+    m = Geometry(32, 32, p["s"]).basic_masses(mu)
+    for e, k in ((4 * eps, 2), (2 * eps, 2), (eps, 4)):
+        g.set_eps(e)
+        o.set_eps(e)
+        for it in range(k):
+            for part in (0, 1):
+                st = g.iterate(part)
+                ref = o.iterate(part)
+                assert abs(st["objective"] - ref["E"]) <= 1e-6 * abs(ref["E"]), (e, it, part, st["objective"], ref["E"])
+                assert st["n_maxiter"] == 0
+            f = g.flow_update()
+            fo = o.flow_update()
+            t = np.max(np.abs(g.basic_moments()["D"]) / m)
+            bound = 2 * (1e-6 + 1e-7) * t * max(f["moved"], 1e-300) + 1e-15
+            assert abs(f["value"] - fo["value"]) <= bound, (e, it, f["value"], fo["value"], bound)
+    g.close()
 
 
 def test_set_plan_roundtrip_and_rejection(dd):
@@ -523,3 +584,51 @@ def test_clusters_on_boxes_beyond_shared_memory(dd, cl):
     got = np.array([bb[2].sum() for bb in g.plan()])
     assert np.allclose(got, m, rtol=1e-5)
     g.close()
+
+
+@pytest.mark.parametrize("cl", [1, 2])
+def test_global_scratch_cells_match_oracle(dd, cl):
+    """Cells whose boxes exceed shared memory keep log2 nu_J and the Y dual in the
+    global scratch pool (the third size class). First A half-iteration of the
+    512 x 512 uneven workload from the KR plan, 30 fixed iterations, cold start:
+    the three largest such boxes (each > 3e4 pixels, beyond the ~2.5e4-float
+    shared-memory capacity next to the tables) are compared with the FP64 oracle
+    (dense log-sum-exp, Alg. 1 cell problem, then CompositeToBasic) element by
+    element, solved by one CTA (cl = 1) or by a cluster of two (cl = 2, each CTA
+    its own rows of the scratch arrays); the trace shows which. Bound as for the
+    sampled 256 x 256 cells: L1 <= 1e-4 m_i per member, D_i within 1e-4."""
+    mu, nu, eps, p = synth.workload("uneven512", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    K = 30
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, fixed_iters=K,
+                  flags=dd.DD_FLAG_KEEP_PREBALANCE | dd.DD_FLAG_TRACE | dd.DD_FLAG_NO_GRAPH)
+    g.set_tuning([512, 256, 512], 1536, 64, cl_size=cl, cl_cells=16 if cl > 1 else 0)
+    g.iterate(0)
+    pre = g.prebalance()
+    D = g.basic_moments()["D"].copy()
+    thr = g.trace(0)[:, 3].copy()
+    comp = g.composite(0)
+    g.close()
+    area = np.array([a.shape[0] * a.shape[1] for _, _, a in comp])
+    big = np.flatnonzero(area > 30000)
+    if cl > 1:
+        big = big[thr[big] == 512 * cl]
+    else:
+        big = big[thr[big] == 512]
+    assert big.size >= 3, (area.max(), thr[np.argsort(-area)[:8]])
+    big = big[np.argsort(-area[big])][:3]
+    geom = Geometry(512, 512, 4)
+    m = geom.basic_masses(mu)
+    bx = [Box(o1, o2, np.asarray(a)) for o1, o2, a in boxes]
+    cells = geom.partition(0)
+    for J in big:
+        members = cells[J]
+        nuJ = basic_to_composite(bx, members)
+        assert nuJ.h * nuJ.w == area[J]
+        res = solve_cell(geom, mu, eps, 1.0 / 512, members, nuJ, None, 1e-5, 100000, fixed_iters=K)
+        arrs, Dref = composite_to_basic(geom, members, nuJ, res)
+        for k, i in enumerate(members):
+            o1, o2, got = pre[i]
+            assert (o1, o2, got.shape) == (nuJ.o1, nuJ.o2, nuJ.a.shape)
+            assert np.abs(got - arrs[k]).sum() <= 1e-4 * m[i], (J, i, np.abs(got - arrs[k]).sum() / m[i])
+            assert D[i] == pytest.approx(Dref[k], rel=1e-4), (J, i)
