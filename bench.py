@@ -41,15 +41,15 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # in the same run and the line reports both
 EX2_PER_CLK_SM = 32
 SM_MAX_MHZ_DEFAULT = 2070.0
-# cell solver of every arm: eps-scaling inside each solve (eps 16, 4, 1 x the
-# target; the stop and the solution are those of the target eps), Anderson
-# acceleration of the X-dual iteration (memory 4; same fixed point, same stop)
+# cell solver of every arm: Anderson acceleration of the X-dual iteration
+# (memory 4; same fixed point, same stop; with it, eps-scaling inside each solve
+# no longer pays and is off)
 # and the batch error budget (cell budgets ~ 1e-5 mu(X) / #cells, weighted by
 # the cell's previous iteration count relative to the mean and rescaled to sum
 # to 1e-5 mu(X), so the half-iteration's total L1 X error stays <= 1e-5 mu(X),
 # the paper's batch criterion); the line reports how many cell solves ended on a
 # plateau or at the iteration cap
-SOLVER = dict(eps_levels=2, eps_factor=4.0, eps_tol=1e-3, tol_share=1.0, tol_gamma=1.0, anderson=4)
+SOLVER = dict(eps_levels=0, tol_share=1.0, tol_gamma=1.0, anderson=4)
 
 
 def peaks():
@@ -152,7 +152,8 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
     torch.cuda.synchronize()
     n0 = g.counters()["launches"]
     out = dict(step_ms=[], cell_ms=[], terms=[], cells=0, hbm_bytes=[], iters_mean=[], iters_max=[], first_ms=first_ms,
-               stalled=0, maxiter=0, l1x_max=0.0, mcf_ms=[], pivots=[])
+               stalled=0, maxiter=0, l1x_max=0.0, mcf_ms=[], pivots=[], c2b_ms=[], c2b_bytes=[], xch_ms=[],
+               xch_bytes=[])
     for _ in range(args.steps):
         flush.zero_()  # evict the state from L2 between steps (outside the timed events)
         a0 = torch.cuda.Event(enable_timing=True)
@@ -161,6 +162,8 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
         sa, sb, sf = g.step(1, stats=True)
         out["mcf_ms"].append(sf["ms_solve"])
         out["pivots"].append(sf["pivots"])
+        out["xch_ms"].append(sf["ms_exchange"])
+        out["xch_bytes"].append(sf["bytes_exchange"])
         a1.record(stream)
         a1.synchronize()
         out["step_ms"].append(a0.elapsed_time(a1))
@@ -173,6 +176,8 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
             out["stalled"] += s_["n_stalled"]
             out["l1x_max"] = max(out["l1x_max"], s_["l1_x"])
             out["maxiter"] += s_["n_maxiter"]
+            out["c2b_ms"].append(s_["ms_c2b"])
+            out["c2b_bytes"].append(s_["bytes_c2b"])
             # algorithmic bytes of the cell kernels: read the member boxes, write
             # nu_J, b and the member outputs (4 B each)
             out["hbm_bytes"].append(4.0 * (4 * s_["stored_entries"]))
@@ -318,6 +323,20 @@ def run_ours(args):
                "d2h_bytes_per_step": int(bo)}
         ge2.close()
 
+    # HBM-bound streams of the step: CompositeToBasic + balancing + truncation
+    # (k_c2b) and the flow exchange (k_plan_exchange + k_exchange), algorithmic
+    # bytes / event time, against the measured copy bandwidth
+    def stream_gbs(ms, by):
+        ms, by = float(np.mean(ms)), float(np.mean(by))
+        gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        return {"ms": round(ms, 4), "bytes": int(by), "achieved_gbs": round(gbs, 1),
+                "frac": round(gbs / pk["hbm_gbs"], 4)}
+
+    streams = {"k_c2b": stream_gbs(warm["c2b_ms"], warm["c2b_bytes"]),
+               "k_exchange": stream_gbs(warm["xch_ms"], warm["xch_bytes"]), "peak_gbs": pk["hbm_gbs"]}
+    ttt = None if args.no_ttt else time_to_tolerance(dd, mu, nu, eps, p, boxes, weights, tune, stream)
+    cfgs = None if args.no_configs else large_configs(dd, weights, args)
+
     arm_map = {k: x for k, x in (("plain", plain), ("warm", warm), ("affine", affine)) if x is not None}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -366,6 +385,9 @@ def run_ours(args):
         "ex2_probe": {"measured_tex2_s": round(ex2_meas / 1e12, 4), "ms": round(ex2_ms, 4),
                       "ex2_per_clk_sm_at_max_clock": round(ex2_meas / (n_sm * sm_max * 1e6), 2)},
         "cell_lse_fixed_iterations": micro,
+        "hbm_streams": streams,
+        "time_to_tolerance": ttt,
+        "configs": cfgs,
         "clocks": clocks,
         "gpu_launches": int(warm["launches"]),
         "e2e": e2e,
@@ -502,6 +524,121 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_to_tolerance(dd, mu, nu, eps, p, boxes, weights, tune, stream, n_ref=1200, gaps=(1e-3, 1e-4)):
+    """End-to-end time to tolerance on the bench workload, plain vs learned warm
+    start: device time of the hybrid run from the KR plan (first iteration step
+    by step, then graph replays) until the objective E_k is within `gap` of E*
+    (relative), every half-iteration at total L1 X error <= 1e-5. E* is the
+    smallest objective of a reference run of n_ref iterations with the same
+    solver. Iteration counts come from a run with per-step statistics; the time
+    from a second run of exactly that many steps without them."""
+    import numpy as np
+    import torch
+
+    def make(warm):
+        g = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=warm,
+                      weights=weights if warm == dd.DD_WARM_MLP else None, **SOLVER)
+        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        return g
+
+    ref = make(dd.DD_WARM_PREV)
+    Es = []
+    for _ in range(n_ref):
+        sa, sb, sf = ref.step(1, stats=True)
+        Es.append(sb["objective"])
+    ref.close()
+    Estar = float(min(Es))
+    out = {"E_star": Estar, "E_star_from": f"min objective of {n_ref} hybrid iterations (plain start, same solver)",
+           "l1x_per_half_iteration": "<= 1e-5 (batch budget)", "runs": {}}
+    for name, warm in (("plain", dd.DD_WARM_PREV), ("warm", dd.DD_WARM_MLP)):
+        g = make(warm)
+        need = {}
+        l1x = 0.0
+        for k in range(1, n_ref + 1):
+            sa, sb, sf = g.step(1, stats=True)
+            l1x = max(l1x, sa["l1_x"], sb["l1_x"])
+            for gap in gaps:
+                if gap not in need and (sb["objective"] - Estar) <= gap * abs(Estar):
+                    need[gap] = k
+            if len(need) == len(gaps):
+                break
+        g.close()
+        res = {}
+        for gap in gaps:
+            if gap not in need:
+                res[str(gap)] = None
+                continue
+            g = make(warm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(need[gap], stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            res[str(gap)] = {"iterations": need[gap], "ms": round(e0.elapsed_time(e1), 2)}
+            g.close()
+        out["runs"][name] = dict(res, l1x_max=l1x)
+    return out
+
+
+def large_configs(dd, weights, args):
+    """Per-iteration figures of the larger configurations, same cell solver:
+    uneven512 (512 x 512, uniform mu, 8 narrow Gaussians, eps = h^2, KR plan) and
+    dd1024 (1024 x 1024, 6-component mixtures, eps = 2 h^2) from its configured
+    initial plan: a 512 x 512 plan of the 2 x 2-coarsened measures after 100
+    hybrid iterations from KR, prolongated with 1 % seeded noise projected onto
+    exact marginals (synth.prolongate), learned warm start. Each: 3 warm-up
+    iterations, then 3 timed (CUDA events, graph replay)."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    res = {}
+
+    def timed(g, n_warm=3, n=3):
+        g.step(n_warm, stats=False)
+        ms, l1x, stalls, capped, mcf, cells, itmax = [], 0.0, 0, 0, [], [], []
+        for _ in range(n):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sa, sb, sf = g.step(1, stats=True)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            l1x = max(l1x, sa["l1_x"], sb["l1_x"])
+            stalls += sa["n_stalled"] + sb["n_stalled"]
+            capped += sa["n_maxiter"] + sb["n_maxiter"]
+            mcf.append(sf["ms_solve"])
+            cells.append(sa["ms_cells"] + sb["ms_cells"])
+            itmax.append(max(sa["iters_max"], sb["iters_max"]))
+        return {"ms_per_step": round(float(np.mean(ms)), 3), "cell_kernels_ms": round(float(np.mean(cells)), 3),
+                "min_cost_flow_host_ms": round(float(np.mean(mcf)), 3), "half_iteration_l1x_max": l1x,
+                "plateau_stops": stalls, "capped": capped, "sinkhorn_iters_max": int(max(itmax)),
+                "cells_per_half_iteration": [g.ncell[0], g.ncell[1]]}
+
+    mu, nu, eps, p = synth.workload("uneven512", 0)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    g = dd.DomDec(mu, nu, eps, 4, boxes=boxes, tol=1e-5, max_iter=20000, warm=dd.DD_WARM_PREV, **SOLVER)
+    res["uneven512"] = timed(g)
+    g.close()
+
+    mu, nu, eps, p = synth.workload("dd1024", 0)
+    muc, nuc = synth.coarsen(mu), synth.coarsen(nu)
+    bc = synth.boxes_from_coupling(muc.shape, 4, *synth.knothe_rosenblatt(muc, nuc))
+    gc = dd.DomDec(muc, nuc, 4 * eps, 4, boxes=bc, tol=1e-5, max_iter=20000, warm=dd.DD_WARM_PREV, **SOLVER)
+    gc.step(100, stats=False)
+    coarse = [(o1, o2, a) for o1, o2, a in gc.plan()]
+    gc.close()
+    fine = synth.prolongate(coarse, mu, nu, 4, noise=0.01, seed=0)
+    g = dd.DomDec(mu, nu, eps, 4, boxes=fine, tol=1e-5, max_iter=20000, plan_tol=1e-6, warm=dd.DD_WARM_MLP,
+                  weights=weights, **SOLVER)
+    res["dd1024_prolongated"] = timed(g)
+    g.close()
+    return res
+
+
 def box_sweep(tune, ex2_peak, K=50):
     """Cell-LSE throughput per box size: (2048/m)^2 independent cells with 8 x 8 X
     blocks and m x m boxes (synth.cell_lse_sweep), K fixed iterations from a cold
@@ -552,6 +689,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration (no autotuning)")
     ap.add_argument("--no-micro", action="store_true", help="skip the fixed-iteration cell-LSE microbenchmark")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the end-to-end time-to-tolerance runs")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 512 x 512 and 1024 x 1024 configurations")
     ap.add_argument("--tuning", default="", help="fixed launch configuration t0,t1,t2,small_area,small_side"
                                                "[,cl_size,cl_cells] instead of autotuning (profiling runs)")
     ap.add_argument("--arms", default="plain,warm,affine,eager",

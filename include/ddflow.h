@@ -139,6 +139,11 @@ typedef struct dd_stats {
     double ms_total;       /* device time of the half-iteration (ms)              */
     double ms_cells;       /* device time of the fused cell kernel (ms)           */
     int64_t stored_entries;/* entries of the output basic boxes                   */
+    double ms_c2b;         /* device time of CompositeToBasic + balancing +
+                              truncation (part of ms_cells, ms)                   */
+    double bytes_c2b;      /* its algorithmic bytes: read nu_J (4 B per composite
+                              box entry), write the output basic boxes (4 B per
+                              stored entry)                                       */
 } dd_stats;
 
 /* Statistics of one flow update (Section 3.2, steps of Section 5.1). */
@@ -150,6 +155,8 @@ typedef struct dd_flow_stats {
     double ms_costs;     /* device time, edge costs (ms)                          */
     double ms_solve;     /* host time, min-cost flow (ms)                         */
     double ms_exchange;  /* device time, exchange + re-box (ms)                   */
+    double bytes_exchange; /* algorithmic bytes of the exchange: read every source
+                              box with w_ij > 0, write the new boxes (4 B each)  */
 } dd_flow_stats;
 
 typedef struct dd_ctx dd_ctx;

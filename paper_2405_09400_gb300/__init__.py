@@ -57,7 +57,7 @@ class dd_stats(C.Structure):
     _fields_ = [("part", C.c_int32), ("ncell", C.c_int32), ("iters_max", C.c_int32), ("n_maxiter", C.c_int32),
                 ("n_stalled", C.c_int32), ("iters_mean", C.c_double), ("objective", C.c_double), ("l1_x", C.c_double),
                 ("lse_terms", C.c_double), ("ms_total", C.c_double), ("ms_cells", C.c_double),
-                ("stored_entries", C.c_int64)]
+                ("stored_entries", C.c_int64), ("ms_c2b", C.c_double), ("bytes_c2b", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,7 +65,8 @@ class dd_stats(C.Structure):
 
 class dd_flow_stats(C.Structure):
     _fields_ = [("value", C.c_double), ("nonzero", C.c_int32), ("pivots", C.c_int32), ("moved", C.c_double),
-                ("ms_costs", C.c_double), ("ms_solve", C.c_double), ("ms_exchange", C.c_double)]
+                ("ms_costs", C.c_double), ("ms_solve", C.c_double), ("ms_exchange", C.c_double),
+                ("bytes_exchange", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

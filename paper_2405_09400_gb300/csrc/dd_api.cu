@@ -568,8 +568,8 @@ static float event_ms(cudaEvent_t a, cudaEvent_t b) {
 }
 
 static int fill_stats(dd_ctx* c, int part, dd_stats* st, int slot = 0, cudaEvent_t e0 = nullptr,
-                      cudaEvent_t e1 = nullptr, cudaEvent_t e2 = nullptr) {
-    if (!e0) { e0 = c->ev[0]; e1 = c->ev[1]; e2 = c->ev[2]; }
+                      cudaEvent_t e1 = nullptr, cudaEvent_t e2 = nullptr, cudaEvent_t ec = nullptr) {
+    if (!e0) { e0 = c->ev[0]; e1 = c->ev[1]; e2 = c->ev[2]; ec = c->ev[7]; }
     DevPart& P = c->part[part];
     std::vector<int32_t> it(P.ncell), ch((size_t)CH_N * P.ncell), xb;
     std::vector<double> er(P.ncell), E(P.ncell);
@@ -612,6 +612,11 @@ static int fill_stats(dd_ctx* c, int part, dd_stats* st, int slot = 0, cudaEvent
         int64_t ent = 0;
         for (int i = 0; i < c->nb; ++i) ent += (int64_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
         st->stored_entries = ent;
+        // CompositeToBasic, balancing, truncation: reads nu_J, writes the basic boxes
+        double comp_entries = 0.0;
+        for (int J = 0; J < P.ncell; ++J) comp_entries += (double)ch[CH_N * J + CH_H] * ch[CH_N * J + CH_W];
+        st->ms_c2b = ec ? event_ms(ec, e2) : 0.0;
+        st->bytes_c2b = 4.0 * (comp_entries + (double)ent);
     }
     // a kernel found its shared memory too small, or a pool slot beyond its buffer, and skipped
     if (status[2] > 0 || status[4] > 0) return DD_ERR_POOL;
@@ -824,6 +829,7 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
                                    std::max({dims[0][2], dims[1][2], dims[2][2], dims[3][2]})};
         const size_t sm = c2b_smem_bytes(c, dall[1], dall[2]);
         if (sm > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
+        CK(cudaEventRecord(c->ev[7], c->stream));
         RET(launch_c2b(c, part, dall, sm));
         c->n_launch += 1;
     }
@@ -871,6 +877,13 @@ int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
 // exchange: ev[2..3])
 static void flow_stats(dd_ctx* c, double value, int32_t piv, double ms_solve, cudaEvent_t* ev, dd_flow_stats* st) {
     dd_flow_stats fs{};
+    // entries read (source boxes with w_ij > 0) and written by the exchange,
+    // totalled by its planning kernel
+    long long xt[2] = {0, 0};
+    if (d2h(xt, c->d_tot + PT_PAD0, 2, c->stream) == DD_OK && cudaStreamSynchronize(c->stream) == cudaSuccess)
+        fs.bytes_exchange = 4.0 * (double)(xt[0] + xt[1]);
+    else
+        cudaGetLastError();
     fs.value = value;
     fs.pivots = piv;
     int nz = 0;
@@ -1060,6 +1073,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
         CK(cudaMemcpyAsync(c->d_pred_old[part], c->d_pred, sizeof(float) * DD_MLP_NOUT * P.ncell,
                            cudaMemcpyDeviceToDevice, c->stream));
     const long long dc[3] = {0, g.h2, g.w2};
+    CK(cudaEventRecordWithFlags(c->gev[10 + (stage - 1)], c->stream, cudaEventRecordExternal));
     RET(launch_c2b(c, part, dc, g.smem_c2b));
     c->n_launch += 1;
     CK(cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal));
@@ -1199,7 +1213,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
         if (r_eager != DD_OK && r_eager != DD_ERR_MAXITER && r_eager != DD_ERR_FLOW) return r_eager;
         return r_eager == DD_ERR_FLOW ? r_eager : (r_graph != DD_OK ? r_graph : r_eager);
     };
-    int rg = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);  // A ran in the graph
+    int rg = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2], c->gev[10]);  // A ran in the graph
     if (rg != DD_OK && rg != DD_ERR_MAXITER) return rg;
     if (guard == 2) {
         c->cur = 1 - parity;
@@ -1210,7 +1224,7 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     c->part[1].warm_valid = c->part[1].solved = true;
     c->part[1].pred_old_valid = mlp_keeps_old(c);
     {
-        int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);  // B ran in the graph
+        int r = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5], c->gev[11]);  // B ran in the graph
         if (r != DD_OK && r != DD_ERR_MAXITER) return r;
         if (r != DD_OK) rg = r;
     }
@@ -1238,9 +1252,9 @@ int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
             // statistics of the replayed iteration (objective / errors always, for
             // dd_get_objective); capped cells (DD_ERR_MAXITER, already in r)
             // neither end the statistics nor the remaining iterations
-            int r1 = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2]);
+            int r1 = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2], c->gev[10]);
             if (r1 != DD_OK && r1 != DD_ERR_MAXITER) return r1;
-            int r2 = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5]);
+            int r2 = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5], c->gev[11]);
             if (r2 != DD_OK && r2 != DD_ERR_MAXITER) return r2;
             flow_stats(c, c->g_value, c->g_piv, c->g_ms_solve, c->gev + 6, sf);
         }

@@ -75,7 +75,7 @@ __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const i
     const int T = blockDim.x;
     const int per = (nb + T - 1) / T;
     const int c0 = min(nb, threadIdx.x * per), c1 = min(nb, c0 + per);
-    long long sa = 0;
+    long long sa = 0, sin = 0, sout = 0;
     for (int j = c0; j < c1; ++j) {
         int lo1 = INT32_MAX, lo2 = INT32_MAX, hi1 = INT32_MIN, hi2 = INT32_MIN;
         for (int k = 0; k < 5; ++k) {
@@ -84,6 +84,7 @@ __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const i
             if (!(w[5 * i + rev[5 * j + k]] > 0.0)) continue;
             const int32_t* b = bhdr + BH_N * i;
             if (b[BH_H] <= 0 || b[BH_W] <= 0) continue;
+            sin += (long long)b[BH_H] * b[BH_W];
             lo1 = min(lo1, b[BH_O1]);
             lo2 = min(lo2, b[BH_O2]);
             hi1 = max(hi1, b[BH_O1] + b[BH_H]);
@@ -94,8 +95,11 @@ __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const i
         int32_t* x = xhdr + CH_N * j;
         x[CH_O1] = lo1; x[CH_O2] = lo2; x[CH_H] = h; x[CH_W] = ww; x[CH_STRIDE] = (ww + 3) & ~3;
         sa += (long long)h * ((ww + 3) & ~3);
+        sout += (long long)h * ww;
     }
-    long long ta;
+    long long ta, tin, tout;
+    (void)block_exscan_x(sin, sh, &tin);
+    (void)block_exscan_x(sout, sh, &tout);
     long long ea = block_exscan_x(sa, sh, &ta);
     for (int j = c0; j < c1; ++j) {
         int32_t* x = xhdr + CH_N * j;
@@ -104,6 +108,8 @@ __global__ void k_plan_exchange(int nb, const int32_t* __restrict__ nbr, const i
     }
     if (threadIdx.x == 0) {
         tot[PT_OUT] = ta;
+        tot[PT_PAD0] = tin;   // entries of the source boxes read (algorithmic bytes)
+        tot[PT_PAD1] = tout;  // entries of the new boxes written
         // graph mode: the output pool was captured with a fixed capacity
         if (guard && ta > pool_cap) atomicCAS(guard, 0, stage);
     }

@@ -134,7 +134,7 @@ struct dd_ctx {
     long long* d_soff = nullptr;
     double* d_cellmass = nullptr;
 
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[8] = {};  // eager timing: half-iteration 0-2 (ev[7]: CompositeToBasic), flow 3-6
     cudaStream_t side = nullptr;  // second stream: the large-box class of cells
     cudaStream_t side2 = nullptr;  // third stream: the cells solved by clusters
     cudaStream_t side3 = nullptr;  // step by step: the small-box class (normal priority)
@@ -177,7 +177,7 @@ struct dd_ctx {
     int32_t g_piv = 0;
     int g_frc = DD_OK;
     bool g_skipped = false;
-    cudaEvent_t gev[10] = {};
+    cudaEvent_t gev[12] = {};  // graph timing: A 0-2, B 3-5, flow 6-9, CompositeToBasic of A 10, of B 11
 
     // learned warm start: network, per-cell features / outputs / targets
     dd_mlp* mlp = nullptr;

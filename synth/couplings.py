@@ -142,26 +142,37 @@ def coarsen(a: np.ndarray) -> np.ndarray:
 
 
 def prolongate(boxes_c, mu, nu, s: int, noise: float = 0.01, seed: int = 0, tol: float = 1e-13,
-               max_sweeps: int = 500, trunc: float = 0.0):
+               max_sweeps: int = 500, trunc: float = 0.0, rebalance: str = "project"):
     """A fine initial plan from a coarse one (input recipe of the large 1024 x 1024
     configuration). boxes_c: basic-cell Y-marginals [(o1, o2, array)] of a plan
     for the 2 x 2-coarsened measures (coarsen(mu), coarsen(nu)) with the same
     cell size s; mu, nu the fine measures. Parent basic cell i -> its 4 children
     i' and coarse pixel y -> its 4 fine pixels y':
         nu_i'(y') = (m_i' / m_i) nu_i(parent(y')) nu(y') / coarsen(nu)(parent(y')),
-    each entry times (1 + noise u), u ~ U[-1, 1] (seeded), then iterative
-    proportional fitting on that support (rows: basic masses m_i', columns: nu)
-    until both L1 errors are below tol; optionally the entries below `trunc`
-    dropped and the rows scaled back to m_i' (the dropped mass then shows in the
-    Y error). Returns [(o1, o2, array)] on minimal boxes."""
+    which has both fine marginals exactly; then 1 % seeded multiplicative noise
+    (u ~ U[-1, 1]) and a rebalancing to the exact marginals:
+      * rebalance="project" (default): within each (parent cell, coarse pixel)
+        block of 4 children x 4 fine pixels the base plan is a (x) b
+        (a_k = share of child k, b_q = share of fine pixel q); the noise is
+        entry-wise base * noise * u~ with u~ = u minus its b-weighted row means
+        and a-weighted column means (plus the joint mean), which has zero row and
+        column sums in every block: both marginals stay exact in exact
+        arithmetic (float64 rounding only) and every entry stays within
+        (1 +- 4 noise) of its base value;
+      * rebalance="ipf": entries times (1 + noise u), then iterative proportional
+        fitting on that support (rows: basic masses m_i', columns: nu) until both
+        L1 errors are below tol or max_sweeps sweeps.
+    Optionally the entries below `trunc` are dropped and the rows scaled back to
+    m_i' (the dropped mass then shows in the Y error). Returns [(o1, o2, array)]
+    on minimal boxes."""
     rng = np.random.default_rng(seed)
     N1, N2 = mu.shape
     n2 = N2 // s
     nc2 = (N2 // 2) // s
     m = mu.reshape(N1 // s, s, n2, s).sum(axis=(1, 3)).reshape(-1)
     nuc = coarsen(nu)
-    # packed fine entries: cell index, pixel index, value
-    cells, pix, vals = [], [], []
+    # blocks: one per (parent cell, coarse pixel with mass); children k (4) x fine pixels q (4)
+    blk_cell, blk_pix, blk_val = [], [], []
     for ic, (o1, o2, a) in enumerate(boxes_c):
         a = np.asarray(a, dtype=np.float64)
         if a.size == 0:
@@ -169,33 +180,47 @@ def prolongate(boxes_c, mu, nu, s: int, noise: float = 0.01, seed: int = 0, tol:
         bi, bj = divmod(ic, nc2)
         mi = m.reshape(N1 // s, n2)[2 * bi:2 * bi + 2, 2 * bj:2 * bj + 2].reshape(-1)
         kids = np.array([(2 * bi + di) * n2 + 2 * bj + dj for di in (0, 1) for dj in (0, 1)])
-        y1 = 2 * (o1 + np.arange(a.shape[0]))
-        y2 = 2 * (o2 + np.arange(a.shape[1]))
-        F1 = (y1[:, None] + np.array([0, 1])[None, :]).reshape(-1)   # fine rows
-        F2 = (y2[:, None] + np.array([0, 1])[None, :]).reshape(-1)
-        up = np.kron(a, np.ones((2, 2)))                               # nu_i(parent(y'))
-        ratio = nu[np.ix_(F1, F2)] / np.kron(nuc[o1:o1 + a.shape[0], o2:o2 + a.shape[1]], np.ones((2, 2)))
-        base = up * ratio
-        P = (F1[:, None] * N2 + F2[None, :]).reshape(-1)
-        for k, c in enumerate(kids):
-            v = (mi[k] / mi.sum()) * base.reshape(-1)
-            keep = v > 0
-            cells.append(np.full(keep.sum(), c))
-            pix.append(P[keep])
-            vals.append(v[keep])
-    cell = np.concatenate(cells)
-    pix = np.concatenate(pix)
-    val = np.concatenate(vals) * (1.0 + noise * rng.uniform(-1.0, 1.0, size=sum(len(v) for v in vals)))
+        r, c = np.nonzero(a > 0)
+        if r.size == 0:
+            continue
+        Y1, Y2 = 2 * (o1 + r), 2 * (o2 + c)
+        fr = np.stack([Y1, Y1, Y1 + 1, Y1 + 1], axis=1)          # fine pixels q of each coarse pixel
+        fc = np.stack([Y2, Y2 + 1, Y2, Y2 + 1], axis=1)
+        share = nu[fr, fc] / nuc[o1 + r, o2 + c][:, None]          # b_q
+        ak = mi / mi.sum()                                         # a_k
+        base = a[r, c][:, None, None] * ak[None, :, None] * share[:, None, :]
+        blk_cell.append(np.broadcast_to(kids[None, :, None], base.shape))
+        blk_pix.append(np.broadcast_to((fr * N2 + fc)[:, None, :], base.shape))
+        blk_val.append(base)
+    base = np.concatenate(blk_val)                                 # (nblk, 4, 4)
+    cell_b = np.concatenate(blk_cell)
+    pix_b = np.concatenate(blk_pix)
+    u = rng.uniform(-1.0, 1.0, size=base.shape)
     nuf = nu.reshape(-1)
-    for _ in range(max_sweeps):
-        rs = np.bincount(cell, weights=val, minlength=len(m))
-        val *= (m / rs)[cell]
-        cs = np.bincount(pix, weights=val, minlength=nuf.size)
-        ex = np.abs(rs - m).sum()
-        val *= np.where(cs > 0, nuf / np.where(cs > 0, cs, 1.0), 1.0)[pix]
-        rs2 = np.bincount(cell, weights=val, minlength=len(m))
-        if np.abs(rs2 - m).sum() < tol and ex < tol:
-            break
+    if rebalance == "project":
+        tot = base.sum(axis=(1, 2), keepdims=True)
+        ak = base.sum(axis=2, keepdims=True) / tot                 # (nblk, 4, 1)
+        bq = base.sum(axis=1, keepdims=True) / tot                 # (nblk, 1, 4)
+        ut = u - (u * bq).sum(axis=2, keepdims=True) - (ak * u).sum(axis=1, keepdims=True) \
+            + (ak * u * bq).sum(axis=(1, 2), keepdims=True)
+        val3 = base * (1.0 + noise * ut)
+        cell, pix, val = cell_b.reshape(-1), pix_b.reshape(-1), val3.reshape(-1)
+    elif rebalance == "ipf":
+        cell, pix = cell_b.reshape(-1), pix_b.reshape(-1)
+        val = (base * (1.0 + noise * u)).reshape(-1)
+        for _ in range(max_sweeps):
+            rs = np.bincount(cell, weights=val, minlength=len(m))
+            val *= (m / rs)[cell]
+            cs = np.bincount(pix, weights=val, minlength=nuf.size)
+            ex = np.abs(rs - m).sum()
+            val *= np.where(cs > 0, nuf / np.where(cs > 0, cs, 1.0), 1.0)[pix]
+            rs2 = np.bincount(cell, weights=val, minlength=len(m))
+            if np.abs(rs2 - m).sum() < tol and ex < tol:
+                break
+    else:
+        raise ValueError("rebalance must be 'project' or 'ipf'")
+    keep = val > 0
+    cell, pix, val = cell[keep], pix[keep], val[keep]
     # drop entries below trunc, then the rows back to their masses (the dropped
     # mass, <= trunc per entry, goes to the Y error)
     if trunc > 0.0:

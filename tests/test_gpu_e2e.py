@@ -338,6 +338,42 @@ def test_dd1024_maximum_size(dd):
     g.close()
 
 
+def test_dd1024_from_prolongated_plan(dd):
+    """The 1024 x 1024 configuration from its configured initial plan: a 512 x 512
+    plan of the 2 x 2-coarsened measures (here after 10 hybrid iterations from KR
+    on the GPU), prolongated with 1 % seeded noise projected onto exact
+    marginals (synth.prolongate). The GPU plan is stored in FP32, so the fine plan
+    is feasible to FP32 storage (accepted with plan_tol 1e-6); the learned,
+    Anderson-accelerated solver then keeps both marginals over two hybrid
+    iterations, every half-iteration within the batch tolerance."""
+    from paper_2405_09400_gb300 import warmstart as ws
+
+    mu, nu, eps, p = synth.workload("dd1024", 0)
+    muc, nuc = synth.coarsen(mu), synth.coarsen(nu)
+    bc = synth.boxes_from_coupling(muc.shape, 4, *synth.knothe_rosenblatt(muc, nuc))
+    solver = dict(tol=1e-5, max_iter=20000, tol_share=1.0, tol_gamma=1.0, anderson=4)
+    gc = dd.DomDec(muc, nuc, 4 * eps, 4, boxes=bc, warm=dd.DD_WARM_PREV, **solver)
+    gc.step(10, stats=False)
+    coarse = [(o1, o2, a) for o1, o2, a in gc.plan()]
+    gc.close()
+    fine = synth.prolongate(coarse, mu, nu, 4, noise=0.01, seed=0)
+    geom = Geometry(1024, 1024, 4)
+    m = geom.basic_masses(mu)
+    assert np.allclose([a.sum() for _, _, a in fine], m, rtol=1e-6)
+    params, _ = ws.load_params()
+    g = dd.DomDec(mu, nu, eps, 4, boxes=fine, plan_tol=1e-6, warm=dd.DD_WARM_MLP, weights=params, **solver)
+    for _ in range(2):
+        sa, sb, sf = g.step(1)
+        assert sa["n_maxiter"] == 0 and sb["n_maxiter"] == 0
+        assert sa["l1_x"] <= 1e-5 and sb["l1_x"] <= 1e-5
+        assert sf["value"] <= 0
+    E, l1x, l1y = g.objective()
+    assert l1y <= 1e-6
+    got = np.array([b[2].sum() for b in g.plan()])
+    assert np.allclose(got, m, rtol=1e-5)
+    g.close()
+
+
 def test_four_bumps_flow_updates_remove_freezing(dd):
     """Section 5.2: mu = nu with four symmetric bumps, initial plan rotated by a
     quarter turn (Eq. T0), eps = (h/2)^2 (the paper's (dx/2)^2 on [-1, 1]^2), small
