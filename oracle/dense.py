@@ -79,17 +79,21 @@ def domdec_iter(pi, geom, part, mu, C, eps, tol=1e-12, max_iter=200000, alpha_pr
     return pi, alphas
 
 
-def flow_update(pi, geom, mu, C):
-    """Def. 3.4 with product gluing candidates. Returns (new plan, w, c_bar, value)."""
+def flow_update(pi, geom, mu, C, gammas=None):
+    """Def. 3.4 with gluing candidates: product (gammas None) or from the plans
+    gamma_ij in `gammas` ((i, k) -> rows X_i, columns X_j), Eq. (glued-plan).
+    Returns (new plan, w, c_bar, value)."""
     mu_f = mu.reshape(-1)
     nbr = geom.neighbours()
     m = geom.basic_masses(mu)
     rows = [cell_rows(geom, i) for i in range(geom.nb)]
     nu_i = [pi[r].sum(axis=0) for r in rows]
 
-    def cand(i, j):  # pi_hat_ij restricted to X_j x Y
+    def cand(i, j, k):  # pi_hat_ij restricted to X_j x Y
         if i == j:
             return pi[rows[i]] / m[i]
+        if gammas is not None:  # sum_{x'} gamma(x', x) pi_i(x', y) / mu(x')
+            return gammas[(i, k)].T @ (pi[rows[i]] / mu_f[rows[i]][:, None])
         return np.outer(mu_f[rows[j]] / m[j], nu_i[i] / m[i])
 
     cbar = np.full((geom.nb, 5), np.nan)
@@ -97,12 +101,12 @@ def flow_update(pi, geom, mu, C):
         for k in range(5):
             j = nbr[i, k]
             if j >= 0:
-                cbar[i, k] = float(np.sum(C[rows[j]] * cand(i, j)) - np.sum(C[rows[i]] * cand(i, i)))
+                cbar[i, k] = float(np.sum(C[rows[j]] * cand(i, j, k)) - np.sum(C[rows[i]] * cand(i, i, 0)))
     w, value, _ = min_cost_flow(nbr, cbar, m)
     new = np.zeros_like(pi)
     for i in range(geom.nb):
         for k in range(5):
             j = nbr[i, k]
             if j >= 0 and w[i, k] > 0:
-                new[rows[j]] += w[i, k] * cand(i, j)
+                new[rows[j]] += w[i, k] * cand(i, j, k)
     return new, w, cbar, value

@@ -1,8 +1,10 @@
 """The flow update (Section 3.2) on the basic-cell box state.
 
-Edge candidates are product gluing candidates (Def. 3.7 with gamma_ij the
-product coupling, Remark 3.8): pi_hat_ij = mu_j/m_j (x) nu_i/m_i for j != i, and
-pi_hat_ii = pi_i/m_i (Def. 3.4). The edge cost Eq. (edge-cost) is then
+Edge candidates are gluing candidates (Def. 3.7): with gamma_ij the product
+coupling (Remark 3.8, eps_gamma = inf), pi_hat_ij = mu_j/m_j (x) nu_i/m_i for
+j != i, and pi_hat_ii = pi_i/m_i (Def. 3.4); with an entropic gamma_ij (small
+eps_gamma) see gluing_plan / edge_costs_glued below. For the product candidate
+the edge cost Eq. (edge-cost) is
 
     c_bar_ij = <c, mu_j/m_j (x) nu_i/m_i> - <c, pi_i> / m_i   (j != i),
     c_bar_ii = 0,
@@ -25,7 +27,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.optimize import linprog
 
-from .cell import sq_cost
+from .cell import cell_sinkhorn, gibbs_plan, sq_cost
 from .domdec import Box, box_pixels, embed, truncate_box, union_header
 
 
@@ -49,6 +51,70 @@ def edge_costs(geom, mu, boxes, D, hgrid) -> np.ndarray:
             mu_j = mu[Xj[:, 0], Xj[:, 1]] / m[j]
             cand = float(mu_j @ sq_cost(Xj, Y, hgrid) @ nu_i)
             cbar[i, k] = cand - D[i] / m[i]
+    return cbar
+
+
+def gluing_plan(geom, mu, i, j, hgrid, eps_gamma, tol=1e-13, max_iter=1000000):
+    """gamma_ij in Pi(mu_i/m_i, mu_j/m_j) for the gluing edge candidate (Def. 3.7,
+    Remark 3.8): the entropic optimal plan between the normalised basic-cell
+    measures for the squared distance on X with regularisation eps_gamma (the
+    paper's small-eps_gamma choice), solved by the oracle's dense log-domain
+    Sinkhorn (cell.cell_sinkhorn: Y-marginal mu_j/m_j exact, X-marginal within
+    tol); eps_gamma = inf gives the product coupling. Rows over X_i, columns
+    over X_j, in Geometry.cell_pixels order."""
+    Xi, Xj = geom.cell_pixels(i), geom.cell_pixels(j)
+    a = mu[Xi[:, 0], Xi[:, 1]]
+    b = mu[Xj[:, 0], Xj[:, 1]]
+    a, b = a / a.sum(), b / b.sum()
+    if not np.isfinite(eps_gamma):
+        return np.outer(a, b)
+    C = sq_cost(Xi, Xj, hgrid)
+    res = cell_sinkhorn(a, b, C, eps_gamma, np.zeros(len(a)), tol=tol, max_iter=max_iter)
+    return gibbs_plan(res["alpha"], res["beta_t"], a, b, C, eps_gamma)
+
+
+def gluing_plans(geom, mu, hgrid, eps_gamma):
+    """gamma_ij for every edge (i, j) of the neighbourhood set with j != i, keyed
+    by (i, k) with j = Geometry.neighbours()[i, k]."""
+    nbr = geom.neighbours()
+    return {(i, k): gluing_plan(geom, mu, i, int(nbr[i, k]), hgrid, eps_gamma)
+            for i in range(geom.nb) for k in range(1, 5) if nbr[i, k] >= 0}
+
+
+def glued_candidate(G, pi_i, mu_i):
+    """pi_hat_ij on X_j x Y from gamma_ij (G, rows X_i, columns X_j) and the
+    basic-cell plan pi_i (rows X_i) by Eq. (glued-plan): the disintegration of
+    gamma_ij at x' (G[x', .] m_i / mu(x')) times the disintegration of pi_i at
+    x' (pi_i(x', .) / mu(x')), integrated against mu_i / m_i, i.e.
+        pi_hat_ij(x, y) = sum_{x'} G[x', x] pi_i(x', y) / mu(x'),
+    the matrix product of Remark 3.8."""
+    return G.T @ (pi_i / mu_i[:, None])
+
+
+def edge_costs_glued(geom, mu, plans, D, hgrid, gammas) -> np.ndarray:
+    """c_bar (nb, 5) of Eq. (edge-cost) with gluing edge candidates:
+    c_bar_ij = <c, pi_hat_ij> - D_i / m_i, pi_hat_ij = glued_candidate(gamma_ij, pi_i),
+    evaluated as explicit sums over X_j x Y. plans[i] = (Y pixels (ny, 2), pi_i
+    (s^2, ny)): the basic cell's part of the Gibbs cell plan of the latest
+    half-iteration, the plan D_i = <c, pi_i> comes from (reading: both terms from
+    the same plan, before balancing)."""
+    nbr = geom.neighbours()
+    m = geom.basic_masses(mu)
+    cbar = np.full((geom.nb, 5), np.nan)
+    for i in range(geom.nb):
+        Y, pi_i = plans[i]
+        Xi = geom.cell_pixels(i)
+        mu_i = mu[Xi[:, 0], Xi[:, 1]]
+        for k in range(5):
+            j = nbr[i, k]
+            if j < 0:
+                continue
+            if j == i:
+                cbar[i, k] = 0.0
+                continue
+            Xj = geom.cell_pixels(j)
+            cand = glued_candidate(gammas[(i, k)], pi_i, mu_i)
+            cbar[i, k] = float(np.sum(sq_cost(Xj, Y, hgrid) * cand)) - D[i] / m[i]
     return cbar
 
 

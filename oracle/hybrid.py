@@ -14,13 +14,16 @@ from __future__ import annotations
 import numpy as np
 
 from .domdec import Box, half_iteration, l1_y_error, truncate_box
-from .flow import edge_costs, exchange, min_cost_flow
+from .flow import edge_costs, edge_costs_glued, exchange, gluing_plans, min_cost_flow
 from .geometry import Geometry
 
 
 class OracleDD:
     def __init__(self, mu, nu, eps, s, boxes=None, tol=1e-5, max_iter=100000,
-                 fixed_iters=None, thr=1e-15, hgrid=None):
+                 fixed_iters=None, thr=1e-15, hgrid=None, eps_gamma=None):
+        """eps_gamma: None (or inf) for product gluing candidates, else the
+        regularisation of the entropic gamma_ij of the gluing candidates
+        (Def. 3.7, Remark 3.8)."""
         self.mu = np.asarray(mu, dtype=np.float64)
         self.nu = np.asarray(nu, dtype=np.float64)
         self.eps = float(eps)
@@ -35,6 +38,9 @@ class OracleDD:
                       for b in boxes]
         self.alpha = {0: None, 1: None}
         self.D = None
+        self.eps_gamma = None if eps_gamma is None or not np.isfinite(eps_gamma) else float(eps_gamma)
+        self.gammas = None
+        self.basic_plans = None  # per basic cell (Y pixels, pi_i) of the latest half-iteration
         self.k = 0
         self.history = []
 
@@ -49,11 +55,18 @@ class OracleDD:
         self.eps = float(eps)
 
     def iterate(self, part: int, keep_plans=False):
+        glued = self.eps_gamma is not None
         self.boxes, info = half_iteration(
             self.geom, self.mu, self.nu, self.eps, self.hgrid, self.boxes, part,
-            self.alpha[part], self.tol, self.max_iter, self.fixed_iters, self.thr, keep_plans)
+            self.alpha[part], self.tol, self.max_iter, self.fixed_iters, self.thr, keep_plans or glued)
         self.alpha[part] = info["alpha"]
         self.D = info["D"]
+        if glued:  # the basic cells' rows of the Gibbs cell plans (member-major)
+            ss = self.geom.s * self.geom.s
+            self.basic_plans = [None] * self.geom.nb
+            for members, (X, Y, pi) in zip(self.geom.partition(part), info["plans"]):
+                for k, i in enumerate(members):
+                    self.basic_plans[i] = (Y, pi[k * ss:(k + 1) * ss])
         info["l1_y"] = l1_y_error(self.boxes, self.nu)
         self.history.append(("A" if part == 0 else "B", info["E"], info["l1_x"], info["l1_y"]))
         return info
@@ -62,7 +75,12 @@ class OracleDD:
         if self.D is None:
             raise RuntimeError("flow update needs a preceding half-iteration")
         nbr = self.geom.neighbours()
-        cbar = edge_costs(self.geom, self.mu, self.boxes, self.D, self.hgrid)
+        if self.eps_gamma is None:
+            cbar = edge_costs(self.geom, self.mu, self.boxes, self.D, self.hgrid)
+        else:
+            if self.gammas is None:
+                self.gammas = gluing_plans(self.geom, self.mu, self.hgrid, self.eps_gamma)
+            cbar = edge_costs_glued(self.geom, self.mu, self.basic_plans, self.D, self.hgrid, self.gammas)
         w, value, _ = min_cost_flow(nbr, cbar, self.m)
         self.boxes = exchange(self.geom, self.boxes, w, nbr, self.m, self.thr)
         self.D = None

@@ -165,3 +165,144 @@ def test_flow_update_lemmas_on_full_plan():
     assert l1_y_error(o.boxes, mu) < 1e-13
     m = g.basic_masses(mu)
     assert np.allclose([b.a.sum() for b in o.boxes], m, rtol=1e-10, atol=0)
+
+
+def _small_gluing(N=8, s=2, seed=3):
+    mu = synth.gaussian_mixture(N, 2, (0.1, 0.3), 1e-2, seed=seed)
+    g = Geometry(N, N, s)
+    return mu, g
+
+
+def test_gluing_plan_is_a_coupling_and_limits():
+    """gamma_ij (Def. 3.7): a coupling of mu_i/m_i and mu_j/m_j (both marginals to
+    1e-12); eps_gamma = inf is the product coupling; for a small eps_gamma it
+    concentrates on the optimal assignment between the two blocks (adjacent
+    blocks of a constant measure: the translation by one cell, mass on the
+    shifted pixel >= 0.99)."""
+    from oracle.flow import gluing_plan
+
+    mu, g = _small_gluing()
+    nbr = g.neighbours()
+    for i in (0, 5, 9):
+        for k in range(1, 5):
+            j = nbr[i, k]
+            if j < 0:
+                continue
+            G = gluing_plan(g, mu, i, j, 1.0 / 8, (0.5 / 8) ** 2)
+            Xi, Xj = g.cell_pixels(i), g.cell_pixels(j)
+            a = mu[Xi[:, 0], Xi[:, 1]]
+            b = mu[Xj[:, 0], Xj[:, 1]]
+            assert np.abs(G.sum(axis=1) - a / a.sum()).sum() < 1e-12
+            assert np.abs(G.sum(axis=0) - b / b.sum()).sum() < 1e-12
+            P = gluing_plan(g, mu, i, j, 1.0 / 8, np.inf)
+            assert np.allclose(P, np.outer(a / a.sum(), b / b.sum()), rtol=1e-15)
+    # constant measure: the small-eps plan is (nearly) the translation
+    N, s = 8, 4
+    mu = np.full((N, N), 1.0 / N ** 2)
+    g = Geometry(N, N, s)
+    G = gluing_plan(g, mu, 0, 1, 1.0 / N, (0.1 / N) ** 2)
+    Xi, Xj = g.cell_pixels(0), g.cell_pixels(1)
+    shifted = [int(np.flatnonzero((Xj == Xi[q] + np.array([0, s])).all(axis=1))[0]) for q in range(len(Xi))]
+    assert min(G[q, shifted[q]] * len(Xi) for q in range(len(Xi))) >= 0.99
+
+
+def test_glued_candidate_lemma_3_9_items_1_and_2():
+    """Lemma 3.9 (1): pi_hat_ij in Pi(mu_j/m_j, nu_i/m_i); (2): its density w.r.t.
+    mu_j (x) nu is (1/m_j) int dpi_i/d(mu_i (x) nu)(x', y) d(gamma_ij)_x(x') with
+    (gamma_ij)_x the disintegration against the mu_j/m_j marginal -- computed
+    here by that formula, independently of the matrix product."""
+    from oracle.flow import glued_candidate, gluing_plan
+
+    N, s = 8, 2
+    mu, g = _small_gluing(N, s)
+    nu = synth.gaussian_mixture(N, 2, (0.1, 0.3), 1e-2, seed=4)
+    C = dense.cost_matrix(N, N, 1.0 / N)
+    pi, _ = dense.global_sinkhorn(mu, nu, 4.0 / N ** 2, 1.0 / N, tol=1e-14)
+    m = g.basic_masses(mu)
+    nbr = g.neighbours()
+    nuf = nu.reshape(-1)
+    for i in (0, 6, 10):
+        rows_i = dense.cell_rows(g, i)
+        mu_i = mu.reshape(-1)[rows_i]
+        pi_i = pi[rows_i]
+        for k in range(1, 5):
+            j = nbr[i, k]
+            if j < 0:
+                continue
+            G = gluing_plan(g, mu, i, j, 1.0 / N, (0.5 / N) ** 2)
+            cand = glued_candidate(G, pi_i, mu_i)
+            mu_j = mu.reshape(-1)[dense.cell_rows(g, j)]
+            assert np.abs(cand.sum(axis=1) - mu_j / m[j]).sum() < 1e-12
+            assert np.abs(cand.sum(axis=0) - pi_i.sum(axis=0) / m[i]).sum() < 1e-12
+            dens_i = pi_i / (mu_i[:, None] * nuf[None, :])          # dpi_i / d(mu_i (x) nu)
+            cond = G / (mu_j / m[j])[None, :]                       # (gamma)_x(x') over x'
+            dens = (cond.T @ dens_i) / m[j]
+            assert np.allclose(cand, dens * mu_j[:, None] * nuf[None, :], rtol=1e-11, atol=1e-18)
+    _ = C
+
+
+def test_glued_flow_update_on_full_plan_and_box_version():
+    """Flow update with gluing candidates from entropic gamma_ij (eps_gamma =
+    (h/2)^2) on a full plan: marginals kept (Lemma 3.5), the transport-cost change
+    equals the optimal value (Eq. total-cost-update), the entropy term does not
+    increase (Lemma 3.9 (3)) and so the objective decreases (Prop. 3.10). The
+    box version (OracleDD with eps_gamma) has the same edge costs, value and new
+    basic marginals."""
+    from oracle.flow import gluing_plans
+
+    N, s = 8, 2
+    mu = synth.four_bumps(N)
+    eps = 1.0 / N ** 2
+    g = Geometry(N, N, s)
+    C = dense.cost_matrix(N, N, 1.0 / N)
+    pi = np.zeros((N * N, N * N))
+    x, y, mm = synth.rotation_coupling(mu)
+    pi[x, y] = mm
+    pi, _ = dense.domdec_iter(pi, g, 0, mu, C, eps, tol=1e-12)
+    gam = gluing_plans(g, mu, 1.0 / N, (0.5 / N) ** 2)
+    new, w, cbar, value = dense.flow_update(pi, g, mu, C, gammas=gam)
+    assert value < -1e-6
+    assert np.abs(new.sum(axis=0) - pi.sum(axis=0)).sum() < 1e-14
+    assert np.abs(new.sum(axis=1) - pi.sum(axis=1)).sum() < 1e-12
+    ref = np.outer(mu.reshape(-1), mu.reshape(-1))
+    assert float((C * new).sum() - (C * pi).sum()) == pytest.approx(value, rel=1e-12, abs=1e-16)
+    assert dense.kl(new, ref) <= dense.kl(pi, ref) + 1e-14
+    assert dense.objective(new, mu, mu, C, eps) < dense.objective(pi, mu, mu, C, eps)
+    # the product candidates give a different (weaker or equal) flow value here
+    _, _, cbar_p, value_p = dense.flow_update(pi, g, mu, C)
+    assert not np.allclose(cbar[~np.isnan(cbar)], cbar_p[~np.isnan(cbar_p)])
+    # box version
+    boxes = synth.boxes_from_coupling(mu.shape, s, x, y, mm)
+    o = OracleDD(mu, mu, eps, s, boxes=boxes, tol=1e-12, eps_gamma=(0.5 / N) ** 2)
+    o.iterate(0)
+    f = o.flow_update()
+    assert np.allclose(f["cbar"][~np.isnan(cbar)], cbar[~np.isnan(cbar)], rtol=1e-8, atol=1e-14)
+    assert f["value"] == pytest.approx(value, rel=1e-9)
+    for i in range(g.nb):
+        ref_i = new[dense.cell_rows(g, i)].sum(axis=0).reshape(N, N)
+        assert np.abs(embed(o.boxes[i], 0, 0, N, N) - ref_i).sum() < 1e-10
+
+
+def test_glued_costs_with_product_gamma_equal_product_costs():
+    """eps_gamma = inf: edge_costs_glued (matrix product of the plan) equals the
+    product-candidate edge_costs (moments of the basic marginals) on the same
+    pre-balance plan, to 1e-12 relative."""
+    from oracle.domdec import Box
+    from oracle.flow import edge_costs, edge_costs_glued, gluing_plans
+
+    N, s = 16, 4
+    mu, nu, eps, p = synth.workload("dd32", 0, N=N)
+    o = OracleDD(mu, nu, eps, s, tol=1e-10, eps_gamma=1e30)
+    o.iterate(0)
+    g = o.geom
+    gam = gluing_plans(g, mu, 1.0 / N, np.inf)
+    cg = edge_costs_glued(g, mu, o.basic_plans, o.D, 1.0 / N, gam)
+    pre = []
+    for i in range(g.nb):
+        Y, pi_i = o.basic_plans[i]
+        a = np.zeros((N, N))
+        np.add.at(a, (Y[:, 0], Y[:, 1]), pi_i.sum(axis=0))
+        pre.append(Box(0, 0, a))
+    cp = edge_costs(g, mu, pre, o.D, 1.0 / N)
+    ok = ~np.isnan(cp)
+    assert np.allclose(cg[ok], cp[ok], rtol=1e-12, atol=1e-15 * np.abs(cp[ok]).max())
