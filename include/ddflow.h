@@ -122,6 +122,13 @@ typedef struct dd_options {
                             mu-weighted least squares on the residuals, restarted
                             when the L1 X error more than doubles; same fixed point,
                             same stopping pair (alpha_old, beta); omega is ignored */
+    double eps_gamma;    /* edge candidates of the flow update (Def. 3.7, Remark 3.8):
+                            0 (default) = product gluing candidates (eps_gamma =
+                            infinity); > 0 = gluing candidates from the entropic
+                            optimal plans gamma_ij between mu_i / m_i and mu_j / m_j
+                            at this regularisation (cost units, like eps), computed
+                            once by dd_init in FP64 (L1 marginal error <= 1e-13);
+                            cell_size <= 8                                         */
 } dd_options;
 
 /* Statistics of one half-iteration (Alg. 4). */

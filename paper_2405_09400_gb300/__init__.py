@@ -50,7 +50,8 @@ class dd_options(C.Structure):
                 ("init_kind", C.c_int32), ("warm", C.c_int32), ("threads", C.c_int32), ("flags", C.c_int32),
                 ("plan_tol", C.c_double), ("omega", C.c_double), ("graph_margin", C.c_double),
                 ("eps_levels", C.c_int32), ("eps_factor", C.c_double), ("eps_tol", C.c_double),
-                ("tol_share", C.c_double), ("tol_gamma", C.c_double), ("anderson", C.c_int32)]
+                ("tol_share", C.c_double), ("tol_gamma", C.c_double), ("anderson", C.c_int32),
+                ("eps_gamma", C.c_double)]
 
 
 class dd_stats(C.Structure):

@@ -256,6 +256,7 @@ void dd_default_options(dd_options* o) {
     o->tol_share = 0.0;
     o->tol_gamma = 0.0;
     o->anderson = 0;
+    o->eps_gamma = 0.0;
 }
 
 const char* dd_last_error(void) { return g_last_error; }
@@ -304,6 +305,7 @@ void dd_destroy(dd_ctx* c) {
     if (c->mlp) dd_mlp_destroy(c->mlp);
     dfree(c->d_cbar); dfree(c->d_w); dfree(c->d_xhdr); dfree(c->d_yacc); dfree(c->d_red);
     dfree(c->d_plan64); dfree(c->d_soff); dfree(c->d_cellmass);
+    dfree(c->d_gAB); dfree(c->d_pmom);
     if (c->h_tot) cudaFreeHost(c->h_tot);
     if (c->h_cbar) cudaFreeHost(c->h_cbar);
     if (c->h_w) cudaFreeHost(c->h_w);
@@ -352,7 +354,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         c->opt.eps_levels < 0 || c->opt.eps_levels > 8 ||
         (c->opt.eps_levels > 0 && !(c->opt.eps_factor > 1.0 && c->opt.eps_tol > 0.0)) || (learned && s != 4) ||
         !(c->opt.tol_share >= 0.0 && c->opt.tol_share <= 1.0) || !(c->opt.tol_gamma >= 0.0 && c->opt.tol_gamma <= 4.0) ||
-        c->opt.anderson < 0 || c->opt.anderson > 4) {
+        c->opt.anderson < 0 || c->opt.anderson > 4 || !(c->opt.eps_gamma >= 0.0) || !std::isfinite(c->opt.eps_gamma) ||
+        (c->opt.eps_gamma > 0.0 && s > 8)) {
         delete c;
         return DD_ERR_ARG;
     }
@@ -517,6 +520,19 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
             rc = DD_ERR_CUDA;
             goto fail;
+        }
+        if (c->opt.eps_gamma > 0.0) {
+            // gluing candidates: gamma_ij of every directed edge, once (mu is fixed)
+            const size_t n = (size_t)c->s * c->s;
+            TRY(dmalloc(&c->d_gAB, (size_t)c->nb * 4 * n * 3));
+            TRY(dmalloc(&c->d_pmom, (size_t)c->nb * n * 3));
+            if (cudaMemsetAsync(c->d_pmom, 0, sizeof(double) * c->nb * n * 3, c->stream) != cudaSuccess ||
+                cudaMemsetAsync(c->d_status + 6, 0, sizeof(int), c->stream) != cudaSuccess) {
+                rc = DD_ERR_CUDA;
+                goto fail;
+            }
+            TRY(launch_gamma(c, c->d_status + 6));
+            c->n_launch += 1;
         }
         if (c->opt.init_kind == DD_INIT_PRODUCT) {
             // nu_i = m_i nu on the whole grid, truncated like every other state

@@ -248,6 +248,7 @@ __global__ void k_l1y(long long n, const double* __restrict__ acc, const double*
 }  // namespace
 
 int launch_cbar(dd_ctx* c) {
+    if (c->opt.eps_gamma > 0.0) return launch_cbar_glued(c);
     k_cbar<<<(c->nb + 255) / 256, 256, 0, c->stream>>>(c->nb, c->d_nbr, c->d_xmom, c->d_bmom, c->d_m,
                                                        c->h * c->h, c->d_cbar, c->capturing ? c->d_guard : nullptr);
     return launch_status(__func__);

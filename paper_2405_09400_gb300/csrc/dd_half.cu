@@ -238,6 +238,9 @@ struct HalfArgs {
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
     // Anderson acceleration of the X-dual iteration (tolerance mode): memory, 0 = off
     int aa_m;
+    // gluing edge candidates: per basic cell and pixel, mass r and mean displacement
+    // d (2) of the Gibbs cell plan (nb x s^2 x 3, FP64), or null (product candidates)
+    double* pmom;
     // eps-scaling inside each solve (tolerance mode only): levels eps f^L .. eps
     int eps_levels;
     float eps_factor;
@@ -1636,6 +1639,8 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
         float* tab1;
         float* tab2;
         float* a;
+        float* L;  // gluing candidates: per (v1, u2) log2 of the row sum over v2, and
+        float* E;  // the mean of v2 under it (h x 2s each)
         float* coef;
         int* ctl;
     } S;
@@ -1645,6 +1650,8 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     S.tab1 = f; f += A.smaxH * s2;
     S.tab2 = f; f += BS * s2;
     S.a = f; f += A.amax;
+    S.L = f; f += A.pmom ? A.smaxH * s2 : 0;
+    S.E = f; f += A.pmom ? A.smaxH * s2 : 0;
     S.coef = f; f += 16;
     S.ctl = reinterpret_cast<int*>(f);
     if (reinterpret_cast<char*>(f + 32) - smem_raw > (long long)dyn_smem_bytes()) {
@@ -1678,6 +1685,61 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     for (int u = tid; u < nx; u += NT) S.a[u] = ap[u];
     float* aC = S.a;
     __syncthreads();
+
+    // ---- per-pixel moments of the cell plan (gluing candidates) ------------
+    // pi(u, v) = 2^(a(u) + b~(v) - tab1(u1, v1) - tab2(u2, v2)) for the returned
+    // pair (its Y-marginal is nu_J). For every pixel u of the block: the mass
+    // r(u) = sum_v pi(u, v) and the mean displacement d(u) = E[y | u] - x(u),
+    // separable like the X-update: per (v1, u2) the row sum over v2 and the mean
+    // of v2 under it, then per u the sum over v1.
+    if (A.pmom) {
+        for (int q = tid; q < h * wx; q += NT) {
+            const int v1 = q / wx, u2 = q - v1 * wx;
+            const float* br = A.comp_b + comp + (long long)v1 * stride;
+            const float* tb = S.tab2 + u2 * bs;
+            float mx = DD_NEG;
+            for (int v2 = 0; v2 < w; ++v2)
+                if (br[v2] > 0.5f * DD_NEG) mx = fmaxf(mx, br[v2] - tb[v2]);
+            float t0 = 0.f, t1 = 0.f;
+            if (mx > 0.5f * DD_NEG)
+                for (int v2 = 0; v2 < w; ++v2)
+                    if (br[v2] > 0.5f * DD_NEG) {
+                        const float e = ex2f(br[v2] - tb[v2] - mx);
+                        t0 += e;
+                        t1 += e * (float)v2;
+                    }
+            S.L[q] = t0 > 0.f ? mx + lg2f(t0) : DD_NEG;
+            S.E[q] = t0 > 0.f ? t1 / t0 : 0.f;
+        }
+        __syncthreads();
+        for (int u = tid; u < nx; u += NT) {
+            const int u1 = u / wx, u2 = u - u1 * wx;
+            const float* tb = S.tab1 + u1 * h;
+            float mx = DD_NEG;
+            for (int v1 = 0; v1 < h; ++v1)
+                if (S.L[v1 * wx + u2] > 0.5f * DD_NEG) mx = fmaxf(mx, S.L[v1 * wx + u2] - tb[v1]);
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            if (mx > 0.5f * DD_NEG)
+                for (int v1 = 0; v1 < h; ++v1) {
+                    const float Lv = S.L[v1 * wx + u2];
+                    if (!(Lv > 0.5f * DD_NEG)) continue;
+                    const float e = ex2f(Lv - tb[v1] - mx);
+                    t0 += e;
+                    t1 += e * (float)v1;
+                    t2 += e * S.E[v1 * wx + u2];
+                }
+            const bool live = aC[u] > 0.5f * DD_NEG && t0 > 0.f;
+            const double r = live ? exp2((double)aC[u] + (double)mx + (double)lg2f(t0)) : 0.0;
+            const double e1 = live ? (double)(t1 / t0) : 0.0, e2 = live ? (double)(t2 / t0) : 0.0;
+            const int rg = u1 / s, cg = u2 / s, k = rg * (wx / s) + cg;
+            if (k >= nmem) continue;
+            const int q = (u1 - rg * s) * s + (u2 - cg * s);
+            double* pm = A.pmom + ((long long)mem[k] * s * s + q) * 3;
+            pm[0] = r;
+            pm[1] = live ? (double)(o1 - r0) + e1 - (double)u1 : 0.0;
+            pm[2] = live ? (double)(o2 - c0) + e2 - (double)u2 : 0.0;
+        }
+    }
 
     // ---- 3. CompositeToBasic with D_i -----------------------------------
     // C1: per column group cg, T2(cg, u1, v2) = LSE over u2 in the group, and
@@ -1916,7 +1978,8 @@ size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long m
 
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw) {
     const size_t s2 = 2 * c->s, BS = (size_t)padw((int)maxw);
-    size_t fl = 4 * s2 * BS + (size_t)maxh * s2 + BS * s2 + (size_t)c->amax + 16 + 32;
+    size_t fl = 4 * s2 * BS + (size_t)maxh * s2 + BS * s2 + (size_t)c->amax + 16 + 32 +
+                (c->opt.eps_gamma > 0.0 ? 2 * (size_t)maxh * s2 : 0);
     return sizeof(double) * (32 * 16 + 16) + sizeof(float) * fl;
 }
 
@@ -2061,6 +2124,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.count = nullptr;
     A.trace = (c->opt.flags & DD_FLAG_TRACE) ? c->d_trace[part] : nullptr;
     A.aa_m = c->opt.fixed_iters > 0 ? 0 : c->opt.anderson;
+    A.pmom = c->opt.eps_gamma > 0.0 ? c->d_pmom : nullptr;
     A.eps_levels = c->opt.eps_levels;
     A.eps_factor = (float)c->opt.eps_factor;
     A.eps_tol = c->opt.eps_tol;

@@ -124,6 +124,12 @@ struct dd_ctx {
     dd_flow_stats last_flow{};
     McfSolver* mcf = nullptr;  // persistent basis across flow updates
 
+    // gluing edge candidates (opt.eps_gamma > 0): per directed edge (i, k = 1..4) and
+    // pixel x' of X_i the moments A, B (3) of gamma_ij's disintegration at x';
+    // per basic cell and pixel the mass and mean displacement (3) of the cell plan
+    double* d_gAB = nullptr;   // nb x 4 x s^2 x 3
+    double* d_pmom = nullptr;  // nb x s^2 x 3
+
     // l1_y scratch
     double* d_yacc = nullptr;
     double* d_red = nullptr;
@@ -247,3 +253,6 @@ int launch_cbar(dd_ctx* c);
 int launch_plan_exchange(dd_ctx* c, int stage = 0);
 int launch_exchange(dd_ctx* c);
 int launch_l1y(dd_ctx* c, double* out_dev);
+// dd_glue.cu
+int launch_gamma(dd_ctx* c, int* status_dev);
+int launch_cbar_glued(dd_ctx* c);

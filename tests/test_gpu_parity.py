@@ -286,3 +286,64 @@ def test_cell_lse_box_sweep_cells_match_oracle(dd, m, small_threads):
             assert (o1, o2, got.shape) == (nuJ.o1, nuJ.o2, nuJ.a.shape)
             assert np.abs(got - arrs[k]).sum() <= 1e-5 * mi[i], (m, J, i)
             assert abs(D[i] - Dref[k]) <= 1e-5 * abs(Dref[k]), (m, J, i)
+
+
+def _basic_plans_from_gpu_duals(g, part, mu, nu, eps, geom):
+    """The Gibbs cell plans of the GPU's exported duals (FP64), split into the
+    basic cells' rows: per basic cell (Y pixels, pi_i), and D_i = <c, pi_i>."""
+    alpha, betas = g.duals(part)
+    comp = g.composite(part)
+    N = mu.shape[0]
+    ss = geom.s * geom.s
+    plans, D = [None] * geom.nb, np.zeros(geom.nb)
+    for J, members in enumerate(geom.partition(part)):
+        X = geom.composite_pixels(members)
+        o1, o2, nuJ = comp[J]
+        _, _, beta = betas[J]
+        Y = box_pixels(o1, o2, nuJ.shape[0], nuJ.shape[1])
+        supp = nuJ.reshape(-1) > 0
+        C = sq_cost(X, Y[supp], 1.0 / N)
+        a = alpha[X[:, 0], X[:, 1]]
+        b = beta.reshape(-1)[supp]
+        pi = np.exp((a[:, None] + b[None, :] - C) / eps) * mu[X[:, 0], X[:, 1]][:, None] * nu[Y[supp][:, 0], Y[supp][:, 1]][None, :]
+        for k, i in enumerate(members):
+            plans[i] = (Y[supp], pi[k * ss:(k + 1) * ss])
+            D[i] = float((C[k * ss:(k + 1) * ss] * pi[k * ss:(k + 1) * ss]).sum())
+    return plans, D
+
+
+def test_glued_edge_costs_match_oracle_on_gpu_state(dd):
+    """Gluing candidates from entropic gamma_ij (eps_gamma = (h/2)^2, Def. 3.7,
+    Remark 3.8): the library's edge costs (gamma_ij by its FP64 device solve,
+    the per-pixel mass and mean displacement of each cell plan from the FP32
+    duals) against the oracle's explicit sums <c, pi_hat_ij> - D_i / m_i over the
+    matrix-product candidate of Eq. (glued-plan), built from the same exported
+    duals in FP64 with the oracle's own gamma_ij. Both terms of c_bar come from
+    FP32 plan moments summed in FP32 per pixel (relative ~1e-6 each, the terms up
+    to max |c_bar|): within 2e-6 of max |c_bar|; then the flow value equals the
+    oracle LP's on those costs (1e-9) and the exchange matches."""
+    from oracle.flow import edge_costs_glued, gluing_plans
+
+    N, s = 32, 4
+    mu, nu, eps, _ = synth.workload("dd32", 0, N=N)
+    geom = Geometry(N, N, s)
+    m = geom.basic_masses(mu)
+    nbr = geom.neighbours()
+    eg = (0.5 / N) ** 2
+    g = dd.DomDec(mu, nu, eps, s, tol=1e-6, eps_gamma=eg)
+    g.iterate(0)
+    g.iterate(1)
+    state = as_boxes(g.plan())
+    f = g.flow_update()
+    cbar, w = g.flow()
+    plans, D = _basic_plans_from_gpu_duals(g, 1, mu, nu, eps, geom)
+    ref = edge_costs_glued(geom, mu, plans, D, 1.0 / N, gluing_plans(geom, mu, 1.0 / N, eg))
+    ok = ~np.isnan(ref)
+    scale = np.abs(ref[ok]).max()
+    assert np.abs(cbar[ok] - ref[ok]).max() <= 2e-6 * scale, np.abs(cbar[ok] - ref[ok]).max() / scale
+    _, val_ref, _ = min_cost_flow(nbr, cbar, m)
+    assert f["value"] == pytest.approx(val_ref, rel=1e-9, abs=1e-18)
+    assert f["value"] < 0
+    new_ref = exchange(geom, state, w, nbr, m, 1e-15)
+    assert plan_l1(as_boxes(g.plan()), new_ref, mu.shape) <= 1e-6
+    g.close()
