@@ -16,6 +16,11 @@
  * Conventions shared by every entry point:
  *  - Return value: DD_OK (0) or a negative DD_ERR_* code; dd_strerror() names it.
  *  - Pointers are HOST pointers; the library copies inputs in and outputs out.
+ *    With DD_FLAG_DEVICE_PTRS in dd_options.flags, the array arguments of
+ *    dd_init (mu, nu), dd_set_plan (hdr, data), dd_get_plan (hdr, data) and
+ *    dd_get_duals (alpha, hdr, beta) are instead CUDA device pointers on the
+ *    context's device (copies ordered on the context's stream); every other
+ *    entry point keeps host pointers unless its comment says otherwise.
  *    Outputs are caller-allocated. Where an entry point takes a `size_t* count`,
  *    passing NULL for the data pointer only stores the required element count.
  *  - Arrays are row-major. Pixel (p, q) has flat index p * N2 + q; basic cell
@@ -80,6 +85,9 @@ extern "C" {
                                       every solve (predicted change of the dual),
                                       not only before solves without a previous
                                       dual                                        */
+#define DD_FLAG_DEVICE_PTRS 32 /* the arrays of dd_init, dd_set_plan, dd_get_plan
+                                  and dd_get_duals are device pointers (see the
+                                  conventions above)                              */
 
 typedef struct dd_grid {
     int32_t N1, N2; /* pixels per axis                                          */

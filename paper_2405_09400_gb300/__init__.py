@@ -26,7 +26,7 @@ DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
 DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
 DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
-DD_FLAG_MLP_EVERY_SOLVE = 16
+DD_FLAG_MLP_EVERY_SOLVE, DD_FLAG_DEVICE_PTRS = 16, 32
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 DD_STATIC_MAX_PIXELS, DD_STATIC_MAX_CELLS = 1024 * 1024, 65536
 
@@ -200,6 +200,57 @@ def dd_init(mu, nu, eps, cell_size, h=None, options=None, stream=None):
     _check(lib.dd_init(_ptr(mu, _f64p), _ptr(nu, _f64p), C.byref(g), float(eps), int(cell_size), C.byref(opt),
                        stream, C.byref(ctx)), "dd_init")
     return ctx
+
+
+def dd_init_device(mu_t, nu_t, eps, cell_size, h=None, options=None, stream=None):
+    """dd_init with DD_FLAG_DEVICE_PTRS: mu_t, nu_t are (N1, N2) float64 CUDA tensors
+    (their device addresses are passed; the flag is added to the options)."""
+    lib = load()
+    opt = options if options is not None else default_options()
+    opt.flags |= DD_FLAG_DEVICE_PTRS
+    N1, N2 = int(mu_t.shape[0]), int(mu_t.shape[1])
+    g = dd_grid(N1, N2, 1.0 / N1 if h is None else h)
+    ctx = C.c_void_p()
+    _check(lib.dd_init(C.cast(C.c_void_p(mu_t.data_ptr()), _f64p), C.cast(C.c_void_p(nu_t.data_ptr()), _f64p),
+                       C.byref(g), float(eps), int(cell_size), C.byref(opt),
+                       stream if stream is not None else current_stream(), C.byref(ctx)), "dd_init")
+    return ctx
+
+
+def dd_set_plan_device(ctx, hdr_t, data_t):
+    """dd_set_plan on a DD_FLAG_DEVICE_PTRS context: int32 / float64 CUDA tensors."""
+    _check(load().dd_set_plan(ctx, C.cast(C.c_void_p(hdr_t.data_ptr()), _i32p),
+                              C.cast(C.c_void_p(data_t.data_ptr()), _f64p), int(data_t.numel())), "dd_set_plan")
+
+
+def dd_get_plan_device(ctx, nbasic):
+    """dd_get_plan on a DD_FLAG_DEVICE_PTRS context: (hdr, data) as CUDA tensors."""
+    import torch
+
+    cnt = C.c_size_t(0)
+    lib = load()
+    hdr = torch.empty((nbasic, 4), dtype=torch.int32, device="cuda")
+    _check(lib.dd_get_plan(ctx, C.cast(C.c_void_p(hdr.data_ptr()), _i32p), None, C.byref(cnt)), "dd_get_plan")
+    data = torch.empty(max(1, cnt.value), dtype=torch.float64, device="cuda")
+    _check(lib.dd_get_plan(ctx, C.cast(C.c_void_p(hdr.data_ptr()), _i32p), C.cast(C.c_void_p(data.data_ptr()), _f64p),
+                           C.byref(cnt)), "dd_get_plan")
+    return hdr, data[:cnt.value]
+
+
+def dd_get_duals_device(ctx, part, shape, ncell):
+    """dd_get_duals on a DD_FLAG_DEVICE_PTRS context: (alpha, hdr, beta) as CUDA tensors."""
+    import torch
+
+    cnt = C.c_size_t(0)
+    lib = load()
+    hdr = torch.empty((ncell, 4), dtype=torch.int32, device="cuda")
+    hp = C.cast(C.c_void_p(hdr.data_ptr()), _i32p)
+    _check(lib.dd_get_duals(ctx, int(part), None, hp, None, C.byref(cnt)), "dd_get_duals")
+    alpha = torch.empty(shape, dtype=torch.float64, device="cuda")
+    beta = torch.empty(max(1, cnt.value), dtype=torch.float64, device="cuda")
+    _check(lib.dd_get_duals(ctx, int(part), C.cast(C.c_void_p(alpha.data_ptr()), _f64p), hp,
+                            C.cast(C.c_void_p(beta.data_ptr()), _f64p), C.byref(cnt)), "dd_get_duals")
+    return alpha, hdr, beta[:cnt.value]
 
 
 def dd_set_eps(ctx, eps):

@@ -161,7 +161,8 @@ int ensure_plan64(dd_ctx* c, size_t n) {
 // there into the pool that is not current; with `validate` the device checks
 // the plan in FP64 (entries finite and >= 0, |nu_i| = m_i and sum_i nu_i = nu
 // within plan_tol, L1). The packed plan becomes the state only if it passes.
-int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n, bool validate) {
+int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n, bool validate,
+                bool data_on_device = false) {
     std::vector<int32_t> bh;
     std::vector<long long> soff;
     size_t total = 0;
@@ -169,7 +170,11 @@ int upload_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n, boo
     const int dst = 1 - c->cur;
     RET(ensure_plan64(c, n));
     RET(ensure_floats(c, &c->pool[dst], &c->pool_cap[dst], total));
-    RET(h2d(c->d_plan64, data, n, c->stream));
+    if (data_on_device) {
+        if (n) CK(cudaMemcpyAsync(c->d_plan64, data, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        RET(h2d(c->d_plan64, data, n, c->stream));
+    }
     RET(h2d(c->d_soff, soff.data(), soff.size(), c->stream));
     RET(h2d(c->bhdr[dst], bh.data(), bh.size(), c->stream));
     CK(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 3, c->stream));
@@ -329,6 +334,20 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     if (N1 <= 0 || N2 <= 0 || !(grid->h > 0) || !(eps > 0) || s <= 0 || N1 % s || N2 % s) return DD_ERR_ARG;
     if ((N1 / s) % 2 || (N2 / s) % 2 || 2 * s > 16) return DD_ERR_ARG;
     const size_t np = (size_t)N1 * N2;
+    // DD_FLAG_DEVICE_PTRS: mu and nu are device arrays; the library keeps host
+    // copies of both (checks, basic masses, statistics), so copy them in first
+    std::vector<double> mu_h, nu_h;
+    if (opt && (opt->flags & DD_FLAG_DEVICE_PTRS)) {
+        cudaStream_t st = (cudaStream_t)stream;
+        mu_h.resize(np);
+        nu_h.resize(np);
+        cudaError_t e = cudaMemcpyAsync(mu_h.data(), mu, sizeof(double) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(nu_h.data(), nu, sizeof(double) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return dd_record_cuda_error(e, "dd_init: device inputs");
+        mu = mu_h.data();
+        nu = nu_h.data();
+    }
     // compensated (Neumaier) sums: a plain running sum over a megapixel grid is
     // off by ~1e-11 and would reject correctly normalised measures
     double smu = 0, snu = 0, cmu = 0, cnu = 0;
@@ -570,6 +589,12 @@ fail:
 
 int dd_set_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     if (!c || !hdr || (!data && n)) return DD_ERR_ARG;
+    if (c->opt.flags & DD_FLAG_DEVICE_PTRS) {  // headers are laid out on the host
+        std::vector<int32_t> hh(4 * (size_t)c->nb);
+        CK(cudaMemcpyAsync(hh.data(), hdr, sizeof(int32_t) * hh.size(), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return upload_plan(c, hh.data(), data, n, true, true);
+    }
     return upload_plan(c, hdr, data, n, true);
 }
 
@@ -1291,9 +1316,18 @@ int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
         n += (size_t)bh[BH_N * i + BH_H] * bh[BH_N * i + BH_W];
     }
     soff[nb] = (long long)n;
-    if (hdr)
+    const bool devp = (c->opt.flags & DD_FLAG_DEVICE_PTRS) != 0;
+    if (hdr) {
+        std::vector<int32_t> hh(4 * (size_t)nb);
         for (int i = 0; i < nb; ++i)
-            for (int k = 0; k < 4; ++k) hdr[4 * i + k] = bh[BH_N * i + k];
+            for (int k = 0; k < 4; ++k) hh[4 * i + k] = bh[BH_N * i + k];
+        if (devp) {
+            RET(h2d(hdr, hh.data(), hh.size(), c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        } else {
+            std::memcpy(hdr, hh.data(), sizeof(int32_t) * hh.size());
+        }
+    }
     if (!data) { *count = n; return DD_OK; }
     if (*count < n) return DD_ERR_ARG;
     // unpack on the device (FP32 pool rows -> packed FP64) and copy out once
@@ -1301,7 +1335,11 @@ int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
     RET(h2d(c->d_soff, soff.data(), soff.size(), c->stream));
     RET(launch_unpack_plan(c));
     c->n_launch += 1;
-    RET(d2h(data, c->d_plan64, n, c->stream));
+    if (devp) {
+        if (n) CK(cudaMemcpyAsync(data, c->d_plan64, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        RET(d2h(data, c->d_plan64, n, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     c->n_d2h += (long long)(sizeof(double) * n + sizeof(int32_t) * bh.size());
     *count = n;
@@ -1355,8 +1393,34 @@ int dd_get_composite(dd_ctx* c, int part, int32_t* hdr, double* data, size_t* co
     return DD_OK;
 }
 
+static int get_duals_host(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta, size_t* count);
+
 int dd_get_duals(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta, size_t* count) {
     if (!c || !count || part < 0 || part > 1) return DD_ERR_ARG;
+    if (!(c->opt.flags & DD_FLAG_DEVICE_PTRS)) return get_duals_host(c, part, alpha, hdr, beta, count);
+    // device outputs: the gauge conversion runs on the host, the results are copied in once
+    const size_t np = (size_t)c->N1 * c->N2;
+    std::vector<int32_t> hh(4 * (size_t)c->part[part].ncell);
+    size_t n = 0;
+    RET(get_duals_host(c, part, nullptr, hh.data(), nullptr, &n));
+    if (hdr) RET(h2d(hdr, hh.data(), hh.size(), c->stream));
+    if (!alpha && !beta) {
+        CK(cudaStreamSynchronize(c->stream));
+        *count = n;
+        return DD_OK;
+    }
+    if (beta && *count < n) return DD_ERR_ARG;
+    std::vector<double> ah(alpha ? np : 0), bh(beta ? n : 0);
+    size_t n2 = n;
+    RET(get_duals_host(c, part, alpha ? ah.data() : nullptr, nullptr, beta ? bh.data() : nullptr, &n2));
+    if (alpha) RET(h2d(alpha, ah.data(), np, c->stream));
+    if (beta) RET(h2d(beta, bh.data(), n, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = n;
+    return DD_OK;
+}
+
+static int get_duals_host(dd_ctx* c, int part, double* alpha, int32_t* hdr, double* beta, size_t* count) {
     DevPart& P = c->part[part];
     if (!P.solved) return DD_ERR_STATE;
     std::vector<int32_t> ch, xb((size_t)XB_N * P.ncell);
