@@ -353,7 +353,7 @@ int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
 /*
  * Autotuner: times every candidate configuration (threads of the small class
  * 64 / 128 / 256 and of the large class 256 / 512, the small-class limit, then
- * clusters of 2 or 4 CTAs for 16, 32 or 48 cells on the two fastest) on the
+ * clusters of 2 or 4 CTAs for 4, 8, 16, 32 or 48 cells on the two fastest) on the
  * context's current state, both partitions, every cell solved to the
  * context's tolerance from the current warm start (restored before each trial
  * and after the last, so every configuration does the same solves and the
@@ -367,8 +367,9 @@ int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
 int dd_autotune(dd_ctx* ctx, const char* cache_path, dd_tuning* out);
 
 /* With DD_FLAG_TRACE: the timeline of the last solve of every cell of `part`,
- * ncell x 4 int64 (HOST): start and end of the solve (ns, the GPU's global
- * timer), the SM it ran on, its CTA size. */
+ * ncell x 8 int64 (HOST): start and end of the solve (ns, the GPU's global
+ * timer), the SM it ran on, its CTA size (x cluster size), the end of the
+ * gather of nu_J, the start and the end of the Sinkhorn iterations, 0. */
 int dd_get_trace(dd_ctx* ctx, int part, int64_t* trace);
 
 /*

@@ -402,9 +402,10 @@ def dd_get_graph_counters(ctx):
 
 
 def dd_get_trace(ctx, part, ncell):
-    """Per-cell solve timeline of the last half-iteration on `part`: (ncell, 4)
-    int64 (start ns, end ns, SM, CTA size)."""
-    t = np.zeros((ncell, 4), dtype=np.int64)
+    """Per-cell solve timeline of the last half-iteration on `part`: (ncell, 8)
+    int64 (start ns, end ns, SM, CTA size, end of the gather, start and end of the
+    Sinkhorn iterations, 0)."""
+    t = np.zeros((ncell, 8), dtype=np.int64)
     _check(load().dd_get_trace(ctx, int(part), _ptr(t, P(C.c_int64))), "dd_get_trace")
     return t
 

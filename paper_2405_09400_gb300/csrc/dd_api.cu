@@ -499,8 +499,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
         if (c->opt.flags & DD_FLAG_TRACE)
             for (int p = 0; p < 2; ++p) {
-                TRY(dmalloc(&c->d_trace[p], 4 * (size_t)c->part[p].ncell));
-                if (cudaMemsetAsync(c->d_trace[p], 0, 4 * sizeof(long long) * c->part[p].ncell, c->stream) != cudaSuccess) {
+                TRY(dmalloc(&c->d_trace[p], 8 * (size_t)c->part[p].ncell));
+                if (cudaMemsetAsync(c->d_trace[p], 0, 8 * sizeof(long long) * c->part[p].ncell, c->stream) != cudaSuccess) {
                     rc = DD_ERR_CUDA;
                     goto fail;
                 }
@@ -1542,7 +1542,7 @@ int dd_debug_cell(dd_ctx* c, int part, int J, float* a, float* b, float* gauge, 
 int dd_get_trace(dd_ctx* c, int part, int64_t* trace) {
     if (!c || !trace || part < 0 || part > 1) return DD_ERR_ARG;
     if (!(c->opt.flags & DD_FLAG_TRACE)) return DD_ERR_STATE;
-    RET(d2h(reinterpret_cast<long long*>(trace), c->d_trace[part], 4 * (size_t)c->part[part].ncell, c->stream));
+    RET(d2h(reinterpret_cast<long long*>(trace), c->d_trace[part], 8 * (size_t)c->part[part].ncell, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DD_OK;
 }

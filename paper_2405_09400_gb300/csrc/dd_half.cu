@@ -506,73 +506,100 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
         cnt = head = 0;
         prev = false;
     }
-    __syncwarp();
-    auto store_state = [&](int c, int hd, bool pv) {
-        if (lane == 0) S.ctl[8] = c | (hd << 4) | ((pv ? 1 : 0) << 8);
-    };
     float* const dG = S.aa;
     float* const dX = dG + m * amax;
     float* const gp = dX + m * amax;
     float* const xp = gp + amax;
     float* const Mg = xp + amax;  // kAAMax x kAAMax
+    const int q = prev ? min(cnt + 1, m) : cnt;
+    const int head_next = prev ? (head + 1 == m ? 0 : head + 1) : head;
+    // the new difference column, the stored iterate / residual, and this lane's
+    // parts of the new Gram row <dG_head, dG_j> and of the right-hand side <dG_j, g>
+    float v[2 * kAAMax];
+#pragma unroll
+    for (int j = 0; j < 2 * kAAMax; ++j) v[j] = 0.f;
     for (int u = lane; u < nx; u += 32) {
         const bool live = S.lgm[u] > 0.5f * DD_NEG;
         const float g = live ? aN[u] - aC[u] : 0.f;
         const float x = live ? aC[u] : 0.f;
+        float gn = 0.f;
         if (prev) {
-            dG[head * amax + u] = g - gp[u];
+            gn = g - gp[u];
+            dG[head * amax + u] = gn;
             dX[head * amax + u] = x - xp[u];
         }
         gp[u] = g;
         xp[u] = x;
-    }
-    __syncwarp();
-    const int q = prev ? min(cnt + 1, m) : cnt;
-    const int head_next = prev ? (head + 1 == m ? 0 : head + 1) : head;
-    if (q == 0) {  // the plain update stays in aN
-        store_state(0, 0, true);
-        return;
-    }
-    float pm[kAAMax], pr[kAAMax];
-#pragma unroll
-    for (int j = 0; j < kAAMax; ++j) pm[j] = pr[j] = 0.f;
-    for (int u = lane; u < nx; u += 32) {
         const float w = S.muxf[u] * wnorm;
-        const float g = gp[u];
-        const float gn = prev ? dG[head * amax + u] : 0.f;
 #pragma unroll
         for (int j = 0; j < kAAMax; ++j) {
             if (j < q) {
-                const float dj = w * dG[j * amax + u];
-                pm[j] += dj * gn;
-                pr[j] += dj * g;
+                const float dj = w * dG[j * amax + u];  // own writes: visible to this lane
+                v[j] += dj * gn;
+                v[kAAMax + j] += dj * g;
             }
         }
     }
+    if (q == 0) {  // the plain update stays in aN
+        if (lane == 0) S.ctl[8] = (1 << 8);
+        return;
+    }
+    // sum the 8 values over the warp: halve the values per lane at each of the
+    // first three steps (lane bit 16, 8, 4), then two plain butterfly steps; lane
+    // l ends with the total of value ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
+    {
+        const bool b = lane & 16;
 #pragma unroll
-    for (int j = 0; j < kAAMax; ++j) {
-        for (int o = 16; o > 0; o >>= 1) {
-            pm[j] += __shfl_xor_sync(0xffffffffu, pm[j], o);
-            pr[j] += __shfl_xor_sync(0xffffffffu, pr[j], o);
+        for (int i = 0; i < 4; ++i) {
+            const float send = b ? v[i] : v[i + 4];
+            const float keep = b ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
     }
-    if (prev && lane == 0) {
+    {
+        const bool b = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = b ? v[i] : v[i + 2];
+            const float keep = b ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool b = lane & 4;
+        const float send = b ? v[0] : v[1];
+        const float keep = b ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    float pm[kAAMax], pr[kAAMax];
+#pragma unroll
+    for (int k = 0; k < 2 * kAAMax; ++k) {
+        const float t = __shfl_sync(0xffffffffu, v[0], ((k >> 2) & 1) * 16 + ((k >> 1) & 1) * 8 + (k & 1) * 4);
+        if (k < kAAMax) pm[k] = t;
+        else pr[k - kAAMax] = t;
+    }
+    // Gram matrix: the stored entries, with the new row / column of `head`
+    float L[kAAMax][kAAMax];
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < kAAMax; ++i) {
+#pragma unroll
+        for (int j = 0; j < kAAMax; ++j) {
+            float e = 0.f;
+            if (i < q && j < q) e = (prev && i == head) ? pm[j] : (prev && j == head) ? pm[i] : Mg[i * kAAMax + j];
+            L[i][j] = e;
+        }
+        if (i < q) tr += L[i][i];
+    }
+    if (prev && lane == 0) {  // keep the new row for the next iterations (read after a block barrier)
 #pragma unroll
         for (int j = 0; j < kAAMax; ++j)
             if (j < q) {
                 Mg[head * kAAMax + j] = pm[j];
                 Mg[j * kAAMax + head] = pm[j];
             }
-    }
-    __syncwarp();
-    // Cholesky of M + lam I (q x q, lower factor L in registers), every lane alike
-    float L[kAAMax][kAAMax];
-    float tr = 0.f;
-#pragma unroll
-    for (int i = 0; i < kAAMax; ++i) {
-#pragma unroll
-        for (int j = 0; j < kAAMax; ++j) L[i][j] = (i < q && j < q) ? Mg[i * kAAMax + j] : 0.f;
-        if (i < q) tr += L[i][i];
     }
     // Tikhonov term: relative to the Gram trace, and at least the squared FP32
     // resolution of the dual differences (8e-6 in base-2 units), so that
@@ -592,11 +619,11 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
 #pragma unroll
             for (int i = 0; i < kAAMax; ++i) {
                 if (i > j && i < q) {
-                    float v = L[i][j];
+                    float t = L[i][j];
 #pragma unroll
                     for (int k = 0; k < kAAMax; ++k)
-                        if (k < j) v -= L[i][k] * L[j][k];
-                    L[i][j] = v / dj;
+                        if (k < j) t -= L[i][k] * L[j][k];
+                    L[i][j] = t / dj;
                 }
             }
         }
@@ -604,30 +631,30 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
     float gam[kAAMax];
 #pragma unroll
     for (int i = 0; i < kAAMax; ++i) {  // L y = r
-        float v = pr[i];
+        float t = pr[i];
 #pragma unroll
         for (int k = 0; k < kAAMax; ++k)
-            if (k < i) v -= L[i][k] * gam[k];
-        gam[i] = i < q ? v / L[i][i] : 0.f;
+            if (k < i) t -= L[i][k] * gam[k];
+        gam[i] = i < q ? t / L[i][i] : 0.f;
     }
 #pragma unroll
     for (int i = kAAMax - 1; i >= 0; --i) {  // L^T gamma = y
         if (i < q) {
-            float v = gam[i];
+            float t = gam[i];
 #pragma unroll
             for (int k = 0; k < kAAMax; ++k)
-                if (k > i && k < q) v -= L[k][i] * gam[k];
-            gam[i] = v / L[i][i];
+                if (k > i && k < q) t -= L[k][i] * gam[k];
+            gam[i] = t / L[i][i];
         }
     }
     float gs = 0.f;
 #pragma unroll
     for (int j = 0; j < kAAMax; ++j) gs += fabsf(gam[j]);
     if (!ok || !(gs <= 1e3f)) {  // keep the plain update; restart the history
-        store_state(0, 0, false);
+        if (lane == 0) S.ctl[8] = 0;
         return;
     }
-    store_state(q, head_next, true);
+    if (lane == 0) S.ctl[8] = q | (head_next << 4) | (1 << 8);
     for (int u = lane; u < nx; u += 32) {
         if (!(S.lgm[u] > 0.5f * DD_NEG)) continue;
         float xn = xp[u] + gp[u];
@@ -677,7 +704,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         }
         if (t >= ncell) break;
         const int J = A.order[t];
-        unsigned long long t_start = 0;
+        unsigned long long t_start = 0, t_gather = 0, t_loop0 = 0, t_loop1 = 0;
         if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int32_t* xb = A.xblk + XB_N * J;
         const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
@@ -723,19 +750,27 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // per-thread partial sums in FP32 (a few entries each), block sum in FP64;
         // they only choose the change of gauge, which is exact for any value
         float gf[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // member boxes relative to the composite box (registers, read once)
+        int mo1[4], mo2[4], mh[4], mw[4], mst[4];
+        long long mstart[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mh[k] = 0; mw[k] = 0; mo1[k] = 0; mo2[k] = 0; mst[k] = 0; mstart[k] = 0;
+            if (mem[k] < 0) continue;
+            const int32_t* bh = A.bhdr_in + BH_N * mem[k];
+            mo1[k] = bh[BH_O1] - o1; mo2[k] = bh[BH_O2] - o2; mh[k] = bh[BH_H]; mw[k] = bh[BH_W];
+            mst[k] = bh[BH_STRIDE]; mstart[k] = bh[BH_START];
+        }
         for (int v = rlo * bs + tid; v < rhi * bs; v += NT) {
             const int v1 = v / bs, v2 = v - v1 * bs;
             float lg = DD_NEG;
             if (v2 < w) {
-                const int y1 = o1 + v1, y2 = o2 + v2;
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    if (mem[k] < 0) continue;
-                    const int32_t* bh = A.bhdr_in + BH_N * mem[k];
-                    const int p1 = y1 - bh[BH_O1], p2 = y2 - bh[BH_O2];
-                    if (p1 >= 0 && p1 < bh[BH_H] && p2 >= 0 && p2 < bh[BH_W])
-                        acc += A.pool_in[(long long)bh[BH_START] + (long long)p1 * bh[BH_STRIDE] + p2];
+                    const int p1 = v1 - mo1[k], p2 = v2 - mo2[k];
+                    if (p1 >= 0 && p1 < mh[k] && p2 >= 0 && p2 < mw[k])
+                        acc += A.pool_in[mstart[k] + (long long)p1 * mst[k] + p2];
                 }
                 A.comp_nu[comp + (long long)v1 * stride + v2] = acc;
                 if (acc > 0.f) lg = lg2f(acc);
@@ -758,6 +793,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) gm[k] = gf[k];
         block_sum_d<12>(gm, S.red);
+        if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_gather));
         if constexpr (CL > 1) {  // nu_J moments over all rows (the mu moments are complete in every CTA)
             double nv[6] = {gm[0], gm[1], gm[2], gm[3], gm[4], gm[10]};
             cluster_sum_d<6>(nv, S.clx, 0);
@@ -768,18 +804,34 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // per-axis stretch l_k absorbed so that the kernel
         //   k2 (sqrt(l_k) ubar_k - vbar_k / sqrt(l_k))^2
         // is small along the cell's local map; keeps the FP32 duals small.
-        const float uc1 = (float)(gm[6] / gm[5]), uc2 = (float)(gm[7] / gm[5]);
-        const float vc1 = (float)(gm[1] / gm[0]), vc2 = (float)(gm[2] / gm[0]);
-        const double vu1 = fmax(gm[8] / gm[5] - (double)uc1 * uc1, 0.0), vu2 = fmax(gm[9] / gm[5] - (double)uc2 * uc2, 0.0);
-        const double vv1 = fmax(gm[3] / gm[0] - (double)vc1 * vc1, 0.0), vv2 = fmax(gm[4] / gm[0] - (double)vc2 * vc2, 0.0);
-        const float l1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
-        const float l2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
+        // The scalars are computed in FP64 by one warp and shared through shared
+        // memory: at GB300's FP64 rate the same divisions and square roots in
+        // every thread of a 512-thread CTA would cost microseconds per solve.
+        // The affine start (and the learned one) use the full 2 x 2 map (q), needed
+        // only where a solve starts from it or writes training targets.
+        const bool need_q = (A.affine && !A.warm) || (A.pred && nx == kMlpBlock) || A.targ;
+        if (wid == 0) {
+            const double duc1 = gm[6] / gm[5], duc2 = gm[7] / gm[5];
+            const double dvc1 = gm[1] / gm[0], dvc2 = gm[2] / gm[0];
+            const float fuc1 = (float)duc1, fuc2 = (float)duc2, fvc1 = (float)dvc1, fvc2 = (float)dvc2;
+            const double vu1 = fmax(gm[8] / gm[5] - (double)fuc1 * fuc1, 0.0), vu2 = fmax(gm[9] / gm[5] - (double)fuc2 * fuc2, 0.0);
+            const double vv1 = fmax(gm[3] / gm[0] - (double)fvc1 * fvc1, 0.0), vv2 = fmax(gm[4] / gm[0] - (double)fvc2 * fvc2, 0.0);
+            const float fl1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
+            const float fl2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
+            float fq11 = 0.f, fq12 = 0.f, fq22 = 0.f;
+            if (need_q)
+                affine_excess(vu1, gm[11] / gm[5] - (double)fuc1 * fuc2, vu2, vv1, gm[10] / gm[0] - (double)fvc1 * fvc2,
+                              vv2, fl1, fl2, fq11, fq12, fq22);
+            if (lane == 0) {
+                S.coef[0] = fuc1; S.coef[1] = fuc2; S.coef[2] = fvc1; S.coef[3] = fvc2;
+                S.coef[4] = fl1; S.coef[5] = fl2; S.coef[6] = fq11; S.coef[7] = fq12; S.coef[8] = fq22;
+            }
+        }
+        __syncthreads();
+        const float uc1 = S.coef[0], uc2 = S.coef[1], vc1 = S.coef[2], vc2 = S.coef[3];
+        const float l1 = S.coef[4], l2 = S.coef[5];
+        const float q11 = S.coef[6], q12 = S.coef[7], q22 = S.coef[8];
         const float d1 = (float)(r0 - o1) + uc1 - vc1, d2 = (float)(c0 - o2) + uc2 - vc2;
-        // the affine start (and the learned one) use the full 2 x 2 map
-        float q11 = 0.f, q12 = 0.f, q22 = 0.f;
-        if (A.affine || A.targ)
-            affine_excess(vu1, gm[11] / gm[5] - (double)uc1 * uc2, vu2, vv1, gm[10] / gm[0] - (double)vc1 * vc2, vv2,
-                          l1, l2, q11, q12, q22);
         // Kernel tables (see build_tables), at the coarsest level of the optional
         // eps-scaling: eps_L = eps f^L, the cost in base-2 units k2 / f^L.
         const bool scaling = A.eps_levels > 0 && A.fixed_iters <= 0;
@@ -882,6 +934,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         int lp2 = 0, lpx = 0;
         while ((1 << lp2) < P2) ++lp2;
         while ((1 << lpx) < PX) ++lpx;
+        if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_loop0));
         while (true) {
             ++it;
             // Y-update stage 1: T(u1, v2) = LSE_u2 [a(u1, u2) - K2(u2, v2)]
@@ -1297,6 +1350,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             aN = tmp;
         }
         __syncthreads();  // every thread has read the error partials in S.red
+        if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_loop1));
         if (A.fixed_iters <= 0 && err > tolm && tid == 0 && lead) atomicAdd(&A.status[stalled ? 3 : 0], 1);
         if constexpr (CL == 1)
             if (A.targ && nx == kMlpBlock) write_targets(A, S, J, aC, h, w, bs, hx, wx, gm[5], uc1, uc2, q11, q12, q22);
@@ -1359,11 +1413,15 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 unsigned smid;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
                 asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-                long long* tr = A.trace + 4LL * J;
+                long long* tr = A.trace + 8LL * J;
                 tr[0] = (long long)t_start;
                 tr[1] = (long long)t_end;
                 tr[2] = (long long)smid;
                 tr[3] = (long long)blockDim.x * CL;
+                tr[4] = (long long)t_gather;
+                tr[5] = (long long)t_loop0;
+                tr[6] = (long long)t_loop1;
+                tr[7] = 0;
             }
             A.err[J] = err;
             A.Ecell[J] = A.eps * eloc[0];

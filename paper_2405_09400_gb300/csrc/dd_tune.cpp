@@ -245,7 +245,7 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
               [](const std::pair<double, dd_tuning>& a, const std::pair<double, dd_tuning>& b) { return a.first < b.first; });
     for (size_t b = 0; b < std::min<size_t>(2, one_cta.size()); ++b) {
         for (int cls : {2, 4}) {
-            for (int cells : {16, 32, 48}) {
+            for (int cells : {4, 8, 16, 32, 48}) {
                 if (r != DD_OK) break;
                 if (c->opt.flags & DD_FLAG_COLLECT) break;  // training targets: one-CTA solves only
                 dd_tuning t = one_cta[b].second;

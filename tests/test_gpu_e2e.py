@@ -285,14 +285,18 @@ def test_autotune_restores_state_and_caches(dd, tmp_path):
 
 def test_trace_records_every_cell(dd):
     """DD_FLAG_TRACE: every cell of the last half-iteration has a start <= end
-    inside the half-iteration's span, a valid SM index and its CTA size."""
+    inside the half-iteration's span, a valid SM index, its CTA size, and the
+    phase stamps in order (start <= gather end <= iterations start <= iterations
+    end <= end)."""
     mu, nu, eps, p = synth.workload("dd32", 0, N=64)
     g = dd.DomDec(mu, nu, eps, 4, tol=1e-5, flags=dd.DD_FLAG_TRACE)
     g.iterate(0)
     st = g.iterate(1)
     tr = g.trace(1)
-    assert tr.shape == (g.ncell[1], 4)
+    assert tr.shape == (g.ncell[1], 8)
     assert (tr[:, 0] > 0).all() and (tr[:, 1] >= tr[:, 0]).all()
+    assert (tr[:, 4] >= tr[:, 0]).all() and (tr[:, 5] >= tr[:, 4]).all()
+    assert (tr[:, 6] >= tr[:, 5]).all() and (tr[:, 1] >= tr[:, 6]).all()
     assert (tr[:, 1].max() - tr[:, 0].min()) * 1e-6 <= st["ms_total"] + 1.0
     assert ((tr[:, 2] >= 0) & (tr[:, 2] < 1024)).all()
     assert set(np.unique(tr[:, 3])) <= {128, 256, 512, 512 * 2, 512 * 4, 256 * 2, 256 * 4}
