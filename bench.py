@@ -46,7 +46,7 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # below (profiles/dd256_step_kernels.md); reported only when the autotuner picks
 # that configuration and the kernels are unchanged since the capture
 TRAFFIC_CELL_REGION = 18.75e6
-TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1)
+TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, sm_reserve=0)
 # cell solver of every arm: Anderson acceleration of the X-dual iteration
 # (memory 4; same fixed point, same stop; with it, eps-scaling inside each solve
 # no longer pays and is off)
@@ -143,7 +143,8 @@ def _arm(dd, mu, nu, eps, p, boxes, warm, weights, args, flush, stream, tune=Non
     g = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=warm, weights=weights,
                   flags=flags, **SOLVER)
     if tune is not None:
-        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"],
+                     tune.get("sm_reserve", 0))
     # the first hybrid iteration from the initial coupling (cold solves for the
     # plain arm): part of the warm-up, reported on its own
     torch.cuda.synchronize()
@@ -220,9 +221,9 @@ def run_ours(args):
     tune = None
     if args.tuning:
         t = [int(x) for x in args.tuning.split(",")]
-        t += [1, 0][len(t) - 5:] if len(t) < 7 else []
-        tune = dict(threads=t[:3], small_area=t[3], small_side=t[4], cl_size=t[5], cl_cells=t[6], ms_default=None,
-                    ms_best=None, trials=0)
+        t += [1, 0, 0][len(t) - 5:] if len(t) < 8 else []
+        tune = dict(threads=t[:3], small_area=t[3], small_side=t[4], cl_size=t[5], cl_cells=t[6], sm_reserve=t[7],
+                    ms_default=None, ms_best=None, trials=0)
     elif not args.no_tune:
         tctx = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
                          weights=weights, **SOLVER)
@@ -274,14 +275,16 @@ def run_ours(args):
     if not args.no_micro:
         gm = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_PREV,
                        **SOLVER)
-        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"],
+                     tune.get("sm_reserve", 0))
         gm.step(args.warmup, stats=False)
         hdr_m, data_m = dd.dd_get_plan(gm.ctx, gm.nbasic)
         gm.close()
         K = 100
         gm = dd.DomDec(mu, nu, eps, p["s"], boxes=(hdr_m, data_m), fixed_iters=K, plan_tol=1e-5, warm=dd.DD_WARM_COLD,
                        flags=dd.DD_FLAG_NO_GRAPH)
-        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        gm.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"],
+                     tune.get("sm_reserve", 0))
         gm.iterate(0)  # warm-up (sizes, allocation)
         rs = []
         for part in (0, 1, 0, 1):
@@ -302,7 +305,8 @@ def run_ours(args):
     if not args.no_e2e:
         ge2 = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, plan_tol=1e-5,
                         warm=dd.DD_WARM_MLP, weights=weights, **SOLVER)
-        ge2.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        ge2.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"],
+                     tune.get("sm_reserve", 0))
         for _ in range(args.warmup):
             ge2.step(1, stats=False)
         hdr, data = dd.dd_get_plan(ge2.ctx, ge2.nbasic)
@@ -547,7 +551,8 @@ def time_to_tolerance(dd, mu, nu, eps, p, boxes, weights, tune, stream, n_ref=12
     def make(warm):
         g = dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=warm,
                       weights=weights if warm == dd.DD_WARM_MLP else None, **SOLVER)
-        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"])
+        g.set_tuning(tune["threads"], tune["small_area"], tune["small_side"], tune["cl_size"], tune["cl_cells"],
+                     tune.get("sm_reserve", 0))
         return g
 
     ref = make(dd.DD_WARM_PREV)
@@ -701,7 +706,7 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the end-to-end time-to-tolerance runs")
     ap.add_argument("--no-configs", action="store_true", help="skip the 512 x 512 and 1024 x 1024 configurations")
     ap.add_argument("--tuning", default="", help="fixed launch configuration t0,t1,t2,small_area,small_side"
-                                               "[,cl_size,cl_cells] instead of autotuning (profiling runs)")
+                                               "[,cl_size,cl_cells[,sm_reserve]] instead of autotuning (profiling runs)")
     ap.add_argument("--arms", default="plain,warm,affine,eager",
                     help="comma list of arms to time besides the learned warm start (plain, affine, eager)")
     args = ap.parse_args()

@@ -343,17 +343,23 @@ typedef struct dd_tuning {
                           (and at most #SMs / cl_size): whole quarter-octave
                           buckets of the work key h w (previous iterations), from
                           the top, boxes of at least 1024 entries                */
+    int32_t sm_reserve; /* the persistent grid of the large-box class has at most
+                           (#SMs - sm_reserve) x (CTAs per SM) CTAs, so that the
+                           small-box class starts on the reserved SMs at once (a
+                           512-thread large-box CTA holds a whole SM's registers);
+                           0 = off, < #SMs                                        */
 } dd_tuning;
 
 /* Defaults: threads {256, 128, 256}, small_area 1536, small_side 64, clusters
-   off. */
+   off, sm_reserve 0. */
 int dd_get_tuning(dd_ctx* ctx, dd_tuning* t);
 int dd_set_tuning(dd_ctx* ctx, const dd_tuning* t);
 
 /*
  * Autotuner: times every candidate configuration (threads of the small class
  * 64 / 128 / 256 and of the large class 256 / 512, the small-class limit, then
- * clusters of 2 or 4 CTAs for 4, 8, 16, 32 or 48 cells on the two fastest) on the
+ * clusters of 2 or 4 CTAs for 4, 8, 16, 32 or 48 cells on the two fastest, and
+ * 8, 16 or 32 SMs reserved for the small-box class on the fastest) on the
  * context's current state, both partitions, every cell solved to the
  * context's tolerance from the current warm start (restored before each trial
  * and after the last, so every configuration does the same solves and the

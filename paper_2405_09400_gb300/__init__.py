@@ -76,12 +76,12 @@ class dd_flow_stats(C.Structure):
 class dd_tuning(C.Structure):
     _fields_ = [("threads", C.c_int32 * 3), ("small_area", C.c_int32), ("small_side", C.c_int32),
                 ("ms_default", C.c_double), ("ms_best", C.c_double), ("trials", C.c_int32),
-                ("cl_size", C.c_int32), ("cl_cells", C.c_int32)]
+                ("cl_size", C.c_int32), ("cl_cells", C.c_int32), ("sm_reserve", C.c_int32)]
 
     def as_dict(self):
         return dict(threads=list(self.threads), small_area=self.small_area, small_side=self.small_side,
                     ms_default=self.ms_default, ms_best=self.ms_best, trials=self.trials, cl_size=self.cl_size,
-                    cl_cells=self.cl_cells)
+                    cl_cells=self.cl_cells, sm_reserve=self.sm_reserve)
 
 
 class DDError(RuntimeError):
@@ -416,9 +416,9 @@ def dd_get_tuning(ctx):
     return t.as_dict()
 
 
-def dd_set_tuning(ctx, threads, small_area, small_side, cl_size=None, cl_cells=None):
-    """Launch configuration of the cell kernels; cl_size / cl_cells None keep the
-    context's current cluster setting."""
+def dd_set_tuning(ctx, threads, small_area, small_side, cl_size=None, cl_cells=None, sm_reserve=None):
+    """Launch configuration of the cell kernels; cl_size / cl_cells / sm_reserve
+    None keep the context's current setting."""
     t = dd_tuning()
     _check(load().dd_get_tuning(ctx, C.byref(t)), "dd_get_tuning")
     t.threads = (C.c_int32 * 3)(*threads)
@@ -427,6 +427,8 @@ def dd_set_tuning(ctx, threads, small_area, small_side, cl_size=None, cl_cells=N
         t.cl_size = int(cl_size)
     if cl_cells is not None:
         t.cl_cells = int(cl_cells)
+    if sm_reserve is not None:
+        t.sm_reserve = int(sm_reserve)
     _check(load().dd_set_tuning(ctx, C.byref(t)), "dd_set_tuning")
 
 
@@ -651,8 +653,8 @@ class DomDec:
     def trace(self, part):
         return dd_get_trace(self.ctx, part, self.ncell[part])
 
-    def set_tuning(self, threads, small_area, small_side, cl_size=None, cl_cells=None):
-        dd_set_tuning(self.ctx, threads, small_area, small_side, cl_size, cl_cells)
+    def set_tuning(self, threads, small_area, small_side, cl_size=None, cl_cells=None, sm_reserve=None):
+        dd_set_tuning(self.ctx, threads, small_area, small_side, cl_size, cl_cells, sm_reserve)
 
     def autotune(self, cache_path=None):
         return dd_autotune(self.ctx, cache_path)

@@ -366,7 +366,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
     if (opt) c->opt = *opt; else dd_default_options(&c->opt);
     c->tune.threads[0] = 256; c->tune.threads[1] = 128; c->tune.threads[2] = 256;
     c->tune.small_area = 1536; c->tune.small_side = 64;
-    c->tune.cl_size = 1; c->tune.cl_cells = 0;
+    c->tune.cl_size = 1; c->tune.cl_cells = 0; c->tune.sm_reserve = 0;
     const bool learned = c->opt.warm == DD_WARM_MLP || (c->opt.flags & DD_FLAG_COLLECT);
     if (!(c->opt.tol >= 0) || c->opt.max_iter <= 0 || !(c->opt.trunc >= 0) || !(c->opt.omega < 2.0) ||
         (c->opt.omega >= 0.0 && c->opt.omega < 1.0) || c->opt.warm < DD_WARM_PREV || c->opt.warm > DD_WARM_MLP ||
@@ -845,7 +845,14 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         if (cls_cells[k].empty()) continue;
         const int n = (int)cls_cells[k].size();
         int occ = std::max(1, half_occupancy(thr_c[k], smem_c[k]));
-        int grid = std::max(1, std::min(n, c->nsm * occ));
+        // the large-box classes leave sm_reserve SMs, and the SMs of the cluster
+        // class, to a concurrent small-box class
+        const int ncl_sm = cls_cells[3].empty() ? 0
+                           : std::max(1, std::min((int)cls_cells[3].size(), c->nsm / half_cluster_size(c->tune.cl_size))) *
+                                 half_cluster_size(c->tune.cl_size);
+        const int sms = (k != 1 && side_used && c->tune.sm_reserve > 0)
+                            ? std::max(1, c->nsm - c->tune.sm_reserve - ncl_sm) : c->nsm;
+        int grid = std::max(1, std::min(n, sms * occ));
         cudaStream_t st = !side_used ? c->stream : (k != 1 ? c->side : c->side3);
         // the global-scratch class keeps no box array in shared memory: its carve
         // must see area 0, as its shared-memory size was computed with area 0
@@ -1048,7 +1055,10 @@ int graph_prepare(dd_ctx* c) {
     const int* thr = c->tune.threads;
     for (int k = 0; k < 2; ++k) {
         const int occ = std::max(1, half_occupancy(thr[k], g.smem[k]));
-        g.grid[k] = c->nsm * occ;
+        // the large-box class leaves sm_reserve SMs, and the SMs of the cluster
+        // class, to the small-box class
+        const int used = c->tune.sm_reserve > 0 ? c->tune.sm_reserve + g.cl_cap * half_cluster_size(c->tune.cl_size) : 0;
+        g.grid[k] = (k == 0 ? std::max(1, c->nsm - used) : c->nsm) * occ;
     }
 
     // full persistent grids: the class sizes vary between iterations, CTAs that

@@ -109,9 +109,9 @@ bool cache_lookup(const char* path, const std::string& key, dd_tuning* t) {
         if (std::strncmp(line, key.c_str(), k) != 0 || line[k] != ' ') continue;
         dd_tuning x{};
         if (std::sscanf(line + k,
-                        " threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d ms_default=%lf ms_best=%lf",
+                        " threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d reserve=%d ms_default=%lf ms_best=%lf",
                         &x.threads[0], &x.threads[1], &x.threads[2], &x.small_area, &x.small_side, &x.cl_size,
-                        &x.cl_cells, &x.ms_default, &x.ms_best) == 9) {
+                        &x.cl_cells, &x.sm_reserve, &x.ms_default, &x.ms_best) == 10) {
             *t = x;
             found = true;  // the last entry for the key wins
         }
@@ -123,9 +123,10 @@ bool cache_lookup(const char* path, const std::string& key, dd_tuning* t) {
 void cache_store(const char* path, const std::string& key, const dd_tuning& t) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d ms_default=%.4f ms_best=%.4f\n",
+    std::fprintf(f, "%s threads=%d,%d,%d small_area=%d small_side=%d cluster=%d,%d reserve=%d ms_default=%.4f "
+                 "ms_best=%.4f\n",
                  key.c_str(), t.threads[0], t.threads[1], t.threads[2], t.small_area, t.small_side, t.cl_size,
-                 t.cl_cells, t.ms_default, t.ms_best);
+                 t.cl_cells, t.sm_reserve, t.ms_default, t.ms_best);
     std::fclose(f);
 }
 
@@ -173,6 +174,7 @@ int dd_set_tuning(dd_ctx* c, const dd_tuning* t) {
         if (!valid_threads(t->threads[k])) return DD_ERR_ARG;
     if (t->small_area < 16 || t->small_side < 4 || t->small_side > 256) return DD_ERR_ARG;
     if (!(t->cl_size == 1 || t->cl_size == 2 || t->cl_size == 4) || t->cl_cells < 0) return DD_ERR_ARG;
+    if (t->sm_reserve < 0 || t->sm_reserve >= c->nsm) return DD_ERR_ARG;
     if (half_smem_bytes(c, t->small_area, t->small_side, t->small_side) > (size_t)half_kernel_max_smem())
         return DD_ERR_ARG;
     c->tune = *t;
@@ -220,6 +222,7 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
                 t.small_side = sd[1];
                 t.cl_size = 1;
                 t.cl_cells = 0;
+                t.sm_reserve = 0;
                 if (std::memcmp(t.threads, defaults.threads, sizeof(t.threads)) == 0 &&
                     t.small_area == defaults.small_area && t.small_side == defaults.small_side &&
                     defaults.cl_size == 1)
@@ -260,6 +263,25 @@ int dd_autotune(dd_ctx* c, const char* cache_path, dd_tuning* out) {
                         best_ms = ms;
                         best = t;
                     }
+                }
+            }
+        }
+    }
+    // then SMs reserved for the small-box class at launch, on the fastest so far
+    if (r == DD_OK && !(c->opt.flags & DD_FLAG_COLLECT)) {
+        const dd_tuning base = best;
+        for (int res : {8, 16, 32}) {
+            if (r != DD_OK || res >= c->nsm) break;
+            dd_tuning t = base;
+            t.sm_reserve = res;
+            double ms = 0.0;
+            r = trial(c, t, saved, &ms);
+            ++n;
+            if (r == DD_OK) {
+                clustered.push_back({ms, t});
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
                 }
             }
         }
