@@ -88,6 +88,17 @@ extern "C" {
 #define DD_FLAG_DEVICE_PTRS 32 /* the arrays of dd_init, dd_set_plan, dd_get_plan
                                   and dd_get_duals are device pointers (see the
                                   conventions above)                              */
+#define DD_FLAG_FUSED_C2B 64 /* CompositeToBasic, balancing and truncation
+                                (Alg. 1, Def. 3.4) of a cell by the CTA that
+                                solved it, right after the solve (one-CTA
+                                solves whose arrays fit the solve's freed
+                                shared memory; the others after all solves, as
+                                by default, in a kernel of their own). The same
+                                arithmetic, its partial sums over another CTA
+                                size. Off by default: on the 256 x 256 bench
+                                the persistent large-box grid then holds the
+                                SMs longer and the small boxes finish later,
+                                so a half-iteration took as long as without  */
 
 typedef struct dd_grid {
     int32_t N1, N2; /* pixels per axis                                          */
@@ -375,7 +386,8 @@ int dd_autotune(dd_ctx* ctx, const char* cache_path, dd_tuning* out);
 /* With DD_FLAG_TRACE: the timeline of the last solve of every cell of `part`,
  * ncell x 8 int64 (HOST): start and end of the solve (ns, the GPU's global
  * timer), the SM it ran on, its CTA size (x cluster size), the end of the
- * gather of nu_J, the start and the end of the Sinkhorn iterations, 0. */
+ * gather of nu_J, the start and the end of the Sinkhorn iterations, and the end
+ * of the cell's CompositeToBasic when its solving CTA did it (else 0). */
 int dd_get_trace(dd_ctx* ctx, int part, int64_t* trace);
 
 /*

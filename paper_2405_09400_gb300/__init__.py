@@ -26,7 +26,7 @@ DD_ERR_STALL, DD_ERR_FLOW, DD_ERR_POOL, DD_ERR_STATE = -5, -6, -7, -8
 DD_INIT_PRODUCT, DD_INIT_USER = 0, 1
 DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
 DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
-DD_FLAG_MLP_EVERY_SOLVE, DD_FLAG_DEVICE_PTRS = 16, 32
+DD_FLAG_MLP_EVERY_SOLVE, DD_FLAG_DEVICE_PTRS, DD_FLAG_FUSED_C2B = 16, 32, 64
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
 DD_STATIC_MAX_PIXELS, DD_STATIC_MAX_CELLS = 1024 * 1024, 65536
 

@@ -298,7 +298,7 @@ void dd_destroy(dd_ctx* c) {
         dfree(c->pool[p]); dfree(c->bhdr[p]);
     }
     dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
-    dfree(c->d_gscr); dfree(c->d_goff); dfree(c->d_guard);
+    dfree(c->d_gscr); dfree(c->d_goff); dfree(c->d_guard); dfree(c->d_fused);
     for (int p = 0; p < 2; ++p) { dfree(c->d_corder[p]); dfree(c->d_ccount[p]); }
     if (c->h_guard) cudaFreeHost(c->h_guard);
     for (auto& e : c->gev)
@@ -497,6 +497,12 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         if (cudaMemsetAsync(c->d_guard, 0, 4 * sizeof(int), c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         if (cudaMallocHost((void**)&c->h_guard, 4 * sizeof(int)) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
         TRY(dmalloc(&c->d_goff, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        TRY(dmalloc(&c->d_fused, (size_t)std::max(c->part[0].ncell, c->part[1].ncell)));
+        if (cudaMemsetAsync(c->d_fused, 0, sizeof(int) * std::max(c->part[0].ncell, c->part[1].ncell), c->stream) !=
+            cudaSuccess) {
+            rc = DD_ERR_CUDA;
+            goto fail;
+        }
         if (c->opt.flags & DD_FLAG_TRACE)
             for (int p = 0; p < 2; ++p) {
                 TRY(dmalloc(&c->d_trace[p], 8 * (size_t)c->part[p].ncell));
@@ -674,6 +680,7 @@ static int cluster_cap(dd_ctx* c) {
 
 int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     DevPart& P = c->part[part];
+    c->fuse_c2b = with_c2b;  // without k_c2b after them the solves must not mark cells done
     CK(cudaEventRecord(c->ev[0], c->stream));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
@@ -1078,6 +1085,7 @@ int graph_prepare(dd_ctx* c) {
 
 int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     DevPart& P = c->part[part];
+    c->fuse_c2b = true;
     const auto& g = c->gcap;
     c->status_slot = stage;
     cudaEvent_t* ev = c->gev + 3 * (stage - 1);

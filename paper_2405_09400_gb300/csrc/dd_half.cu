@@ -72,25 +72,73 @@ constexpr double kLn2d = 0.69314718055994530942;
 
 // ---------------------------------------------------------------------------
 // block reductions
+//
+// Sums over a CTA in fixed order. Across the lanes of a warp a value travels as
+// an unevaluated sum of two floats (hi + lo, combined by Knuth's error-free
+// two-sum: about 48 significant bits), and only the per-warp results are added
+// in FP64, by one lane per value: GB300 runs FP64 at 1/64 of the FP32 rate
+// shared by the SM, so an FP64 shuffle tree in every warp of every resident CTA
+// cost tens of microseconds per cell.
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+    const float s = h + bh;
+    const float bb = s - h;
+    const float e = ((h - (s - bb)) + (bh - bb)) + (l + bl);  // two-sum error + the low parts
+    h = s + e;
+    l = e - (h - s);
+}
+
 template <int N>
-__device__ void block_sum_d(double (&v)[N], double* sh /* >= 32*N */) {
+__device__ void block_sum_ff(float (&hi)[N], float (&lo)[N], double (&out)[N], double* sh /* >= 33*N */) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float* shf = reinterpret_cast<float*>(sh);  // [warp][value][hi, lo] in sh[0, 32 N)
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        double x = v[k];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[wid * N + k] = x;
+        float h = hi[k], l = lo[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h, o);
+            const float ol = __shfl_down_sync(0xffffffffu, l, o);
+            ff_add(h, l, oh, ol);
+        }
+        if (lane == 0) {
+            shf[2 * (wid * N + k)] = h;
+            shf[2 * (wid * N + k) + 1] = l;
+        }
     }
     __syncthreads();
     if (threadIdx.x < N) {
         double x = 0.0;
-        for (int w = 0; w < nw; ++w) x += sh[w * N + threadIdx.x];
+        for (int w = 0; w < nw; ++w)
+            x += (double)shf[2 * (w * N + threadIdx.x)] + (double)shf[2 * (w * N + threadIdx.x) + 1];
         sh[32 * N + threadIdx.x] = x;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = sh[32 * N + k];
+    for (int k = 0; k < N; ++k) out[k] = sh[32 * N + k];
     __syncthreads();
+}
+
+// block sum of per-thread FP32 partials, totals in FP64 (valid in every thread)
+template <int N>
+__device__ void block_sum_f(const float (&v)[N], double (&out)[N], double* sh) {
+    float h[N], l[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        h[k] = v[k];
+        l[k] = 0.f;
+    }
+    block_sum_ff<N>(h, l, out, sh);
+}
+
+// block sum of per-thread FP64 values (each split into hi + lo floats first)
+template <int N>
+__device__ void block_sum_d(double (&v)[N], double* sh) {
+    float h[N], l[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        h[k] = (float)v[k];
+        l[k] = (float)(v[k] - (double)h[k]);
+    }
+    block_sum_ff<N>(h, l, v, sh);
 }
 
 // exclusive scan over a block of long long (blockDim.x <= 1024)
@@ -238,6 +286,9 @@ struct HalfArgs {
     float* targ;        // ncell x DD_MLP_NOUT training targets written after the solve, or null
     // Anderson acceleration of the X-dual iteration (tolerance mode): memory, 0 = off
     int aa_m;
+    // per cell: 1 once its solving CTA has also done CompositeToBasic (k_sink sets,
+    // k_c2b skips such a cell and clears the mark), or null: k_sink leaves it to k_c2b
+    int* fused;
     // gluing edge candidates: per basic cell and pixel, mass r and mean displacement
     // d (2) of the Gibbs cell plan (nb x s^2 x 3, FP64), or null (product candidates)
     double* pmom;
@@ -665,6 +716,25 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
     }
 }
 
+// Shared-memory arrays of CompositeToBasic (floats unless noted).
+struct C2bSmem {
+    double* red;  // 33 x 16 doubles (block sums)
+    float* T;     // T2 and M2: 2 x (wx / s) x hx x w
+    float* tab1;  // hx x h: axis-1 kernel of the solve's gauge
+    float* tab2;  // wx x padw(w): axis-2 kernel
+    float* L;     // gluing candidates (pmom): h x wx log2 row sums over v2
+    float* E;     // and the means of v2 under them (h x wx)
+    float* coef;  // 16
+    int* ctl;     // 32 (uses [4, 20))
+};
+
+// floats of C2bSmem::T, L and E that one cell needs
+__host__ __device__ __forceinline__ long long c2b_cell_floats(int s, int hx, int wx, int h, int w, bool pmom) {
+    return 2LL * (wx / s) * hx * w + (pmom ? 2LL * h * wx : 0);
+}
+
+__device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float* aC);
+
 // The cell solver. CL = 1: one CTA per cell. CL > 1: the CL CTAs of a thread-block
 // cluster solve one cell together (for the few largest cells, which would
 // otherwise run alone on one SM for most of the half-iteration): rank r owns the
@@ -790,9 +860,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             gf[11] += mux * f1 * f2;
         }
         double gm[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) gm[k] = gf[k];
-        block_sum_d<12>(gm, S.red);
+        block_sum_f<12>(gf, gm, S.red);
         if (A.trace && tid == 0 && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_gather));
         if constexpr (CL > 1) {  // nu_J moments over all rows (the mu moments are complete in every CTA)
             double nv[6] = {gm[0], gm[1], gm[2], gm[3], gm[4], gm[10]};
@@ -1426,6 +1494,33 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             A.err[J] = err;
             A.Ecell[J] = A.eps * eloc[0];
         }
+        // DD_FLAG_FUSED_C2B: CompositeToBasic of this cell right away (one-CTA
+        // solves), its arrays T2, M2 (and L, E) in the box arrays and stage-1
+        // buffers of the solve, which are dead after the outputs above; k_c2b
+        // takes the cells that do not fit
+        if constexpr (CL == 1) {
+            if (A.fused && c2b_cell_floats(A.s, hx, wx, h, w, A.pmom != nullptr) <= (long long)(S.tab1 - S.lgnu)) {
+                __syncthreads();  // outputs and gauge written, partials read
+                C2bSmem C;
+                C.red = S.red;
+                C.T = S.lgnu;
+                C.tab1 = S.tab1;
+                C.tab2 = S.tab2;
+                C.L = S.lgnu + 2LL * (wx / A.s) * hx * w;
+                C.E = C.L + (long long)h * wx;
+                C.coef = S.coef;
+                C.ctl = S.ctl;
+                c2b_cell(A, J, C, aC);
+                if (tid == 0) {
+                    A.fused[J] = 1;
+                    if (A.trace) {
+                        unsigned long long t_c2b;
+                        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_c2b));
+                        A.trace[8LL * J + 7] = (long long)t_c2b;
+                    }
+                }
+            }
+        }
     }
     if constexpr (CL > 1) cg::this_cluster().sync();  // no CTA leaves while others read its shared memory
 }
@@ -1665,12 +1760,17 @@ __global__ void k_collect(int n, const int32_t* __restrict__ idx, const uint4* _
 // CompositeToBasic, D_i, balancing, truncation and compaction of one composite
 // cell per CTA, from the duals k_sink left in global memory (alpha, b~ not
 // needed: the member shares are ratios of partial sums over X).
-__global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
-    extern __shared__ __align__(16) char smem_raw[];
-    if (A.guard && *A.guard) return;
+constexpr int kC2bThreads = 256;  // k_c2b CTA size (3 per SM: 80 registers)
+constexpr int kC2bBatch = 8;      // compaction strides per barrier pair
+
+// CompositeToBasic, D_i, balancing, truncation and compaction of composite cell
+// J by all threads of the calling CTA, from its X dual aC (shared memory) and
+// the change of gauge of its solve (A.gauge, read after a block barrier). The
+// member shares are ratios of partial sums over X, so the Y dual is not needed.
+// Every return is uniform over the CTA.
+__device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float* aC) {
     const int tid = threadIdx.x, NT = blockDim.x;
     const int s = A.s;
-    const int J = blockIdx.x;
     const int32_t* xb = A.xblk + XB_N * J;
     const int r0 = xb[XB_R0], c0 = xb[XB_C0], hx = xb[XB_HX], wx = xb[XB_WX], nmem = xb[XB_NMEM];
     const int32_t* ch = A.chdr + CH_N * J;
@@ -1688,34 +1788,6 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     int32_t mem[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) mem[k] = A.members[4 * J + k];
-    // shared memory
-    const int s2 = 2 * s, BS = padw(A.smaxW);
-    double* dsm = reinterpret_cast<double*>(smem_raw);
-    struct {
-        double* red;
-        float* T;
-        float* tab1;
-        float* tab2;
-        float* a;
-        float* L;  // gluing candidates: per (v1, u2) log2 of the row sum over v2, and
-        float* E;  // the mean of v2 under it (h x 2s each)
-        float* coef;
-        int* ctl;
-    } S;
-    S.red = dsm;
-    float* f = reinterpret_cast<float*>(dsm + 32 * 16 + 16);
-    S.T = f; f += 4 * s2 * BS;
-    S.tab1 = f; f += A.smaxH * s2;
-    S.tab2 = f; f += BS * s2;
-    S.a = f; f += A.amax;
-    S.L = f; f += A.pmom ? A.smaxH * s2 : 0;
-    S.E = f; f += A.pmom ? A.smaxH * s2 : 0;
-    S.coef = f; f += 16;
-    S.ctl = reinterpret_cast<int*>(f);
-    if (reinterpret_cast<char*>(f + 32) - smem_raw > (long long)dyn_smem_bytes()) {
-        if (tid == 0) atomicAdd(&A.status[2], 1);
-        return;
-    }
     // the change of gauge of this cell's solve, and its kernel tables
     const float* gg = A.gauge + 8 * J;
     const float l1 = gg[2], l2 = gg[3], uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
@@ -1739,9 +1811,6 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
             S.tab2[u2 * bs + v2] = kl * D * (D + w0f);
         }
     }
-    const float* ap = A.alpha + (long long)A.amax * J;
-    for (int u = tid; u < nx; u += NT) S.a[u] = ap[u];
-    float* aC = S.a;
     __syncthreads();
 
     // ---- per-pixel moments of the cell plan (gluing candidates) ------------
@@ -1804,7 +1873,7 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     //     M2 = mean of (x2 - y2)^2 under that partial distribution.
     const int ncg = wx / s, nrg = hx / s;
     float* T2 = S.T;
-    float* M2 = S.T + 2 * (2 * s) * padw(A.smaxW);
+    float* M2 = S.T + (long long)ncg * hx * w;
     for (int q = tid; q < ncg * hx * w; q += NT) {
         const int cg = q / (hx * w), rem = q - cg * hx * w;
         const int u1 = rem / w, v2 = rem - u1 * w;
@@ -1826,10 +1895,18 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     //   nu_i(v) = nu_J(v) * sum_{u in X_i} pi(u, v) / sum_u pi(u, v),
     // and the mean squared displacement E_i(v) under pi(., v) restricted to X_i.
     float accm[4] = {0.f, 0.f, 0.f, 0.f}, accd[4] = {0.f, 0.f, 0.f, 0.f};
+    // nu_J of the thread's next entry is loaded one entry ahead (its latency
+    // overlaps the shared-memory work of the current one)
+    auto nu_at = [&](int v) {
+        const int v1 = v / w;
+        return v < nA ? A.comp_nu[comp + (long long)v1 * stride + (v - v1 * w)] : 0.f;
+    };
+    float nuv_next = nu_at(tid);
     for (int v = tid; v < nA; v += NT) {
         const int v1 = v / w, v2 = v - v1 * w;
         const float* tb = S.tab1 + v1;
-        const float nuv = A.comp_nu[comp + (long long)v1 * stride + v2];
+        const float nuv = nuv_next;
+        nuv_next = nu_at(v + NT);
         float num[4] = {0.f, 0.f, 0.f, 0.f}, ew[4] = {0.f, 0.f, 0.f, 0.f};  // ew: sum_u pi(u, v) E_i(v)
         if (nuv > 0.f) {
             float mx = DD_NEG;
@@ -1869,10 +1946,11 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
             accd[k] += ew[k];
         }
     }
-    double red8[8];
+    float red8f[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { red8[k] = accm[k]; red8[4 + k] = accd[k]; }
-    block_sum_d<8>(red8, S.red);
+    for (int k = 0; k < 4; ++k) { red8f[k] = accm[k]; red8f[4 + k] = accd[k]; }
+    double red8[8];
+    block_sum_f<8>(red8f, red8, S.red);
     (void)nrg;
 
     // ---- 4. balancing coefficients (member order walk) -------------------
@@ -1935,12 +2013,23 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) momf[k] = 0.f;
+    // the member values of the thread's next entry are loaded one entry ahead
+    // (an entry's values are only read and written by its own thread)
+    auto vals_at = [&](int v, float (&x)[4]) {
+        const int v1 = v / w;
+        const long long off = slot0 + (long long)v1 * stride + (v - v1 * w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = (v < nA && k < nmem) ? A.pool_out[off + k * area] : 0.f;
+    };
+    float vnext[4];
+    vals_at(tid, vnext);
     for (int v = tid; v < nA; v += NT) {
         const int v1 = v / w, v2 = v - v1 * w;
         const long long off = slot0 + (long long)v1 * stride + v2;
         float vals[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) vals[k] = (k < nmem) ? A.pool_out[off + k * area] : 0.f;
+        for (int k = 0; k < 4; ++k) vals[k] = vnext[k];
+        vals_at(v + NT, vnext);
         if (A.pre) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -1974,9 +2063,7 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
         atomicMax(&S.ctl[4 + 4 * k + 3], bb[k][3]);
     }
     double mom[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) mom[k] = momf[k];
-    block_sum_d<16>(mom, S.red);  // contains __syncthreads
+    block_sum_f<16>(momf, mom, S.red);  // contains __syncthreads
 
     // ---- compaction in place (dst index never exceeds src index) --------
     // Each member is rescaled to its basic mass m_i after truncation, so that
@@ -1991,15 +2078,25 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
         const float fsc = msum > 0.0 ? (float)(A.m[mem[k]] / msum) : 1.f;
         float* sl = A.pool_out + slot0 + k * area;
         const int n = hh * st;
-        for (int base = 0; base < n; base += NT) {
-            const int dI = base + tid;
-            float val = 0.f;
-            if (dI < n) {
-                const int rr = dI / st, cc = dI - rr * st;
-                if (cc < ww) val = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
+        // kC2bBatch strides of NT entries per barrier pair: every read of a batch
+        // precedes its writes, and later batches read only beyond its last write
+        for (int base = 0; base < n; base += kC2bBatch * NT) {
+            float val[kC2bBatch];
+#pragma unroll
+            for (int j = 0; j < kC2bBatch; ++j) {
+                const int dI = base + j * NT + tid;
+                val[j] = 0.f;
+                if (dI < n) {
+                    const int rr = dI / st, cc = dI - rr * st;
+                    if (cc < ww) val[j] = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
+                }
             }
             __syncthreads();
-            if (dI < n) sl[dI] = val;
+#pragma unroll
+            for (int j = 0; j < kC2bBatch; ++j) {
+                const int dI = base + j * NT + tid;
+                if (dI < n) sl[dI] = val[j];
+            }
             __syncthreads();
         }
         if (tid == 0) {
@@ -2020,7 +2117,58 @@ __global__ void __launch_bounds__(128) k_c2b(HalfArgs A) {
             bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
         }
     }
-    
+}
+
+__global__ void __launch_bounds__(kC2bThreads, 3) k_c2b(HalfArgs A) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int J = blockIdx.x;
+    // cells whose solving CTA already did this (k_sink with A.fused): clear the
+    // mark for the next half-iteration and leave
+    if (A.fused) {
+        const int done = A.fused[J];
+        __syncthreads();  // every thread has read the mark before it is cleared
+        if (done) {
+            if (threadIdx.x == 0) A.fused[J] = 0;
+            return;
+        }
+    }
+    if (A.guard && *A.guard) return;
+    const int tid = threadIdx.x;
+    // shared memory
+    const int s = A.s, s2 = 2 * s, BS = padw(A.smaxW);
+    double* dsm = reinterpret_cast<double*>(smem_raw);
+    struct {
+        double* red;
+        float* T;
+        float* tab1;
+        float* tab2;
+        float* a;
+        float* L;  // gluing candidates: per (v1, u2) log2 of the row sum over v2, and
+        float* E;  // the mean of v2 under it (h x 2s each)
+        float* coef;
+        int* ctl;
+    } S;
+    S.red = dsm;
+    float* f = reinterpret_cast<float*>(dsm + 32 * 16 + 16);
+    S.T = f; f += 4 * s2 * BS;
+    S.tab1 = f; f += A.smaxH * s2;
+    S.tab2 = f; f += BS * s2;
+    S.a = f; f += A.amax;
+    S.L = f; f += A.pmom ? A.smaxH * s2 : 0;
+    S.E = f; f += A.pmom ? A.smaxH * s2 : 0;
+    S.coef = f; f += 16;
+    S.ctl = reinterpret_cast<int*>(f);
+    if (reinterpret_cast<char*>(f + 32) - smem_raw > (long long)dyn_smem_bytes()) {
+        if (tid == 0) atomicAdd(&A.status[2], 1);
+        return;
+    }
+    const int32_t* xb = A.xblk + XB_N * J;
+    const int nx = xb[XB_HX] * xb[XB_WX];
+    const float* ap = A.alpha + (long long)A.amax * J;
+    for (int u = tid; u < nx; u += blockDim.x) S.a[u] = ap[u];
+    C2bSmem C;
+    C.red = S.red; C.T = S.T; C.tab1 = S.tab1; C.tab2 = S.tab2; C.L = S.L; C.E = S.E; C.coef = S.coef; C.ctl = S.ctl;
+    c2b_cell(A, J, C, S.a);
 }
 
 }  // namespace
@@ -2182,6 +2330,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.count = nullptr;
     A.trace = (c->opt.flags & DD_FLAG_TRACE) ? c->d_trace[part] : nullptr;
     A.aa_m = c->opt.fixed_iters > 0 ? 0 : c->opt.anderson;
+    A.fused = (c->fuse_c2b && (c->opt.flags & DD_FLAG_FUSED_C2B)) ? c->d_fused : nullptr;
     A.pmom = c->opt.eps_gamma > 0.0 ? c->d_pmom : nullptr;
     A.eps_levels = c->opt.eps_levels;
     A.eps_factor = (float)c->opt.eps_factor;
@@ -2296,7 +2445,8 @@ int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem) {
     A.smaxA = (int)dims[0];
     A.smaxH = (int)dims[1];
     A.smaxW = (int)dims[2];
-    k_c2b<<<c->part[part].ncell, 128, smem, c->stream>>>(A);
+    A.fused = c->d_fused;  // skips (and clears) the cells done by their solving CTAs
+    k_c2b<<<c->part[part].ncell, kC2bThreads, smem, c->stream>>>(A);
     return launch_status(__func__);
 }
 

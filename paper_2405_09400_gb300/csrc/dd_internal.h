@@ -162,6 +162,8 @@ struct dd_ctx {
     int status_slot = 0;             // d_status slice of the running stage (0 eager, 1 A, 2 B)
     cudaStream_t gstream = nullptr;  // capture stream (the legacy stream cannot be captured)
     int* d_guard = nullptr;          // [0]: 0, or the stage (1 A, 2 B, 3 flow) that would overflow a buffer
+    int* d_fused = nullptr;          // per cell: CompositeToBasic done by its solving CTA (cleared by k_c2b)
+    bool fuse_c2b = false;           // the cell launches being issued are followed by k_c2b
     int* h_guard = nullptr;          // pinned copy (read by the flow host node and after a replay)
     int32_t* d_corder[2] = {nullptr, nullptr};  // per partition: class-grouped order, 3 x ncell
     int* d_ccount[2] = {nullptr, nullptr};      // per partition: cells per class

@@ -119,6 +119,50 @@ def _state(g):
     return [(o1, o2, a.copy()) for o1, o2, a in g.plan()]
 
 
+@pytest.mark.parametrize("threads", [(512, 64, 512), (256, 128, 256)])
+def test_fused_composite_to_basic_matches_separate_kernel(dd, threads):
+    """CompositeToBasic, balancing and truncation (Alg. 1, Def. 3.4) done by each
+    cell's solving CTA right after its solve (DD_FLAG_FUSED_C2B), against the
+    same arithmetic in its own kernel after all solves: a 64 x 64 workload from
+    the KR plan with fixed iterations (identical A duals), A then B. Only the CTA
+    size of the per-thread partial sums differs, so after A the basic boxes agree
+    to FP32 rounding (L1 1e-6 m_i; headers exactly unless an entry sits at the
+    truncation threshold) and D_i to 1e-6 relative; B, solved from A outputs that
+    differ by that rounding, within 1e-5. The trace shows that the solving CTAs
+    did it."""
+    mu, nu, eps, p = synth.workload("dd256", 0, N=64)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    kw = dict(boxes=boxes, fixed_iters=40)
+    f = dd.DomDec(mu, nu, eps, 4, flags=dd.DD_FLAG_FUSED_C2B | dd.DD_FLAG_TRACE, **kw)
+    e = dd.DomDec(mu, nu, eps, 4, flags=dd.DD_FLAG_TRACE, **kw)
+    for g in (f, e):
+        g.set_tuning(list(threads), 768, 48, 1, 0, 0)
+    m = Geometry(64, 64, 4).basic_masses(mu)
+    for part in (0, 1):
+        sf = f.iterate(part)
+        se = e.iterate(part)
+        if part == 0:  # the same solves (B starts from A's outputs, which differ by rounding)
+            assert sf["objective"] == se["objective"]
+        else:
+            assert sf["objective"] == pytest.approx(se["objective"], rel=1e-6)
+        tf = np.asarray(f.trace(part))
+        te = np.asarray(e.trace(part))
+        assert (tf[:, 7] > 0).mean() > 0.9  # done by the solving CTAs
+        assert (te[:, 7] == 0).all()
+        tol = 1e-6 if part == 0 else 1e-5  # B: from A outputs that differ by rounding
+        for i, ((a1, a2, a), (b1, b2, b)) in enumerate(zip(f.plan(), e.plan())):
+            if (a1, a2, a.shape) == (b1, b2, b.shape):
+                assert np.abs(a - b).sum() <= tol * m[i], i
+            else:
+                Af = np.zeros((64, 64)); Af[a1:a1 + a.shape[0], a2:a2 + a.shape[1]] = a
+                Ae = np.zeros((64, 64)); Ae[b1:b1 + b.shape[0], b2:b2 + b.shape[1]] = b
+                assert np.abs(Af - Ae).max() < 2e-15 and np.abs(Af - Ae).sum() <= tol * m[i], i
+        Df, De = f.basic_moments()["D"], e.basic_moments()["D"]
+        assert np.allclose(Df, De, rtol=tol, atol=1e-12)
+    f.close()
+    e.close()
+
+
 @pytest.mark.parametrize("cl", [2, 4])
 def test_cluster_solves_match_oracle(dd, cl):
     """Thread-block clusters (cl CTAs per cell, own box rows per CTA, partial
