@@ -990,8 +990,12 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         int P2 = 1;
         while (P2 * 2 * nx <= NT && P2 < 16) P2 *= 2;
         const int nxl = (rhi - rlo) * wx;  // X-update stage 1 lines of this CTA
+        // lines in full rounds of NT take one lane each; the rest, PX lanes each
+        // (the last round is otherwise a few lines for a few warps while the other
+        // warps wait at the barrier)
+        const int xfull = nxl > NT ? (nxl / NT) * NT : 0;
         int PX = 1;
-        while (PX * 2 * nxl <= NT && PX < 8) PX *= 2;
+        while (PX * 2 * (nxl - xfull) <= NT && PX < 8) PX *= 2;
         const float4* b4 = reinterpret_cast<const float4*>(b_p);
         const float4* t24 = reinterpret_cast<const float4*>(S.tab2);
         const int nq = (w + 3) >> 2;  // float4 groups holding data per row
@@ -1212,10 +1216,13 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             // X-update stage 1: R(v1, u2) = LSE_v2 [b(v1, v2) - K2(u2, v2)], float4 over
             // v2; PX adjacent lanes per line (strided float4 groups), combined by
             // warp shuffles, so that short row ranges (clusters) keep every lane busy
-            for (int base = 0; base < nxl * PX; base += NT) {
+            for (int ph = 0; ph < 2; ++ph) {
+            const int PXc = ph == 0 ? 1 : PX, lpxc = ph == 0 ? 0 : lpx;
+            const int nl = ph == 0 ? xfull : nxl - xfull, l0 = ph == 0 ? 0 : xfull;
+            for (int base = 0; base < nl * PXc; base += NT) {
                 const int q = base + tid;
-                const bool act = q < nxl * PX;
-                const int ql = act ? (q >> lpx) : 0, p = q & (PX - 1);
+                const bool act = q < nl * PXc;
+                const int ql = act ? l0 + (q >> lpxc) : 0, p = q & (PXc - 1);
                 const int line = rlo * wx + ql;
                 const int v1 = line / wx, u2 = line - v1 * wx;
                 const float4* br = b4 + v1 * bq;
@@ -1225,8 +1232,8 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 if (act && !first) {
                     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
                     int g = p;
-                    for (; g + PX < nq; g += 2 * PX) {
-                        const float4 bb = br[g], tt = tr[g], bc = br[g + PX], tc = tr[g + PX];
+                    for (; g + PXc < nq; g += 2 * PXc) {
+                        const float4 bb = br[g], tt = tr[g], bc = br[g + PXc], tc = tr[g + PXc];
                         s0 += ex2f(bb.x - tt.x - m) + ex2f(bb.y - tt.y - m);
                         s1 += ex2f(bb.z - tt.z - m) + ex2f(bb.w - tt.w - m);
                         s2 += ex2f(bc.x - tc.x - m) + ex2f(bc.y - tc.y - m);
@@ -1239,27 +1246,28 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     }
                     sacc = (s0 + s1) + (s2 + s3);
                 }
-                for (int o = 1; o < PX; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                for (int o = 1; o < PXc; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
                 const bool bad = act && (first || !shift_ok(sacc));
                 if (__any_sync(0xffffffffu, bad)) {
                     float mm = DD_NEG;
                     if (act)
-                        for (int g = p; g < nq; g += PX) {
+                        for (int g = p; g < nq; g += PXc) {
                             const float4 bb = br[g], tt = tr[g];
                             mm = fmaxf(fmaxf(fmaxf(mm, bb.x - tt.x), fmaxf(bb.y - tt.y, bb.z - tt.z)), bb.w - tt.w);
                         }
-                    for (int o = 1; o < PX; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+                    for (int o = 1; o < PXc; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
                     float ss = 0.f;
                     if (act)
-                        for (int g = p; g < nq; g += PX) {
+                        for (int g = p; g < nq; g += PXc) {
                             const float4 bb = br[g], tt = tr[g];
                             ss += ex2f(bb.x - tt.x - mm) + ex2f(bb.y - tt.y - mm) + ex2f(bb.z - tt.z - mm) +
                                   ex2f(bb.w - tt.w - mm);
                         }
-                    for (int o = 1; o < PX; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    for (int o = 1; o < PXc; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
                     if (bad) { m = mm; sacc = ss; }
                 }
                 if (act && p == 0) S.R[line] = m + lg2f(sacc);
+            }
             }
             __syncthreads();
             // X-update stage 2: a'(u) = log2 mu(u) - LSE_v1 [R(v1, u2) - K1(u1, v1)],
