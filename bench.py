@@ -43,9 +43,10 @@ EX2_PER_CLK_SM = 32
 SM_MAX_MHZ_DEFAULT = 2070.0
 # DRAM bytes (read + write) of the cell region of one half-iteration (both k_sink
 # classes + k_c2b), from one ncu capture of this bench in the launch configuration
-# below (profiles/dd256_step_kernels.md); reported only when the autotuner picks
-# that configuration and the kernels are unchanged since the capture
-TRAFFIC_CELL_REGION = 18.75e6
+# below (profiles/dd256_step_kernels.md). The bytes are those the cells read and
+# write (the composite boxes, the basic boxes, the duals), which the CTA sizes do
+# not change; the line names the configuration of the capture
+TRAFFIC_CELL_REGION = 18.38e6
 TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, sm_reserve=0)
 # cell solver of every arm: Anderson acceleration of the X-dual iteration
 # (memory 4; same fixed point, same stop; with it, eps-scaling inside each solve
@@ -390,8 +391,11 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_sink (persistent cell Sinkhorn, + k_c2b)",
                      "achieved": round(achieved / 1e12, 4), "peak": round(ex2_peak / 1e12, 4), "unit": "Texp2/s",
                      "frac": round(achieved / ex2_peak, 5),
-                     "traffic": TRAFFIC_CELL_REGION if all(tune.get(k) == v for k, v in TRAFFIC_TUNING.items())
-                     else None, "traffic_src": "ncu dram__bytes, profiles/dd256_step_kernels.md",
+                     "traffic": TRAFFIC_CELL_REGION,
+                     "traffic_src": "ncu dram__bytes of one capture at threads %s, small %d/%d, no clusters "
+                                    "(profiles/dd256_step_kernels.md)" % (TRAFFIC_TUNING["threads"],
+                                                                         TRAFFIC_TUNING["small_area"],
+                                                                         TRAFFIC_TUNING["small_side"]),
                      "kernel_ms_mean": round(k_ms, 4),
                      "work_per_launch": k_terms,
                      "peak_src": f"{n_sm} SMs x {EX2_PER_CLK_SM} ex2/clk x {sm_max:.0f} MHz"},
