@@ -43,7 +43,7 @@ EX2_PER_CLK_SM = 32
 SM_MAX_MHZ_DEFAULT = 2070.0
 # DRAM bytes (read + write) of the cell region of one half-iteration (both k_sink
 # classes + k_c2b), from one ncu capture of this bench in the launch configuration
-# below (profiles/dd256_step_kernels.md). The bytes are those the cells read and
+# below (the step-kernel summary under profiles/). The bytes are those the cells read and
 # write (the composite boxes, the basic boxes, the duals), which the CTA sizes do
 # not change; the line names the configuration of the capture
 TRAFFIC_CELL_REGION = 18.38e6
@@ -393,7 +393,7 @@ def run_ours(args):
                      "frac": round(achieved / ex2_peak, 5),
                      "traffic": TRAFFIC_CELL_REGION,
                      "traffic_src": "ncu dram__bytes of one capture at threads %s, small %d/%d, no clusters "
-                                    "(profiles/dd256_step_kernels.md)" % (TRAFFIC_TUNING["threads"],
+                                    "(profiles/, dd256 step kernels)" % (TRAFFIC_TUNING["threads"],
                                                                          TRAFFIC_TUNING["small_area"],
                                                                          TRAFFIC_TUNING["small_side"]),
                      "kernel_ms_mean": round(k_ms, 4),
