@@ -657,16 +657,20 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
     // columns made of rounding noise get no weight
     const float lam = fmaxf(1e-4f * tr / (float)q, 6.4e-11f);
     bool ok = tr > 0.f && isfinite(tr);
+    // the factor's diagonal is kept as its reciprocal (rsqrt, then products only):
+    // the coefficients are extrapolation weights, a few ulp do not matter, and the
+    // chain of IEEE square roots and divisions is most of the step's latency
+    float rd[kAAMax];
 #pragma unroll
     for (int j = 0; j < kAAMax; ++j) {
+        rd[j] = 0.f;
         if (j < q) {
             float d = L[j][j] + lam;
 #pragma unroll
             for (int k = 0; k < kAAMax; ++k)
                 if (k < j) d -= L[j][k] * L[j][k];
             ok = ok && d > 0.f;
-            const float dj = sqrtf(fmaxf(d, 1e-30f));
-            L[j][j] = dj;
+            rd[j] = rsqrtf(fmaxf(d, 1e-30f));
 #pragma unroll
             for (int i = 0; i < kAAMax; ++i) {
                 if (i > j && i < q) {
@@ -674,7 +678,7 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
 #pragma unroll
                     for (int k = 0; k < kAAMax; ++k)
                         if (k < j) t -= L[i][k] * L[j][k];
-                    L[i][j] = t / dj;
+                    L[i][j] = t * rd[j];
                 }
             }
         }
@@ -686,7 +690,7 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
 #pragma unroll
         for (int k = 0; k < kAAMax; ++k)
             if (k < i) t -= L[i][k] * gam[k];
-        gam[i] = i < q ? t / L[i][i] : 0.f;
+        gam[i] = i < q ? t * rd[i] : 0.f;
     }
 #pragma unroll
     for (int i = kAAMax - 1; i >= 0; --i) {  // L^T gamma = y
@@ -695,7 +699,7 @@ __device__ void anderson_step(const Smem& S, int nx, int amax, int m, float err,
 #pragma unroll
             for (int k = 0; k < kAAMax; ++k)
                 if (k > i && k < q) t -= L[k][i] * gam[k];
-            gam[i] = t / L[i][i];
+            gam[i] = t * rd[i];
         }
     }
     float gs = 0.f;
@@ -1138,19 +1142,26 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                         for (int u1 = 0; u1 < 8; ++u1) kk[u1] = tb[u1 * h];
                         const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
                         const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
-                        float m[4], sa[4];
+                        float m[4], sa[4], sb[4];  // even / odd u1: shorter add chains
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             m[k] = ln[k] > 0.5f * DD_NEG ? ln[k] - bp[k] : 0.f;
                             sa[k] = 0.f;
+                            sb[k] = 0.f;
                         }
 #pragma unroll
-                        for (int u1 = 0; u1 < 8; ++u1) {
+                        for (int u1 = 0; u1 < 8; u1 += 2) {
                             sa[0] += ex2f(T4[u1].x - kk[u1] - m[0]);
                             sa[1] += ex2f(T4[u1].y - kk[u1] - m[1]);
                             sa[2] += ex2f(T4[u1].z - kk[u1] - m[2]);
                             sa[3] += ex2f(T4[u1].w - kk[u1] - m[3]);
+                            sb[0] += ex2f(T4[u1 + 1].x - kk[u1 + 1] - m[0]);
+                            sb[1] += ex2f(T4[u1 + 1].y - kk[u1 + 1] - m[1]);
+                            sb[2] += ex2f(T4[u1 + 1].z - kk[u1 + 1] - m[2]);
+                            sb[3] += ex2f(T4[u1 + 1].w - kk[u1 + 1] - m[3]);
                         }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) sa[k] += sb[k];
                         float out[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
