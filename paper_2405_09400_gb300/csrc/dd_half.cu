@@ -438,8 +438,9 @@ __device__ void affine_excess(double s11, double s12, double s22, double t11, do
 __device__ void build_tables(const Smem& S, double k2d, int h, int w, int bs, int hx, int wx, float uc1, float uc2,
                              float vc1, float vc2, float l1, float l2) {
     const int tid = threadIdx.x, NT = blockDim.x;
+    const double il1 = S.clx[12], il2 = S.clx[13];  // 1 / l1, 1 / l2
     for (int v1 = tid; v1 < h; v1 += NT) {
-        const double tt = (v1 - (double)vc1) / (double)l1;
+        const double tt = (v1 - (double)vc1) * il1;
         const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
         const double w0 = 2.0 * ((us - (double)uc1) - tt);
         S.B1[v1] = 0.25 * k2d * l1 * w0 * w0;
@@ -454,7 +455,7 @@ __device__ void build_tables(const Smem& S, double k2d, int h, int w, int bs, in
             for (int u2 = 0; u2 < wx; ++u2) S.tab2[u2 * bs + v2] = 0.f;
             continue;
         }
-        const double tt = (v2 - (double)vc2) / (double)l2;
+        const double tt = (v2 - (double)vc2) * il2;
         const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
         const double w0 = 2.0 * ((us - (double)uc2) - tt);
         S.B2[v2] = 0.25 * k2d * l2 * w0 * w0;
@@ -883,20 +884,34 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // only where a solve starts from it or writes training targets.
         const bool need_q = (A.affine && !A.warm) || (A.pred && nx == kMlpBlock) || A.targ;
         if (wid == 0) {
-            const double duc1 = gm[6] / gm[5], duc2 = gm[7] / gm[5];
-            const double dvc1 = gm[1] / gm[0], dvc2 = gm[2] / gm[0];
+            // two FP64 reciprocals and products (each FP64 division is a long
+            // sequence at GB300's FP64 rate); the stretch ratio in FP32 (the gauge
+            // is exact for any value)
+            const double i5 = 1.0 / gm[5], i0 = 1.0 / gm[0];
+            const double duc1 = gm[6] * i5, duc2 = gm[7] * i5;
+            const double dvc1 = gm[1] * i0, dvc2 = gm[2] * i0;
             const float fuc1 = (float)duc1, fuc2 = (float)duc2, fvc1 = (float)dvc1, fvc2 = (float)dvc2;
-            const double vu1 = fmax(gm[8] / gm[5] - (double)fuc1 * fuc1, 0.0), vu2 = fmax(gm[9] / gm[5] - (double)fuc2 * fuc2, 0.0);
-            const double vv1 = fmax(gm[3] / gm[0] - (double)fvc1 * fvc1, 0.0), vv2 = fmax(gm[4] / gm[0] - (double)fvc2 * fvc2, 0.0);
-            const float fl1 = (vu1 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv1 / vu1))) : 1.f;
-            const float fl2 = (vu2 > 1e-3) ? (float)fmin(8.0, fmax(0.125, sqrt(vv2 / vu2))) : 1.f;
+            const double vu1 = fmax(gm[8] * i5 - (double)fuc1 * fuc1, 0.0), vu2 = fmax(gm[9] * i5 - (double)fuc2 * fuc2, 0.0);
+            const double vv1 = fmax(gm[3] * i0 - (double)fvc1 * fvc1, 0.0), vv2 = fmax(gm[4] * i0 - (double)fvc2 * fvc2, 0.0);
+            const float fl1 = (vu1 > 1e-3) ? fminf(8.f, fmaxf(0.125f, sqrtf((float)vv1 / (float)vu1))) : 1.f;
+            const float fl2 = (vu2 > 1e-3) ? fminf(8.f, fmaxf(0.125f, sqrtf((float)vv2 / (float)vu2))) : 1.f;
             float fq11 = 0.f, fq12 = 0.f, fq22 = 0.f;
             if (need_q)
-                affine_excess(vu1, gm[11] / gm[5] - (double)fuc1 * fuc2, vu2, vv1, gm[10] / gm[0] - (double)fvc1 * fvc2,
+                affine_excess(vu1, gm[11] * i5 - (double)fuc1 * fuc2, vu2, vv1, gm[10] * i0 - (double)fvc1 * fvc2,
                               vv2, fl1, fl2, fq11, fq12, fq22);
             if (lane == 0) {
                 S.coef[0] = fuc1; S.coef[1] = fuc2; S.coef[2] = fvc1; S.coef[3] = fvc2;
                 S.coef[4] = fl1; S.coef[5] = fl2; S.coef[6] = fq11; S.coef[7] = fq12; S.coef[8] = fq22;
+                S.clx[12] = 1.0 / (double)fl1;  // for the kernel tables
+                S.clx[13] = 1.0 / (double)fl2;
+                S.clx[14] = (double)(float)(1.0 / gm[5]);  // 1 / mu(X_J) (FP32 value)
+                // exact displacement of the float origins (FP64) for the gauge
+                // conversion of the outputs, and its constant term
+                const double x1 = (double)(r0 - o1) + (double)fuc1 - (double)fvc1;
+                const double x2 = (double)(c0 - o2) + (double)fuc2 - (double)fvc2;
+                S.clx[9] = x1;
+                S.clx[10] = x2;
+                S.clx[11] = 0.5 * A.k2d * (x1 * x1 + x2 * x2);
             }
         }
         __syncthreads();
@@ -953,16 +968,18 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             // the duals are defined up to (a + C, b - C): start every solve with
             // a mu-weighted mean of zero, so that no constant accumulates across
             // warm starts and the FP32 values keep their resolution
-            double cm[1] = {0.0};
+            // (FP32: the shift only picks the gauge)
+            float cmf[1] = {0.f};
             for (int u = tid; u < nx; u += NT)
-                if (aC[u] > 0.5f * DD_NEG) cm[0] += S.mux[u] * (double)aC[u];
-            block_sum_d<1>(cm, S.red);
-            const float shift = (float)(cm[0] / gm[5]);
+                if (aC[u] > 0.5f * DD_NEG) cmf[0] += S.muxf[u] * aC[u];
+            double cm[1];
+            block_sum_f<1>(cmf, cm, S.red);
+            const float shift = (float)cm[0] * (float)S.clx[14];
             for (int u = tid; u < nx; u += NT)
                 if (aC[u] > 0.5f * DD_NEG) aC[u] -= shift;
             if (tid == 0) {  // empty Anderson history; its weights mu / mu(X_J)
                 S.ctl[8] = 0;
-                S.ctl[9] = __float_as_int((float)(1.0 / gm[5]));
+                S.ctl[9] = __float_as_int((float)S.clx[14]);
             }
         }
         __syncthreads();
@@ -1445,10 +1462,9 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
         // ---- outputs of the solve: duals, objective --------------------------
         float* apo = A.alpha + (long long)A.amax * J;
         double eloc[1] = {0.0};
-        // exact displacement of the float origins (FP64) for the gauge conversion
-        const double dx1 = (double)(r0 - o1) + (double)uc1 - (double)vc1;
-        const double dx2 = (double)(c0 - o2) + (double)uc2 - (double)vc2;
-        const double hd = 0.5 * A.k2d * (dx1 * dx1 + dx2 * dx2);
+        // exact displacement of the float origins for the gauge conversion (FP64,
+        // computed once per cell with the gauge)
+        const double dx1 = S.clx[9], dx2 = S.clx[10], hd = S.clx[11];
         for (int u = tid; u < (lead ? nx : 0); u += NT) {  // X side: one CTA
             apo[u] = aC[u];
             const float lg = S.lgm[u];
@@ -1476,17 +1492,19 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
             }
         }
         eloc[0] += (double)ef;
-        for (int v1 = rlo + tid; v1 < rhi; v1 += NT) {  // rows: B1 and the axis-1 gauge terms
+        // rows: B1 and the axis-1 gauge terms; columns: B2 and the axis-2 ones
+        // (1 / l from the gauge's shared values: no FP64 division per row)
+        for (int v1 = rlo + tid; v1 < rhi; v1 += NT) {
             float rs = 0.f;
             for (int v2 = 0; v2 < w; ++v2) rs += A.comp_nu[comp + (long long)v1 * stride + v2];
             const double vb1 = v1 - (double)vc1;
-            eloc[0] += kLn2d * (S.B1[v1] - A.k2d * (1.0 / l1 - 1.0) * vb1 * vb1 - 2.0 * A.k2d * dx1 * vb1 + hd) * rs;
+            eloc[0] += kLn2d * (S.B1[v1] - A.k2d * (S.clx[12] - 1.0) * vb1 * vb1 - 2.0 * A.k2d * dx1 * vb1 + hd) * rs;
         }
-        for (int v2 = tid; v2 < w; v2 += NT) {  // columns: B2 and the axis-2 gauge terms
+        for (int v2 = tid; v2 < w; v2 += NT) {
             float cs = 0.f;
             for (int v1 = rlo; v1 < rhi; ++v1) cs += A.comp_nu[comp + (long long)v1 * stride + v2];
             const double vb2 = v2 - (double)vc2;
-            eloc[0] += kLn2d * (S.B2[v2] - A.k2d * (1.0 / l2 - 1.0) * vb2 * vb2 - 2.0 * A.k2d * dx2 * vb2) * cs;
+            eloc[0] += kLn2d * (S.B2[v2] - A.k2d * (S.clx[13] - 1.0) * vb2 * vb2 - 2.0 * A.k2d * dx2 * vb2) * cs;
         }
         block_sum_d<1>(eloc, S.red);
         if constexpr (CL > 1) cluster_sum_d<1>(eloc, S.clx, 8);
@@ -1810,8 +1828,15 @@ __device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float
     // the change of gauge of this cell's solve, and its kernel tables
     const float* gg = A.gauge + 8 * J;
     const float l1 = gg[2], l2 = gg[3], uc1 = gg[4], uc2 = gg[5], vc1 = gg[6], vc2 = gg[7];
+    // 1 / l as in the solve's tables (one FP64 division per cell, not per entry)
+    if (tid == 0) {
+        S.red[0] = 1.0 / (double)l1;
+        S.red[1] = 1.0 / (double)l2;
+    }
+    __syncthreads();
+    const double il1 = S.red[0], il2 = S.red[1];
     for (int v1 = tid; v1 < h; v1 += NT) {
-        const double tt = (v1 - (double)vc1) / (double)l1;
+        const double tt = (v1 - (double)vc1) * il1;
         const int us = min(hx - 1, max(0, (int)rint(tt + (double)uc1)));
         const double w0 = 2.0 * ((us - (double)uc1) - tt);
         const float w0f = (float)w0, kl = (float)(A.k2d * l1);
@@ -1821,7 +1846,7 @@ __device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float
         }
     }
     for (int v2 = tid; v2 < w; v2 += NT) {
-        const double tt = (v2 - (double)vc2) / (double)l2;
+        const double tt = (v2 - (double)vc2) * il2;
         const int us = min(wx - 1, max(0, (int)rint(tt + (double)uc2)));
         const double w0 = 2.0 * ((us - (double)uc2) - tt);
         const float w0f = (float)w0, kl = (float)(A.k2d * l2);
