@@ -183,6 +183,9 @@ typedef struct dd_flow_stats {
     double ms_exchange;  /* device time, exchange + re-box (ms)                   */
     double bytes_exchange; /* algorithmic bytes of the exchange: read every source
                               box with w_ij > 0, write the new boxes (4 B each)  */
+    double ms_host_step;   /* device time from the edge costs to the flow back on
+                              the device: the copies, the host solve and the
+                              handover to and from the host (ms)               */
 } dd_flow_stats;
 
 typedef struct dd_ctx dd_ctx;
@@ -263,6 +266,15 @@ int dd_flow_update(dd_ctx* ctx, dd_flow_stats* st);
  * (the state is still updated), else DD_OK; other errors stop at once.
  */
 int dd_step(dd_ctx* ctx, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf);
+
+/* Statistics of the last dd_step iteration (HOST structures, any may be NULL).
+ * A replayed iteration called with all three dd_step statistics pointers NULL
+ * reads nothing back from the device; this call reads them afterwards (the
+ * per-cell counts, errors and event times stay valid until the next
+ * half-iteration, flow update or plan change), so a caller can time iterations
+ * without the read-back and still inspect each one. DD_ERR_STATE if no
+ * dd_step iteration has run since the last such change. */
+int dd_step_stats(dd_ctx* ctx, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf);
 
 /* Basic-cell boxes of the current state: hdr (nbasic x 4), data (float64). */
 int dd_get_plan(dd_ctx* ctx, int32_t* hdr, double* data, size_t* count);

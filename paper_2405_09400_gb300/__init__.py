@@ -34,7 +34,7 @@ EXPORTS = [
     "dd_default_options", "dd_strerror", "dd_last_error", "dd_init", "dd_set_plan", "dd_set_eps", "dd_iterate", "dd_flow_update", "dd_step",
     "dd_get_plan", "dd_get_duals", "dd_get_composite", "dd_get_cell_stats", "dd_get_objective",
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
-    "dd_min_cost_flow", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
+    "dd_min_cost_flow", "dd_step_stats", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
     "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
     "dd_get_tuning", "dd_set_tuning", "dd_autotune", "dd_get_trace", "dd_probe_ex2_rate",
@@ -67,7 +67,7 @@ class dd_stats(C.Structure):
 class dd_flow_stats(C.Structure):
     _fields_ = [("value", C.c_double), ("nonzero", C.c_int32), ("pivots", C.c_int32), ("moved", C.c_double),
                 ("ms_costs", C.c_double), ("ms_solve", C.c_double), ("ms_exchange", C.c_double),
-                ("bytes_exchange", C.c_double)]
+                ("bytes_exchange", C.c_double), ("ms_host_step", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +128,7 @@ def load():
         "dd_get_flow": (C.c_int, [vp, _f64p, _f64p]),
         "dd_get_prebalance": (C.c_int, [vp, _i32p, _f64p, _szp]),
         "dd_min_cost_flow": (C.c_int, [C.c_int32, _i32p, _f64p, _f64p, _f64p, _f64p, _i32p]),
+        "dd_step_stats": (C.c_int, [vp, P(dd_stats), P(dd_stats), P(dd_flow_stats)]),
         "dd_get_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_get_graph_counters": (C.c_int, [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]),
         "dd_get_tuning": (C.c_int, [vp, P(dd_tuning)]),
@@ -293,6 +294,14 @@ def dd_step(ctx, n=1, stats=True):
     fd = sf.as_dict()
     fd["status"] = rc  # DD_ERR_MAXITER: some cell capped; DD_ERR_FLOW: stationary flow kept
     return sa.as_dict(), sb.as_dict(), fd
+
+
+def dd_step_stats(ctx):
+    """Statistics of the last dd_step iteration (read back now if the step was
+    replayed without them): (A stats, B stats, flow stats) dicts."""
+    sa, sb, sf = dd_stats(), dd_stats(), dd_flow_stats()
+    _check(load().dd_step_stats(ctx, C.byref(sa), C.byref(sb), C.byref(sf)), "dd_step_stats")
+    return sa.as_dict(), sb.as_dict(), sf.as_dict()
 
 
 def _boxes_call(fn, ctx, nhdr, *lead, out=None):
@@ -609,6 +618,9 @@ class DomDec:
 
     def step(self, n=1, stats=True):
         return dd_step(self.ctx, n, stats)
+
+    def step_stats(self):
+        return dd_step_stats(self.ctx)
 
     def plan(self):
         return arrays_to_boxes(*dd_get_plan(self.ctx, self.nbasic))

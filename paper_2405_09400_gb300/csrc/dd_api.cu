@@ -595,6 +595,7 @@ fail:
 
 int dd_set_plan(dd_ctx* c, const int32_t* hdr, const double* data, size_t n) {
     if (!c || !hdr || (!data && n)) return DD_ERR_ARG;
+    c->stats_pending = c->last_stats_valid = false;
     if (c->opt.flags & DD_FLAG_DEVICE_PTRS) {  // headers are laid out on the host
         std::vector<int32_t> hh(4 * (size_t)c->nb);
         CK(cudaMemcpyAsync(hh.data(), hdr, sizeof(int32_t) * hh.size(), cudaMemcpyDeviceToHost, c->stream));
@@ -896,6 +897,7 @@ extern "C" {
 
 int dd_set_eps(dd_ctx* c, double eps) {
     if (!c || !(eps > 0.0) || !std::isfinite(eps)) return DD_ERR_ARG;
+    c->stats_pending = c->last_stats_valid = false;
     const double f = c->eps / eps;
     for (int p = 0; p < 2; ++p) {
         DevPart& P = c->part[p];
@@ -913,6 +915,7 @@ int dd_set_eps(dd_ctx* c, double eps) {
 
 int dd_iterate(dd_ctx* c, int part, dd_stats* st) {
     if (!c) return DD_ERR_ARG;
+    c->stats_pending = c->last_stats_valid = false;
     if (part < -1 || part > 1) return DD_ERR_ARG;
     if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
     if (part == -1) part = c->last_part == 0 ? 1 : 0;
@@ -951,12 +954,14 @@ static void flow_stats(dd_ctx* c, double value, int32_t piv, double ms_solve, cu
     fs.ms_costs = event_ms(ev[0], ev[1]);
     fs.ms_solve = ms_solve;
     fs.ms_exchange = event_ms(ev[2], ev[3]);
+    fs.ms_host_step = event_ms(ev[1], ev[2]);
     c->last_flow = fs;
     if (st) *st = fs;
 }
 
 int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     if (!c) return DD_ERR_ARG;
+    c->stats_pending = c->last_stats_valid = false;
     if (!c->flow_ready) return DD_ERR_STATE;
     CK(cudaEventRecord(c->ev[3], c->stream));
     RET(launch_cbar(c));
@@ -1295,30 +1300,57 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
 
 }  // namespace
 
+// statistics of the last replayed graph iteration into the context's copies
+static int resolve_graph_stats(dd_ctx* c) {
+    int r1 = fill_stats(c, 0, &c->last_sa, 1, c->gev[0], c->gev[1], c->gev[2], c->gev[10]);
+    if (r1 != DD_OK && r1 != DD_ERR_MAXITER) return r1;
+    int r2 = fill_stats(c, 1, &c->last_sb, 2, c->gev[3], c->gev[4], c->gev[5], c->gev[11]);
+    if (r2 != DD_OK && r2 != DD_ERR_MAXITER) return r2;
+    flow_stats(c, c->g_value, c->g_piv, c->g_ms_solve, c->gev + 6, &c->last_sf);
+    c->stats_pending = false;
+    c->last_stats_valid = true;
+    return DD_OK;
+}
+
 int dd_step(dd_ctx* c, int n, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
     if (!c || n < 0) return DD_ERR_ARG;
     if (c->pool[c->cur] == nullptr) return DD_ERR_STATE;
+    // statistics go to the context's copies; the caller's structures get the last
+    // iteration's. Without any structure, a replayed iteration reads nothing back
+    // (dd_step_stats and dd_get_objective do it when asked).
+    const bool want = sa || sb || sf;
     int rc = DD_OK;
     for (int k = 0; k < n; ++k) {
         // the graph needs the sizes, flow solver and warm starts of one eager iteration
         const bool can_graph = !(c->opt.flags & DD_FLAG_NO_GRAPH) && c->mcf && c->seen.out > 0 &&
                                c->part[0].warm_valid && c->part[1].warm_valid;
         bool used_graph = false;
-        int r = can_graph ? step_graph(c, sa, sb, sf, &used_graph) : step_eager(c, sa, sb, sf);
+        int r = can_graph ? step_graph(c, &c->last_sa, &c->last_sb, &c->last_sf, &used_graph)
+                          : step_eager(c, &c->last_sa, &c->last_sb, &c->last_sf);
         if (r != DD_OK && r != DD_ERR_MAXITER && r != DD_ERR_FLOW) return r;
         if (r == DD_ERR_FLOW || (r == DD_ERR_MAXITER && rc == DD_OK)) rc = r;  // a failed flow solve first
-        if (used_graph) {
-            // statistics of the replayed iteration (objective / errors always, for
-            // dd_get_objective); capped cells (DD_ERR_MAXITER, already in r)
-            // neither end the statistics nor the remaining iterations
-            int r1 = fill_stats(c, 0, sa, 1, c->gev[0], c->gev[1], c->gev[2], c->gev[10]);
-            if (r1 != DD_OK && r1 != DD_ERR_MAXITER) return r1;
-            int r2 = fill_stats(c, 1, sb, 2, c->gev[3], c->gev[4], c->gev[5], c->gev[11]);
-            if (r2 != DD_OK && r2 != DD_ERR_MAXITER) return r2;
-            flow_stats(c, c->g_value, c->g_piv, c->g_ms_solve, c->gev + 6, sf);
-        }
+        c->stats_pending = used_graph;
+        c->last_stats_valid = !used_graph;
+        // capped cells (DD_ERR_MAXITER, already in r) neither end the statistics
+        // nor the remaining iterations
+        if (used_graph && want) RET(resolve_graph_stats(c));
+    }
+    if (n > 0 && want && c->last_stats_valid) {
+        if (sa) *sa = c->last_sa;
+        if (sb) *sb = c->last_sb;
+        if (sf) *sf = c->last_sf;
     }
     return rc;
+}
+
+int dd_step_stats(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf) {
+    if (!c) return DD_ERR_ARG;
+    if (c->stats_pending) RET(resolve_graph_stats(c));
+    if (!c->last_stats_valid) return DD_ERR_STATE;
+    if (sa) *sa = c->last_sa;
+    if (sb) *sb = c->last_sb;
+    if (sf) *sf = c->last_sf;
+    return DD_OK;
 }
 
 int dd_get_plan(dd_ctx* c, int32_t* hdr, double* data, size_t* count) {
@@ -1526,6 +1558,7 @@ int dd_get_cell_stats(dd_ctx* c, int part, int32_t* iters, double* err) {
 
 int dd_get_objective(dd_ctx* c, double* E, double* l1_x, double* l1_y) {
     if (!c) return DD_ERR_ARG;
+    if (c->stats_pending) RET(resolve_graph_stats(c));  // sets the objective of the last half-iteration
     if (E) *E = c->last_E;
     if (l1_x) *l1_x = c->last_l1x;
     if (l1_y) {

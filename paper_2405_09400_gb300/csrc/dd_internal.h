@@ -147,6 +147,12 @@ struct dd_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
     long long n_launch = 0, n_h2d = 0, n_d2h = 0;
     double last_E = 0, last_l1x = 0;
+    // statistics of the last dd_step iteration: filled at once, or (a graph replay
+    // called without statistics) read back later by dd_step_stats / dd_get_objective
+    dd_stats last_sa{}, last_sb{};
+    dd_flow_stats last_sf{};
+    bool last_stats_valid = false;
+    bool stats_pending = false;
 
     // CUDA-graph execution of dd_step: one graph per parity of `cur` at the start
     // of a hybrid iteration (the state buffers alternate), recaptured whenever a

@@ -265,6 +265,37 @@ def test_graph_step_is_bit_identical_to_step_by_step(dd, margin):
     e.close()
 
 
+def test_step_statistics_read_after_the_step(dd):
+    """dd_step without statistics reads nothing back after a replayed iteration;
+    dd_step_stats reads them afterwards. They equal those of the same iteration
+    run with statistics on an identical context (graph replays are
+    deterministic), and dd_get_objective resolves a pending read-back."""
+    mu, nu, eps, p = synth.workload("dd256", 0, N=64)
+    boxes = synth.boxes_from_coupling(mu.shape, 4, *synth.knothe_rosenblatt(mu, nu))
+    kw = dict(boxes=boxes, tol=1e-5, max_iter=20000, anderson=4)
+    g = dd.DomDec(mu, nu, eps, 4, **kw)
+    e = dd.DomDec(mu, nu, eps, 4, **kw)
+    keys = ("ncell", "iters_max", "n_maxiter", "n_stalled", "objective", "l1_x", "lse_terms", "stored_entries")
+    for it in range(5):
+        se = e.step(1)
+        rc = g.step(1, stats=False)
+        assert rc == 0
+        if it == 2:  # the objective first: it resolves the pending statistics
+            assert g.objective()[:2] == e.objective()[:2]
+        sa, sb, sf = g.step_stats()
+        for got, ref in ((sa, se[0]), (sb, se[1])):
+            for k in keys:
+                assert got[k] == ref[k], (it, k)
+        assert sf["value"] == se[2]["value"] and sf["pivots"] == se[2]["pivots"]
+        assert g.step_stats()[0]["objective"] == sa["objective"]  # idempotent
+    assert g.graph_counters()["replays"] >= 3
+    g.iterate(0)
+    with pytest.raises(RuntimeError):
+        g.step_stats()  # a half-iteration since the last dd_step
+    g.close()
+    e.close()
+
+
 def test_graph_step_with_capped_cells(dd):
     """Cells that stop at max_iter (DD_ERR_MAXITER) end neither a replayed
     iteration's statistics nor dd_step(n > 1): B's and the flow's statistics
