@@ -233,6 +233,7 @@ def run_ours(args):
                          weights=weights, **SOLVER)
         tctx.step(args.warmup + args.steps // 2, stats=False)
         tune = tctx.autotune()
+        tune = rerank_by_replay(tctx, tune)
         tctx.close()
     if world > 1:
         torch.distributed.barrier()
@@ -662,6 +663,45 @@ def large_configs(dd, weights, args):
     res["dd1024_prolongated"] = timed(g)
     g.close()
     return res
+
+
+# finalists of the replay ranking besides the autotuner's choice: the configurations
+# that did best in earlier full runs of this bench
+REPLAY_FINALISTS = (dict(threads=[512, 128, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=32),
+                    dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=0))
+
+
+def rerank_by_replay(g, tune, rounds=3, k=3):
+    """The library's autotuner times its trials step by step; the timed arms replay
+    CUDA graphs, where the size classes start together. Re-rank its choice and the
+    REPLAY_FINALISTS by the cell time of graph replays (interleaved rounds of k
+    steps each on the same trajectory, after one step that recaptures the graph)
+    and return the fastest, with the measured means."""
+    import numpy as np
+
+    cands = [dict(tune)] + [dict(t) for t in REPLAY_FINALISTS]
+    key = lambda t: (tuple(t["threads"]), t["small_area"], t["small_side"], t["cl_size"],
+                     t["cl_cells"] if t["cl_size"] > 1 else 0, t["sm_reserve"])
+    uniq = []
+    for t in cands:
+        if all(key(t) != key(u) for u in uniq):
+            uniq.append(t)
+    ms = [[] for _ in uniq]
+    for _ in range(rounds):
+        for i, t in enumerate(uniq):
+            g.set_tuning(list(t["threads"]), t["small_area"], t["small_side"], t["cl_size"], t["cl_cells"], t["sm_reserve"])
+            g.step(1, stats=False)
+            for _ in range(k):
+                g.step(1, stats=False)
+                sa, sb, _ = g.step_stats()
+                ms[i].append(sa["ms_cells"] + sb["ms_cells"])
+    means = [float(np.mean(m)) for m in ms]
+    best = dict(uniq[int(np.argmin(means))])
+    best.update(ms_default=tune.get("ms_default"), ms_best=tune.get("ms_best"), trials=tune.get("trials"),
+                autotuner_choice={k_: tune[k_] for k_ in ("threads", "small_area", "small_side", "cl_size", "cl_cells",
+                                                          "sm_reserve")},
+                replay_cell_ms={str(key(t)): round(v, 4) for t, v in zip(uniq, means)})
+    return best
 
 
 def box_sweep(tune, ex2_peak, K=50):
