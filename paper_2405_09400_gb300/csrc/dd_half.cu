@@ -1109,33 +1109,37 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                     }
                     const float ln[4] = {ln4.x, ln4.y, ln4.z, ln4.w};
                     const float bp[4] = {bp4.x, bp4.y, bp4.z, bp4.w};
-                    float m[4], sa[4];
+                    // one shift for the four columns (as in the 512-thread path below)
+                    float m0 = DD_NEG, sa[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        m[k] = ln[k] > 0.5f * DD_NEG ? ln[k] - bp[k] : 0.f;
+                        if (ln[k] > 0.5f * DD_NEG) m0 = fmaxf(m0, ln[k] - bp[k]);
                         sa[k] = 0.f;
                     }
+                    if (!(m0 > 0.5f * DD_NEG)) m0 = 0.f;
 #pragma unroll
                     for (int u1 = 0; u1 < 8; ++u1) {
-                        sa[0] += ex2f(T4[u1].x - kk[u1] - m[0]);
-                        sa[1] += ex2f(T4[u1].y - kk[u1] - m[1]);
-                        sa[2] += ex2f(T4[u1].z - kk[u1] - m[2]);
-                        sa[3] += ex2f(T4[u1].w - kk[u1] - m[3]);
+                        const float km = kk[u1] + m0;
+                        sa[0] += ex2f(T4[u1].x - km);
+                        sa[1] += ex2f(T4[u1].y - km);
+                        sa[2] += ex2f(T4[u1].z - km);
+                        sa[3] += ex2f(T4[u1].w - km);
                     }
                     float out[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int v2 = 4 * g4 + k;
                         if (v2 >= w || !(ln[k] > 0.5f * DD_NEG)) { out[k] = DD_NEG; continue; }
+                        float mk = m0;
                         if (!shift_ok(sa[k])) {
                             float mm = DD_NEG;
                             for (int u1 = 0; u1 < 8; ++u1) mm = fmaxf(mm, S.T[u1 * bs + v2] - tb[u1 * h]);
                             float ss = 0.f;
                             for (int u1 = 0; u1 < 8; ++u1) ss += ex2f(S.T[u1 * bs + v2] - tb[u1 * h] - mm);
-                            m[k] = mm;
+                            mk = mm;
                             sa[k] = ss;
                         }
-                        out[k] = ln[k] - (m[k] + lg2f(sa[k]));
+                        out[k] = ln[k] - (mk + lg2f(sa[k]));
                     }
                     reinterpret_cast<float4*>(b_p)[v1 * bq + g4] = make_float4(out[0], out[1], out[2], out[3]);
                 }
