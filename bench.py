@@ -233,8 +233,13 @@ def run_ours(args):
                          weights=weights, **SOLVER)
         tctx.step(args.warmup + args.steps // 2, stats=False)
         tune = tctx.autotune()
-        tune = rerank_by_replay(tctx, tune)
         tctx.close()
+
+        def make_ctx():
+            return dd.DomDec(mu, nu, eps, p["s"], boxes=boxes, tol=p["tol"], max_iter=20000, warm=dd.DD_WARM_MLP,
+                             weights=weights, **SOLVER)
+
+        tune = rerank_by_replay(make_ctx, tune, args.warmup + args.steps // 2)
     if world > 1:
         torch.distributed.barrier()
     none = None
@@ -666,35 +671,43 @@ def large_configs(dd, weights, args):
 
 
 # finalists of the replay ranking besides the autotuner's choice: the configurations
-# that did best in earlier full runs of this bench
-REPLAY_FINALISTS = (dict(threads=[512, 128, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=32),
-                    dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=0))
+# that did best in earlier runs of this bench (clusters of 2 or 4 CTAs for the 8 cells
+# of most expected work gave ~4 % less cell time than none in paired runs)
+REPLAY_FINALISTS = (dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=0),
+                    dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=2, cl_cells=8, sm_reserve=0),
+                    dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=4, cl_cells=8, sm_reserve=0),
+                    dict(threads=[512, 128, 512], small_area=768, small_side=48, cl_size=1, cl_cells=0, sm_reserve=32))
 
 
-def rerank_by_replay(g, tune, rounds=3, k=3):
+def rerank_by_replay(make_ctx, tune, n_pre, k=6):
     """The library's autotuner times its trials step by step; the timed arms replay
     CUDA graphs, where the size classes start together. Re-rank its choice and the
-    REPLAY_FINALISTS by the cell time of graph replays (interleaved rounds of k
-    steps each on the same trajectory, after one step that recaptures the graph)
-    and return the fastest, with the measured means."""
+    REPLAY_FINALISTS by the cell time of graph replays, paired: one context per
+    configuration from the same start, stepped in lockstep through n_pre steps and
+    then k measured steps (the per-step cost varies along the trajectory more than
+    between configurations). Returns the fastest, with the measured means."""
     import numpy as np
 
-    cands = [dict(tune)] + [dict(t) for t in REPLAY_FINALISTS]
     key = lambda t: (tuple(t["threads"]), t["small_area"], t["small_side"], t["cl_size"],
                      t["cl_cells"] if t["cl_size"] > 1 else 0, t["sm_reserve"])
     uniq = []
-    for t in cands:
+    for t in [dict(tune)] + [dict(t) for t in REPLAY_FINALISTS]:
         if all(key(t) != key(u) for u in uniq):
             uniq.append(t)
+    ctxs = []
+    for t in uniq:
+        g = make_ctx()
+        g.set_tuning(list(t["threads"]), t["small_area"], t["small_side"], t["cl_size"], t["cl_cells"], t["sm_reserve"])
+        ctxs.append(g)
     ms = [[] for _ in uniq]
-    for _ in range(rounds):
-        for i, t in enumerate(uniq):
-            g.set_tuning(list(t["threads"]), t["small_area"], t["small_side"], t["cl_size"], t["cl_cells"], t["sm_reserve"])
+    for step in range(n_pre + k):
+        for i, g in enumerate(ctxs):
             g.step(1, stats=False)
-            for _ in range(k):
-                g.step(1, stats=False)
+            if step >= n_pre:
                 sa, sb, _ = g.step_stats()
                 ms[i].append(sa["ms_cells"] + sb["ms_cells"])
+    for g in ctxs:
+        g.close()
     means = [float(np.mean(m)) for m in ms]
     best = dict(uniq[int(np.argmin(means))])
     best.update(ms_default=tune.get("ms_default"), ms_best=tune.get("ms_best"), trials=tune.get("trials"),
