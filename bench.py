@@ -64,9 +64,47 @@ def peaks():
         with open(MEASURED) as fh:
             d = json.load(fh)
         return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", SM_MAX_MHZ_DEFAULT)),
-                    src="measured")
+                    bf16_tflops=float(d.get("bf16_tflops", 1900.0)), src="measured")
     except Exception:
-        return dict(hbm_gbs=6800.0, sm_max_mhz=SM_MAX_MHZ_DEFAULT, src="fallback")
+        return dict(hbm_gbs=6800.0, sm_max_mhz=SM_MAX_MHZ_DEFAULT, bf16_tflops=1900.0, src="fallback")
+
+
+def network_forward(dd, pk, rows=(1089, 16641), reps=50):
+    """Forward pass of the warm-start network (four BF16 layer products) on
+    random inputs: CUDA-event time per pass on the tcgen05 kernel and on the
+    warp-level mma.sync kernel, for the cell counts of one 256^2 and one 1024^2
+    half-iteration."""
+    import torch
+
+    from paper_2405_09400_gb300 import warmstart as ws
+
+    flop_row = 2.0 * (dd.DD_MLP_NIN * dd.DD_MLP_NHID + 2 * dd.DD_MLP_NHID ** 2 + dd.DD_MLP_NHID * dd.DD_MLP_NOUT)
+    net = dd.MLP(max(rows))
+    net.set_params(ws.init_params(0))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    out = {"flop_per_row": flop_row, "peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " bf16 burst"}
+    st = torch.cuda.current_stream()
+    for M in rows:
+        x = torch.randn((M, dd.DD_MLP_NIN), generator=g, device="cuda").to(torch.bfloat16)
+        r = {}
+        for name, kind in (("umma", dd.DD_MLP_GEMM_UMMA), ("mma_sync", dd.DD_MLP_GEMM_MMA)):
+            net.set_gemm(kind)
+            for _ in range(5):
+                net.forward(x)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                net.forward(x)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            tf = flop_row * M / (ms * 1e-3) / 1e12
+            r[name] = {"ms": round(ms, 4), "tflops": round(tf, 2), "frac": round(tf / pk["bf16_tflops"], 4)}
+        out[str(M)] = r
+    net.set_gemm(dd.DD_MLP_GEMM_UMMA)
+    net.close()
+    return out
 
 
 def dist_env():
@@ -354,6 +392,7 @@ def run_ours(args):
 
     streams = {"k_c2b": stream_gbs(warm["c2b_ms"], warm["c2b_bytes"]),
                "k_exchange": stream_gbs(warm["xch_ms"], warm["xch_bytes"]), "peak_gbs": pk["hbm_gbs"]}
+    netfwd = None if args.no_micro else network_forward(dd, pk)
     ttt = None if args.no_ttt else time_to_tolerance(dd, mu, nu, eps, p, boxes, weights, tune, stream)
     cfgs = None if args.no_configs else large_configs(dd, weights, args)
 
@@ -415,6 +454,7 @@ def run_ours(args):
                       "ex2_per_clk_sm_at_max_clock": round(ex2_meas / (n_sm * sm_max * 1e6), 2)},
         "cell_lse_fixed_iterations": micro,
         "hbm_streams": streams,
+        "network_forward": netfwd,
         "time_to_tolerance": ttt,
         "configs": cfgs,
         "clocks": clocks,

@@ -485,8 +485,22 @@ int dd_mlp_set_params(dd_mlp* m, const float* params, int64_t n);
 int dd_mlp_get_params(dd_mlp* m, float* params, int64_t n);
 
 /* Forward pass of M <= max_batch rows: x_dev (M x NIN BF16, DEVICE) -> y_dev
- * (M x NOUT float, DEVICE). Asynchronous. */
+ * (M x NOUT float, DEVICE). Asynchronous. With the default DD_MLP_GEMM_UMMA the
+ * layer products run on the fifth-generation tensor cores (TMA loads,
+ * tcgen05.mma into tensor memory), which needs x_dev and y_dev 16-byte aligned
+ * (DD_ERR_ARG otherwise); a timed-out wait inside them is reported as
+ * DD_ERR_CUDA by the next call that synchronises (dd_mlp_get_params,
+ * dd_mlp_loss_grad, dd_mlp_train_step with a loss). */
 int dd_mlp_forward(dd_mlp* m, const uint16_t* x_dev, int32_t M, float* y_dev);
+
+/* Kernel of the forward layer products: DD_MLP_GEMM_UMMA (default; tcgen05.mma
+ * with TMEM accumulators, operands staged by TMA) or DD_MLP_GEMM_MMA (warp-level
+ * mma.sync, the kernel the backward pass uses; kept as the reference the first
+ * is tested against). Same arithmetic up to the FP32 summation order.
+ * Errors: DD_ERR_ARG (unknown kind). */
+#define DD_MLP_GEMM_UMMA 0
+#define DD_MLP_GEMM_MMA 1
+int dd_mlp_set_gemm(dd_mlp* m, int32_t kind);
 
 /* Loss L = (1/M) sum_rows sum_j w_j (y_j - t_j)^2 of M rows and its gradient:
  * x_dev (M x NIN BF16), t_dev (M x NOUT float), w_dev (NOUT float), all DEVICE;

@@ -28,6 +28,7 @@ DD_WARM_PREV, DD_WARM_COLD, DD_WARM_AFFINE, DD_WARM_MLP = 0, 1, 2, 3
 DD_FLAG_KEEP_PREBALANCE, DD_FLAG_COLLECT, DD_FLAG_NO_GRAPH, DD_FLAG_TRACE = 1, 2, 4, 8
 DD_FLAG_MLP_EVERY_SOLVE, DD_FLAG_DEVICE_PTRS, DD_FLAG_FUSED_C2B = 16, 32, 64
 DD_MLP_NIN, DD_MLP_NHID, DD_MLP_NOUT, DD_MLP_NPARAMS = 336, 256, 320, 300096
+DD_MLP_GEMM_UMMA, DD_MLP_GEMM_MMA = 0, 1
 DD_STATIC_MAX_PIXELS, DD_STATIC_MAX_CELLS = 1024 * 1024, 65536
 
 EXPORTS = [
@@ -36,7 +37,7 @@ EXPORTS = [
     "dd_get_partition", "dd_get_neighbours", "dd_get_basic_moments", "dd_get_flow", "dd_get_prebalance",
     "dd_min_cost_flow", "dd_step_stats", "dd_get_counters", "dd_debug_cell", "dd_l1_y_error_static", "dd_destroy",
     "dd_mlp_create", "dd_mlp_set_params", "dd_mlp_get_params", "dd_mlp_forward", "dd_mlp_loss_grad",
-    "dd_mlp_train_step", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
+    "dd_mlp_train_step", "dd_mlp_set_gemm", "dd_mlp_destroy", "dd_set_warmstart_weights", "dd_collect_cells", "dd_get_graph_counters",
     "dd_get_tuning", "dd_set_tuning", "dd_autotune", "dd_get_trace", "dd_probe_ex2_rate",
 ]
 
@@ -145,6 +146,7 @@ def load():
         "dd_mlp_forward": (C.c_int, [vp, vp, C.c_int32, vp]),
         "dd_mlp_loss_grad": (C.c_int, [vp, vp, vp, vp, C.c_int32, _f64p, P(C.c_float)]),
         "dd_mlp_train_step": (C.c_int, [vp, vp, vp, vp, C.c_int32, vp, C.c_float, _f64p]),
+        "dd_mlp_set_gemm": (C.c_int, [vp, C.c_int32]),
         "dd_mlp_destroy": (None, [vp]),
         "dd_set_warmstart_weights": (C.c_int, [vp, P(C.c_float), C.c_int64]),
         "dd_collect_cells": (C.c_int, [vp, C.c_int, vp, vp, C.c_int32, _i32p]),
@@ -532,6 +534,11 @@ class MLP:
         p = np.zeros(DD_MLP_NPARAMS, dtype=np.float32)
         _check(load().dd_mlp_get_params(self.h, _ptr(p, P(C.c_float)), p.size), "dd_mlp_get_params")
         return p
+
+    def set_gemm(self, kind):
+        """Kernel of the forward layer products: DD_MLP_GEMM_UMMA (tcgen05, the
+        default) or DD_MLP_GEMM_MMA (warp-level mma.sync)."""
+        _check(load().dd_mlp_set_gemm(self.h, int(kind)), "dd_mlp_set_gemm")
 
     def forward(self, x):
         import torch

@@ -492,7 +492,8 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
         TRY(dmalloc(&c->d_tot, PT_N));
         if (cudaMallocHost((void**)&c->h_tot, sizeof(long long) * PT_N) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
         TRY(dmalloc(&c->d_queue, 4));
-        TRY(dmalloc(&c->d_status, 24));
+        TRY(dmalloc(&c->d_status, kStatusInts));
+        if (cudaMemsetAsync(c->d_status, 0, kStatusInts * sizeof(int), c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         TRY(dmalloc(&c->d_guard, 4));
         if (cudaMemsetAsync(c->d_guard, 0, 4 * sizeof(int), c->stream) != cudaSuccess) { rc = DD_ERR_CUDA; goto fail; }
         if (cudaMallocHost((void**)&c->h_guard, 4 * sizeof(int)) != cudaSuccess) { rc = DD_ERR_OOM; goto fail; }
@@ -679,6 +680,14 @@ static int cluster_cap(dd_ctx* c) {
     return std::max(0, std::min(c->tune.cl_cells, c->nsm / half_cluster_size(c->tune.cl_size)));
 }
 
+// the network's GEMM flag as read back from d_status[kStatusMlp]: DD_ERR_CUDA
+// (and the flag cleared) if one of its waits timed out
+static int mlp_status(dd_ctx* c, int flag) {
+    if (!flag) return DD_OK;
+    CK(cudaMemsetAsync(c->d_status + kStatusMlp, 0, sizeof(int), c->stream));
+    return dd_record_cuda_error(cudaErrorLaunchTimeout, "warm-start network (tensor-memory GEMM): a wait timed out");
+}
+
 int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
     DevPart& P = c->part[part];
     c->fuse_c2b = with_c2b;  // without k_c2b after them the solves must not mark cells done
@@ -690,12 +699,15 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         RET(launch_feat(c, part));
         c->n_launch += 1;
         if (mlp_active(c, part)) {
-            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
+            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream, c->d_status + kStatusMlp));
             c->n_launch += 4;
         }
     }
+    int mlp_flag = 0;
+    if (mlp_active(c, part)) RET(d2h(&mlp_flag, c->d_status + kStatusMlp, 1, c->stream));
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    RET(mlp_status(c, mlp_flag));
     const long long comp = c->h_tot[PT_COMP], outn = c->h_tot[PT_OUT];
     if (outn > (long long)INT32_MAX || comp > (long long)INT32_MAX * 4LL) return DD_ERR_POOL;
     if (P.comp_cap < (size_t)comp || !P.comp_b) RET(ensure_comp(c, part, (size_t)comp));
@@ -1102,7 +1114,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
         RET(launch_feat(c, part));
         c->n_launch += 1;
         if (mlp_active(c, part)) {
-            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream));
+            RET(mlp_forward_dev(c->mlp, c->d_feat, P.ncell, c->d_pred, c->stream, c->d_status + kStatusMlp));
             c->n_launch += 4;
         }
     }
@@ -1242,10 +1254,11 @@ int step_graph(dd_ctx* c, dd_stats* sa, dd_stats* sb, dd_flow_stats* sf, bool* u
     c->n_launch += G.launches;
     c->n_replay += 1;
     CK(cudaStreamSynchronize(c->stream));
-    int status[24];
+    int status[kStatusInts];
     RET(d2h(c->h_guard, c->d_guard, 1, c->stream));
-    RET(d2h(status, c->d_status, 24, c->stream));
+    RET(d2h(status, c->d_status, kStatusInts, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    RET(mlp_status(c, status[kStatusMlp]));
     const int guard = *c->h_guard;
     if (guard == 0) {
         c->cur = 1 - parity;

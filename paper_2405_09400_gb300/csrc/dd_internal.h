@@ -66,6 +66,8 @@ struct DevPart {
     std::vector<int32_t> h_xblk;     // host copy
 };
 
+constexpr int kStatusMlp = 24, kStatusInts = 25;  // d_status: flag index, length
+
 struct dd_ctx {
     int N1 = 0, N2 = 0, s = 0, n1 = 0, n2 = 0, nb = 0, amax = 0;
     double h = 0, eps = 0;
@@ -104,7 +106,8 @@ struct dd_ctx {
     long long* h_tot = nullptr;  // pinned
     int* d_queue = nullptr;
     int* d_status = nullptr;   // 3 slices of 8 (eager, graph A, graph B): [0] maxiter, [1] empty cell,
-                               // [2] shared memory too small, [3] stalled
+                               // [2] shared memory too small, [3] stalled; then [kStatusMlp]: a
+                               // wait of the network's tensor-core GEMM timed out
 
     // prebalance copy
     float* d_pre = nullptr;
@@ -255,7 +258,7 @@ int half_occupancy(int threads, size_t smem);
 int launch_feat(dd_ctx* c, int part);
 int launch_collect(dd_ctx* c, int n, const int32_t* idx, uint16_t* feat, float* targ);
 // dd_mlp.cu
-int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st);
+int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st, int* err);
 // dd_flow.cu
 int launch_cbar(dd_ctx* c);
 int launch_plan_exchange(dd_ctx* c, int stage = 0);

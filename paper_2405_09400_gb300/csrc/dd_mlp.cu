@@ -6,15 +6,20 @@
 //
 // Every layer product is one tensor-core GEMM kernel,
 //   C(m, n) = sum_k A(m, k) B(n, k),
-// with A and B read as BF16 in either orientation (K contiguous or not), tiles
-// of 64 x 64 x 32 staged in shared memory and mma.sync m16n8k16 BF16 -> FP32,
-// and a fused epilogue (bias, SiLU, SiLU' of the next layer down, FP32/BF16
-// stores). The forward pass of one layer, the two gradient products of the
-// backward pass (dW = dZ^T H, dH = dZ W) and the bias sums are all of that form.
+// with a fused epilogue (bias, SiLU, SiLU' of the next layer down, FP32/BF16
+// stores). The forward products (A = activations, B = weights, both K
+// contiguous) run on k_gemm_tc: TMA loads into 128-byte-swizzled shared memory,
+// tcgen05.mma with the accumulator in tensor memory, tcgen05.ld epilogue. The
+// two gradient products of the backward pass (dW = dZ^T H, dH = dZ W), whose
+// operands are not all K-contiguous, run on k_gemm: tiles of 64 x 64 x 32 staged
+// in shared memory and warp-level mma.sync m16n8k16 BF16 -> FP32, which also
+// serves as the reference the forward kernel is tested against
+// (dd_mlp_set_gemm).
 //
 // Parameters: one flat FP32 vector (master copy), W_1 (256 x 336, row n = the
 // weights into output n), b_1, W_2, b_2, W_3, b_3, W_4 (320 x 256), b_4; a BF16
 // copy of the same vector feeds the GEMMs; biases are read in FP32.
+#include <cuda.h>  // CUtensorMap and its enums (declarations only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -175,6 +180,282 @@ int gemm(const GemmArgs& g, bool ak, bool bk, cudaStream_t st) {
     return launch_status("mlp gemm");
 }
 
+// ---------------------------------------------------------------------------
+// Forward products on the fifth-generation tensor cores: C = A B^T with A
+// (M x K) and B (N x K) both K-contiguous BF16, FP32 accumulation in tensor
+// memory. One CTA of 4 warps computes a 128 x 64 tile of C:
+//  * thread 0 issues one TMA load (cp.async.bulk.tensor, 128-byte swizzle,
+//    zero fill outside the matrix) per 64-wide K block of A and of B, all at
+//    once (K <= 384: the whole K extent is resident, 24 KB per block), each
+//    block on its own mbarrier;
+//  * as each block lands, the same thread issues four tcgen05.mma (M = 128,
+//    N = 64, K = 16) into a 64-column TMEM accumulator, then tcgen05.commit
+//    arrives on a completion mbarrier;
+//  * every warp reads its 32 TMEM lanes (rows) back with tcgen05.ld and applies
+//    the epilogue (bias, SiLU, FP32 / BF16 stores) in registers.
+// Every wait is bounded (~1 s of %globaltimer): on a timeout the kernel sets
+// *err, waits (bounded) for its copies still in flight, frees its TMEM and
+// returns without storing.
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64, TC_KB_MAX = 6;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2, TC_B_BYTES = TC_BN * TC_BK * 2;
+constexpr int TC_TMEM_COLS = 64;  // FP32 accumulator columns (power of two >= 32)
+// instruction descriptor of kind::f16: D FP32 (bits 4-5), A and B BF16 (bits
+// 7-9, 10-12), both K-major (bits 15, 16 zero), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                              ((uint32_t)(TC_BM >> 4) << 24);
+
+constexpr size_t tc_smem_bytes(int nkb) { return 1024 + (size_t)nkb * (TC_A_BYTES + TC_B_BYTES) + 8 * (TC_KB_MAX + 1) + 16; }
+
+struct TcArgs {
+    int M, N, nkb, epi;
+    const float* bias;
+    float* outf;
+    __nv_bfloat16* outh;
+    long long ldc;
+    int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of the barrier; false after ~1 s without it
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1 (bits 46-48)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcArgs g) {
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN, nkb = g.nkb;
+    // tiles on 1024-byte boundaries (the swizzle pattern repeats every 8 rows of 128 bytes)
+    const uint32_t raw = smem_addr(tc_smem), base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base, sB = sA + nkb * TC_A_BYTES, sBar = sB + nkb * TC_B_BYTES, sDone = sBar + 8 * TC_KB_MAX;
+    uint8_t* tail = tc_smem + (sDone + 8 - raw);
+    volatile uint32_t* slot = reinterpret_cast<volatile uint32_t*>(tail);  // TMEM address from tcgen05.alloc
+    volatile int* fail = reinterpret_cast<volatile int*>(tail + 4);
+    if (tid == 0) {
+        for (int kb = 0; kb < nkb; ++kb) mbar_init(sBar + 8 * kb, 1);
+        mbar_init(sDone, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr((const void*)slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    int issued = 0;  // K blocks whose loads thread 0 issued
+    if (tid == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            mbar_expect_tx(sBar + 8 * kb, TC_A_BYTES + TC_B_BYTES);
+            tma_load_2d(sA + kb * TC_A_BYTES, &tA, sBar + 8 * kb, kb * TC_BK, m0);
+            tma_load_2d(sB + kb * TC_B_BYTES, &tB, sBar + 8 * kb, kb * TC_BK, n0);
+            issued = kb + 1;
+        }
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            ok = mbar_wait(sBar + 8 * kb, 0);
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < TC_BK / 16; ++j)  // K steps of 16: 32 bytes along the swizzled row
+                umma_bf16(tmem, sw128_desc(sA + kb * TC_A_BYTES + 32 * j), sw128_desc(sB + kb * TC_B_BYTES + 32 * j),
+                          (kb | j) != 0);
+        }
+        if (ok) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sDone)
+                         : "memory");
+        } else {
+            *fail = 1;
+            atomicExch(g.err, 1);
+            mbar_arrive(sDone);
+        }
+    }
+    __syncwarp();
+    const bool done = mbar_wait(sDone, 0);
+    tc_fence_after();
+    if (!done) {
+        if (lane == 0) atomicExch(g.err, 1);
+    } else if (!*fail) {
+        // rows of this warp: TMEM lanes 32 warp .. 32 warp + 31
+        const int m = m0 + 32 * warp + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+        for (int c = 0; c < TC_BN / 16; ++c) {
+            uint32_t r[16];
+            tmem_ld16(trow + 16 * c, r);
+            const int nb = n0 + 16 * c;
+            if (m >= g.M || nb >= g.N) continue;
+            float v[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                v[e] = __uint_as_float(r[e]);
+                if (g.epi == EPI_BIAS_F32 || g.epi == EPI_BIAS_SILU) v[e] += g.bias[min(nb + e, g.N - 1)];
+            }
+            const long long o = (long long)m * g.ldc + nb;
+            if (nb + 16 <= g.N) {
+                if (g.outf) {
+                    float4* q = reinterpret_cast<float4*>(g.outf + o);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                }
+                if (g.outh) {
+                    uint32_t h[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float a = g.epi == EPI_BIAS_SILU ? silu_f(v[2 * e]) : v[2 * e];
+                        const float b = g.epi == EPI_BIAS_SILU ? silu_f(v[2 * e + 1]) : v[2 * e + 1];
+                        const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+                        h[e] = *reinterpret_cast<const uint32_t*>(&p);
+                    }
+                    uint4* q = reinterpret_cast<uint4*>(g.outh + o);
+                    q[0] = make_uint4(h[0], h[1], h[2], h[3]);
+                    q[1] = make_uint4(h[4], h[5], h[6], h[7]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    if (nb + e >= g.N) continue;
+                    if (g.outf) g.outf[o + e] = v[e];
+                    if (g.outh) g.outh[o + e] = __float2bfloat16_rn(g.epi == EPI_BIAS_SILU ? silu_f(v[e]) : v[e]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *fail)  // copies still in flight land before the CTA's shared memory is released
+        for (int kb = 0; kb < issued; ++kb) mbar_wait(sBar + 8 * kb, 0);
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+TensorMapEncodeFn tensor_map_encoder() {
+    static TensorMapEncodeFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<TensorMapEncodeFn>(p);
+    }();
+    return fn;
+}
+
+// rows x K BF16 matrix, row stride ld elements, read in boxes of 64 (K) x box_rows
+bool encode_kmajor(CUtensorMap* map, const __nv_bfloat16* p, int rows, int K, long long ld, int box_rows) {
+    const TensorMapEncodeFn fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// whether C = A B^T (both K-contiguous) can run on k_gemm_tc: the whole K extent
+// resident, TMA-legal bases and row strides, vector-aligned epilogue stores
+bool tc_eligible(const GemmArgs& g) {
+    return g.M > 0 && g.N > 0 && g.K > 0 && g.K <= TC_KB_MAX * TC_BK && g.epi != EPI_DSILU && aligned16(g.A) &&
+           aligned16(g.B) && g.lda % 8 == 0 && g.ldb % 8 == 0 && g.lda >= g.K && g.ldb >= g.K && g.ldc >= g.N && g.ldc % 8 == 0 &&
+           (!g.outf || aligned16(g.outf)) && (!g.outh || aligned16(g.outh));
+}
+
+int gemm_tc(const GemmArgs& g, int* err, cudaStream_t st) {
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_KB_MAX)) ==
+               cudaSuccess;
+    }();
+    if (!attr) return dd_record_cuda_error(cudaGetLastError(), "mlp gemm (tensor memory): shared-memory attribute");
+    CUtensorMap ta, tb;
+    if (!encode_kmajor(&ta, g.A, g.M, g.K, g.lda, TC_BM) || !encode_kmajor(&tb, g.B, g.N, g.K, g.ldb, TC_BN))
+        return dd_record_cuda_error(cudaErrorInvalidValue, "mlp gemm (tensor memory): tensor map");
+    TcArgs a{};
+    a.M = g.M; a.N = g.N; a.nkb = (g.K + TC_BK - 1) / TC_BK; a.epi = g.epi;
+    a.bias = g.bias; a.outf = g.outf; a.outh = g.outh; a.ldc = g.ldc; a.err = err;
+    dim3 grid((g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM);
+    k_gemm_tc<<<grid, 128, tc_smem_bytes(a.nkb), st>>>(ta, tb, a);
+    return launch_status("mlp gemm (tensor memory)");
+}
+
 // rows idx[b] of the data set into the batch buffers
 __global__ void k_gather(int B, const int32_t* __restrict__ idx, const uint4* __restrict__ X, const uint4* __restrict__ T,
                          uint4* __restrict__ Xb, uint4* __restrict__ Tb) {
@@ -269,13 +550,15 @@ struct dd_mlp {
     __nv_bfloat16* dzh[2] = {};   // and BF16
     double* dloss = nullptr;
     double* hloss = nullptr;      // pinned
+    int* d_err = nullptr;         // set by k_gemm_tc when a wait timed out
+    int gemm_kind = DD_MLP_GEMM_UMMA;
 };
 
 namespace {
 
 void mlp_free(dd_mlp* m) {
     void* ptrs[] = {m->p, m->p16, m->g, m->am, m->av, m->xb, m->tb, m->y, m->dzf[0], m->dzf[1], m->dzh[0], m->dzh[1],
-                    m->dloss};
+                    m->dloss, m->d_err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int l = 0; l < kL; ++l) {
@@ -286,8 +569,8 @@ void mlp_free(dd_mlp* m) {
 }
 
 // forward pass of the rows x (M x NIN, BF16) into y (M x NOUT, FP32); keeps the
-// hidden pre-activations when `train`
-int forward(dd_mlp* m, const __nv_bfloat16* x, int M, float* y, bool train) {
+// hidden pre-activations when `train`; a timed-out wait of k_gemm_tc sets *err
+int forward(dd_mlp* m, const __nv_bfloat16* x, int M, float* y, bool train, int* err) {
     const __nv_bfloat16* in = x;
     for (int l = 0; l < kL; ++l) {
         GemmArgs g{};
@@ -304,7 +587,10 @@ int forward(dd_mlp* m, const __nv_bfloat16* x, int M, float* y, bool train) {
             g.epi = EPI_BIAS_F32;
             g.outf = y;
         }
-        int r = gemm(g, true, true, m->stream);
+        int r;
+        if (m->gemm_kind == DD_MLP_GEMM_MMA) r = gemm(g, true, true, m->stream);
+        else if (tc_eligible(g)) r = gemm_tc(g, err, m->stream);
+        else r = DD_ERR_ARG;  // a base or row stride the tensor maps cannot take
         if (r != DD_OK) return r;
         if (l < kL - 1) in = m->hh[l + 1];
     }
@@ -314,7 +600,7 @@ int forward(dd_mlp* m, const __nv_bfloat16* x, int M, float* y, bool train) {
 // loss and gradient of the batch (x, t) already in place; gradient into m->g
 int backward(dd_mlp* m, const __nv_bfloat16* x, const float* t, const float* wt, int M) {
     const cudaStream_t st = m->stream;
-    int r = forward(m, x, M, m->y, true);
+    int r = forward(m, x, M, m->y, true, m->d_err);
     if (r != DD_OK) return r;
     if (cudaMemsetAsync(m->dloss, 0, sizeof(double), st) != cudaSuccess) return dd_record_cuda_error(cudaGetLastError(), "mlp memset");
     k_loss<<<2 * m->nsm, 256, 0, st>>>(M, m->y, t, wt, m->dzf[0], m->dzh[0], m->dloss);
@@ -346,14 +632,25 @@ int backward(dd_mlp* m, const __nv_bfloat16* x, const float* t, const float* wt,
     return DD_OK;
 }
 
+// after a synchronisation of the network's stream: DD_ERR_CUDA (and the flag
+// cleared) if a k_gemm_tc wait timed out since the last check
+int take_err(dd_mlp* m) {
+    int e = 0;
+    if (cudaMemcpy(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return dd_record_cuda_error(cudaGetLastError(), "mlp error flag");
+    if (!e) return DD_OK;
+    cudaMemset(m->d_err, 0, sizeof(int));
+    return dd_record_cuda_error(cudaErrorLaunchTimeout, "mlp gemm (tensor memory): a wait timed out");
+}
+
 }  // namespace
 
-int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st) {
+int mlp_forward_dev(dd_mlp* m, const uint16_t* x, int M, float* y, cudaStream_t st, int* err) {
     if (!m || M < 0 || M > m->max_batch) return DD_ERR_ARG;
     if (M == 0) return DD_OK;
     cudaStream_t keep = m->stream;
     m->stream = st;
-    int r = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), M, y, false);
+    int r = forward(m, reinterpret_cast<const __nv_bfloat16*>(x), M, y, false, err ? err : m->d_err);
     m->stream = keep;
     return r;
 }
@@ -375,7 +672,7 @@ int dd_mlp_create(int32_t max_batch, void* stream, dd_mlp** out) {
               cudaMalloc(&m->g, P * 4) == cudaSuccess && cudaMalloc(&m->am, P * 4) == cudaSuccess &&
               cudaMalloc(&m->av, P * 4) == cudaSuccess && cudaMalloc(&m->xb, B * DD_MLP_NIN * 2) == cudaSuccess &&
               cudaMalloc(&m->tb, B * DD_MLP_NOUT * 4) == cudaSuccess && cudaMalloc(&m->y, B * DD_MLP_NOUT * 4) == cudaSuccess &&
-              cudaMalloc(&m->dloss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&m->dloss, sizeof(double)) == cudaSuccess && cudaMalloc(&m->d_err, sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&m->hloss, sizeof(double)) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k)
         ok = cudaMalloc(&m->dzf[k], B * DD_MLP_NOUT * 4) == cudaSuccess &&
@@ -392,6 +689,7 @@ int dd_mlp_create(int32_t max_batch, void* stream, dd_mlp** out) {
     cudaMemsetAsync(m->p16, 0, P * 2, m->stream);
     cudaMemsetAsync(m->am, 0, P * 4, m->stream);
     cudaMemsetAsync(m->av, 0, P * 4, m->stream);
+    cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
         dd_record_cuda_error(cudaGetLastError(), "dd_mlp_create");
         mlp_free(m);
@@ -421,13 +719,19 @@ int dd_mlp_get_params(dd_mlp* m, float* params, int64_t n) {
     if (cudaMemcpyAsync(params, m->p, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
         cudaStreamSynchronize(m->stream) != cudaSuccess)
         return dd_record_cuda_error(cudaGetLastError(), "dd_mlp_get_params");
+    return take_err(m);
+}
+
+int dd_mlp_set_gemm(dd_mlp* m, int32_t kind) {
+    if (!m || (kind != DD_MLP_GEMM_UMMA && kind != DD_MLP_GEMM_MMA)) return DD_ERR_ARG;
+    m->gemm_kind = kind;
     return DD_OK;
 }
 
 int dd_mlp_forward(dd_mlp* m, const uint16_t* x_dev, int32_t M, float* y_dev) {
     if (!m || M < 0 || M > m->max_batch || (M > 0 && (!x_dev || !y_dev))) return DD_ERR_ARG;
     if (M == 0) return DD_OK;
-    return forward(m, reinterpret_cast<const __nv_bfloat16*>(x_dev), M, y_dev, false);
+    return forward(m, reinterpret_cast<const __nv_bfloat16*>(x_dev), M, y_dev, false, m->d_err);
 }
 
 int dd_mlp_loss_grad(dd_mlp* m, const uint16_t* x_dev, const float* t_dev, const float* w_dev, int32_t M,
@@ -441,6 +745,7 @@ int dd_mlp_loss_grad(dd_mlp* m, const uint16_t* x_dev, const float* t_dev, const
         cudaMemcpyAsync(grad_host, m->g, (size_t)DD_MLP_NPARAMS * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
         return dd_record_cuda_error(cudaGetLastError(), "dd_mlp_loss_grad");
     if (cudaStreamSynchronize(m->stream) != cudaSuccess) return dd_record_cuda_error(cudaGetLastError(), "dd_mlp_loss_grad");
+    if ((r = take_err(m)) != DD_OK) return r;
     if (loss) *loss = *m->hloss;
     return DD_OK;
 }
@@ -463,6 +768,7 @@ int dd_mlp_train_step(dd_mlp* m, const uint16_t* x_all, const float* t_all, cons
         if (cudaMemcpyAsync(m->hloss, m->dloss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return dd_record_cuda_error(cudaGetLastError(), "dd_mlp_train_step");
+        if ((r = take_err(m)) != DD_OK) return r;
         *loss = *m->hloss;
     }
     return DD_OK;

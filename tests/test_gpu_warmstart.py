@@ -91,6 +91,41 @@ def test_mlp_forward_and_gradient_match_fp64_reference(dd, M):
     net.close()
 
 
+@pytest.mark.parametrize("M", [1, 128, 129, 1089, 4500])
+def test_mlp_forward_tcgen05_matches_mma_sync(dd, M):
+    """The forward layer products on the tcgen05 kernel (TMA-staged operands,
+    TMEM accumulator; one 128 x 64 tile per CTA, ragged M tails zero-filled by
+    the tensor maps) against the warp-level mma.sync kernel on the same BF16
+    weights and inputs. Both sum the same BF16 products in FP32 and round each
+    hidden layer to BF16, so they differ only through the summation order and
+    the few BF16 roundings it flips: relative Frobenius norm <= 2e-3, and a
+    layout or descriptor error would give an O(1) difference."""
+    p = rand_net(5)
+    rng = np.random.default_rng(20 + M)
+    X = bf16(rng.normal(0, 1, (M, 336))).cuda()
+    net = dd.MLP(M)
+    net.set_params(p)
+    y_tc = net.forward(X).cpu().numpy()
+    net.set_gemm(dd.DD_MLP_GEMM_MMA)
+    y_ref = net.forward(X).cpu().numpy()
+    net.set_gemm(dd.DD_MLP_GEMM_UMMA)
+    y_tc2 = net.forward(X).cpu().numpy()
+    net.get_params()  # synchronises and reports a timed-out wait, if any
+    net.close()
+    assert np.isfinite(y_tc).all()
+    assert np.array_equal(y_tc, y_tc2)  # deterministic
+    assert rel(y_tc, y_ref) <= 2e-3
+    yref64, _ = omlp.forward(p.astype(np.float64), X.cpu().float().numpy().astype(np.float64))
+    assert rel(y_tc, yref64) <= 1e-2
+
+
+def test_mlp_set_gemm_rejects_unknown_kind(dd):
+    net = dd.MLP(8)
+    with pytest.raises(dd.DDError):
+        net.set_gemm(7)
+    net.close()
+
+
 def test_adam_first_step(dd):
     import torch
 
