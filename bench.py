@@ -46,8 +46,8 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # below (the step-kernel summary under profiles/). The bytes are those the cells read and
 # write (the composite boxes, the basic boxes, the duals), which the CTA sizes do
 # not change; the line names the configuration of the capture
-TRAFFIC_CELL_REGION = 18.35e6
-TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=1, sm_reserve=0)
+TRAFFIC_CELL_REGION = 18.59e6
+TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=2, cl_cells=8, sm_reserve=0)
 # cell solver of every arm: Anderson acceleration of the X-dual iteration
 # (memory 4; same fixed point, same stop; with it, eps-scaling inside each solve
 # no longer pays and is off)
@@ -443,10 +443,11 @@ def run_ours(args):
                      "achieved": round(achieved / 1e12, 4), "peak": round(ex2_peak / 1e12, 4), "unit": "Texp2/s",
                      "frac": round(achieved / ex2_peak, 5),
                      "traffic": TRAFFIC_CELL_REGION,
-                     "traffic_src": "ncu dram__bytes of one capture at threads %s, small %d/%d, no clusters "
-                                    "(profiles/, dd256 step kernels)" % (TRAFFIC_TUNING["threads"],
-                                                                         TRAFFIC_TUNING["small_area"],
-                                                                         TRAFFIC_TUNING["small_side"]),
+                     "traffic_src": "ncu dram__bytes of one capture at threads %s, small %d/%d, clusters of %d "
+                                    "for %d cells (profiles/, dd256 step kernels)" % (
+                                        TRAFFIC_TUNING["threads"], TRAFFIC_TUNING["small_area"],
+                                        TRAFFIC_TUNING["small_side"], TRAFFIC_TUNING["cl_size"],
+                                        TRAFFIC_TUNING["cl_cells"]),
                      "kernel_ms_mean": round(k_ms, 4),
                      "work_per_launch": k_terms,
                      "peak_src": f"{n_sm} SMs x {EX2_PER_CLK_SM} ex2/clk x {sm_max:.0f} MHz"},

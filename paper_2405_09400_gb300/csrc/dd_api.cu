@@ -996,7 +996,7 @@ int dd_flow_update(dd_ctx* c, dd_flow_stats* st) {
     RET(h2d(c->d_w, c->h_w, 5 * (size_t)c->nb, c->stream));
     CK(cudaEventRecord(c->ev[5], c->stream));
     RET(launch_plan_exchange(c));
-    c->n_launch += 1;
+    c->n_launch += 2;
     RET(d2h(c->h_tot, c->d_tot, PT_N, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (c->h_tot[PT_OUT] > (long long)INT32_MAX) return DD_ERR_POOL;
@@ -1192,7 +1192,7 @@ int enqueue_flow_graph(dd_ctx* c) {
     CK(cudaMemsetAsync(c->d_status + 5, 0, sizeof(int), c->stream));
     RET(launch_plan_exchange(c, 3));
     RET(launch_exchange(c));
-    c->n_launch += 3;
+    c->n_launch += 4;  // k_cbar, k_xbox, k_plan_exchange, k_exchange
     CK(cudaEventRecordWithFlags(c->gev[9], c->stream, cudaEventRecordExternal));
     c->cur = 1 - c->cur;
     return DD_OK;

@@ -247,6 +247,30 @@ def test_flow_update_matches_oracle_on_gpu_state(dd):
     g.close()
 
 
+def test_flow_update_large_union_boxes_match_oracle(dd):
+    """The exchange when the union box of a target exceeds the 4096 entries its
+    kernel keeps in shared memory (the second gather for the compact write): a
+    wide blur (eps = 0.5) keeps every basic box at the whole 72 x 72 grid."""
+    N, s = 72, 4
+    mu, nu, _, _ = synth.workload("dd32", 0, N=N)
+    geom = Geometry(N, N, s)
+    m = geom.basic_masses(mu)
+    nbr = geom.neighbours()
+    g = dd.DomDec(mu, nu, 0.5, s, tol=1e-6)
+    g.iterate(0)
+    g.iterate(1)
+    state = as_boxes(g.plan())
+    assert max(b.a.size for b in state) > 4096
+    g.flow_update()
+    _, w = g.flow()
+    new_ref = exchange(geom, state, w, nbr, m, 1e-15)
+    new = as_boxes(g.plan())
+    assert max(b.a.size for b in new) > 4096
+    assert plan_l1(new, new_ref, mu.shape) <= 1e-6
+    assert np.allclose([b.a.sum() for b in new], m, rtol=1e-6)
+    g.close()
+
+
 @pytest.mark.parametrize("m,small_threads", [(8, 64), (32, 64), (32, None), (128, None)])
 def test_cell_lse_box_sweep_cells_match_oracle(dd, m, small_threads):
     """The cell-LSE microbenchmark's inputs (synth.cell_lse_sweep: (2048/m)^2
