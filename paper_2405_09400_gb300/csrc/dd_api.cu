@@ -294,7 +294,7 @@ void dd_destroy(dd_ctx* c) {
         DevPart& P = c->part[p];
         dfree(P.members); dfree(P.xblk); dfree(P.mJ); dfree(P.chdr); dfree(P.alpha); dfree(P.gauge);
         dfree(P.budget);
-        dfree(P.iters); dfree(P.err); dfree(P.Ecell); dfree(P.order); dfree(P.comp_b); dfree(P.comp_nu);
+        dfree(P.iters); dfree(P.err); dfree(P.Ecell); dfree(P.order); dfree(P.c2b_order); dfree(P.comp_b); dfree(P.comp_nu);
         dfree(c->pool[p]); dfree(c->bhdr[p]);
     }
     dfree(c->d_bmom); dfree(c->d_tot); dfree(c->d_queue); dfree(c->d_status); dfree(c->d_pre);
@@ -478,6 +478,7 @@ int dd_init(const double* mu, const double* nu, const dd_grid* grid, double eps,
             TRY(dmalloc(&P.xblk, xblk.size())); TRY(h2d(P.xblk, xblk.data(), xblk.size(), c->stream));
             TRY(dmalloc(&P.mJ, mJ.size())); TRY(h2d(P.mJ, mJ.data(), mJ.size(), c->stream));
             TRY(dmalloc(&P.order, order.size())); TRY(h2d(P.order, order.data(), order.size(), c->stream));
+            TRY(dmalloc(&P.c2b_order, order.size())); TRY(h2d(P.c2b_order, order.data(), order.size(), c->stream));
             TRY(dmalloc(&P.chdr, (size_t)CH_N * P.ncell));
             TRY(dmalloc(&P.alpha, (size_t)c->amax * P.ncell));
             TRY(dmalloc(&P.gauge, 8 * (size_t)P.ncell));
@@ -824,6 +825,14 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         order.insert(order.end(), cls_cells[k].begin(), cls_cells[k].end());
     }
     RET(h2d(P.order, order.data(), order.size(), c->stream));
+    // k_c2b: the cluster class, then the large, global-scratch and small classes
+    // (each by descending work key), so the longest CompositeToBasic cells start first
+    {
+        std::vector<int32_t> c2b;
+        c2b.reserve(order.size());
+        for (int k : {3, 0, 2, 1}) c2b.insert(c2b.end(), cls_cells[k].begin(), cls_cells[k].end());
+        RET(h2d(P.c2b_order, c2b.data(), c2b.size(), c->stream));
+    }
     if (gtot > 0) RET(ensure_floats(c, &c->d_gscr, &c->gscr_cap, (size_t)gtot));
     if (!cls_cells[2].empty() || !cls_cells[3].empty()) RET(h2d(c->d_goff, goff.data(), goff.size(), c->stream));
     size_t smem_c[4] = {0, 0, 0, 0};
@@ -898,7 +907,7 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b) {
         const size_t sm = c2b_smem_bytes(c, dall[1], dall[2]);
         if (sm > (size_t)half_kernel_max_smem()) return DD_ERR_POOL;
         CK(cudaEventRecord(c->ev[7], c->stream));
-        RET(launch_c2b(c, part, dall, sm));
+        RET(launch_c2b(c, part, dall, sm, P.c2b_order, nullptr));
         c->n_launch += 1;
     }
     CK(cudaEventRecord(c->ev[2], c->stream));
@@ -1150,7 +1159,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
                            cudaMemcpyDeviceToDevice, c->stream));
     const long long dc[3] = {0, g.h2, g.w2};
     CK(cudaEventRecordWithFlags(c->gev[10 + (stage - 1)], c->stream, cudaEventRecordExternal));
-    RET(launch_c2b(c, part, dc, g.smem_c2b));
+    RET(launch_c2b(c, part, dc, g.smem_c2b, c->d_corder[part], c->d_ccount[part]));
     c->n_launch += 1;
     CK(cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal));
     c->cur = 1 - c->cur;

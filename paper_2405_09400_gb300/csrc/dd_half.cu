@@ -289,6 +289,11 @@ struct HalfArgs {
     // per cell: 1 once its solving CTA has also done CompositeToBasic (k_sink sets,
     // k_c2b skips such a cell and clears the mark), or null: k_sink leaves it to k_c2b
     int* fused;
+    // k_c2b's cell of CTA b: c2b_order[b] (c2b_count null), or from the class lists
+    // of k_classify (c2b_count its three counts: the cluster list at 2 ncell first,
+    // then the large list at 0 and the small list at ncell); null: cell b
+    const int32_t* c2b_order;
+    const int* c2b_count;
     // gluing edge candidates: per basic cell and pixel, mass r and mean displacement
     // d (2) of the Gibbs cell plan (nb x s^2 x 3, FP64), or null (product candidates)
     double* pmom;
@@ -2178,7 +2183,16 @@ __device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float
 
 __global__ void __launch_bounds__(kC2bThreads, 3) k_c2b(HalfArgs A) {
     extern __shared__ __align__(16) char smem_raw[];
-    const int J = blockIdx.x;
+    int J = blockIdx.x;  // cells with the most work first, where an order is given
+    if (A.c2b_order) {
+        if (A.c2b_count) {
+            const int b = blockIdx.x, n2 = A.c2b_count[2], n0 = A.c2b_count[0];
+            J = b < n2 ? A.c2b_order[2LL * A.ncell + b]
+                       : (b - n2 < n0 ? A.c2b_order[b - n2] : A.c2b_order[(long long)A.ncell + (b - n2 - n0)]);
+        } else {
+            J = A.c2b_order[blockIdx.x];
+        }
+    }
     // cells whose solving CTA already did this (k_sink with A.fused): clear the
     // mark for the next half-iteration and leave
     if (A.fused) {
@@ -2368,6 +2382,7 @@ HalfArgs make_args(dd_ctx* c, int part) {
     A.N1 = c->N1; A.N2 = c->N2; A.s = c->s; A.ncell = P.ncell; A.amax = c->amax;
     A.k2 = c->k2; A.k2d = c->k2d; A.eps = c->eps; A.h2 = c->h * c->h;
     A.members = P.members; A.xblk = P.xblk; A.mJ = P.mJ; A.order = P.order;
+    A.c2b_order = nullptr; A.c2b_count = nullptr;
     A.bhdr_in = c->bhdr[c->cur]; A.pool_in = c->pool[c->cur];
     A.bhdr_out = c->bhdr[1 - c->cur]; A.pool_out = c->pool[1 - c->cur];
     A.chdr = P.chdr; A.comp_b = P.comp_b; A.comp_nu = P.comp_nu;
@@ -2496,9 +2511,11 @@ int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, in
     return launch_status(__func__);
 }
 
-int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem) {
+int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem, const int32_t* order, const int* count) {
     RET_IF(set_attrs());
     HalfArgs A = make_args(c, part);
+    A.c2b_order = order;
+    A.c2b_count = count;
     A.smaxA = (int)dims[0];
     A.smaxH = (int)dims[1];
     A.smaxW = (int)dims[2];

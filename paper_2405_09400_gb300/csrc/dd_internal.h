@@ -56,6 +56,7 @@ struct DevPart {
     double* err = nullptr;       // ncell
     double* Ecell = nullptr;     // ncell
     int32_t* order = nullptr;    // ncell, processing order
+    int32_t* c2b_order = nullptr;  // ncell, k_c2b order of the step-by-step path (largest work first)
     float* comp_b = nullptr;     // composite pool: b' (centred base-2 dual, absorbs log2 nu_J)
     float* comp_nu = nullptr;    // composite pool: nu_J
     size_t comp_cap = 0;
@@ -229,7 +230,7 @@ int half_iteration_eager(dd_ctx* c, int part, bool with_c2b);
 size_t half_smem_bytes(dd_ctx* c, long long maxarea, long long maxh, long long maxw);
 int half_kernel_max_smem();
 size_t c2b_smem_bytes(dd_ctx* c, long long maxh, long long maxw);
-int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem);
+int launch_c2b(dd_ctx* c, int part, const long long dims[3], size_t smem, const int32_t* order, const int* count);
 // the cell kernel on thread-block clusters of `cl` (2 or 4) CTAs, one cluster per
 // cell, nclusters clusters; box arrays of cells with goff >= 0 in global scratch
 int launch_half_cluster(dd_ctx* c, int part, const int32_t* order, int ncell, int* queue, const long long dims[3],
