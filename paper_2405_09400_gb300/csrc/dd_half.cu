@@ -743,7 +743,7 @@ __host__ __device__ __forceinline__ long long c2b_cell_floats(int s, int hx, int
     return 2LL * (wx / s) * hx * w + (pmom ? 2LL * h * wx : 0);
 }
 
-__device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float* aC);
+__device__ void c2b_cell_fused(const HalfArgs& A, int J, const C2bSmem& S, const float* aC);
 
 // The cell solver. CL = 1: one CTA per cell. CL > 1: the CL CTAs of a thread-block
 // cluster solve one cell together (for the few largest cells, which would
@@ -1565,7 +1565,7 @@ __global__ void __launch_bounds__(NTB, 768 / NTB) k_sink(HalfArgs A) {
                 C.E = C.L + (long long)h * wx;
                 C.coef = S.coef;
                 C.ctl = S.ctl;
-                c2b_cell(A, J, C, aC);
+                c2b_cell_fused(A, J, C, aC);
                 if (tid == 0) {
                     A.fused[J] = 1;
                     if (A.trace) {
@@ -1823,7 +1823,7 @@ constexpr int kC2bBatch = 8;      // compaction strides per barrier pair
 // the change of gauge of its solve (A.gauge, read after a block barrier). The
 // member shares are ratios of partial sums over X, so the Y dual is not needed.
 // Every return is uniform over the CTA.
-__device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float* aC) {
+__device__ __forceinline__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float* aC) {
     const int tid = threadIdx.x, NT = blockDim.x;
     const int s = A.s;
     const int32_t* xb = A.xblk + XB_N * J;
@@ -2075,44 +2075,46 @@ __device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) momf[k] = 0.f;
-    // the member values of the thread's next entry are loaded one entry ahead
-    // (an entry's values are only read and written by its own thread)
-    auto vals_at = [&](int v, float (&x)[4]) {
-        const int v1 = v / w;
-        const long long off = slot0 + (long long)v1 * stride + (v - v1 * w);
+    // the member values of four entries of the thread are loaded together (an
+    // entry's values are only read and written by its own thread)
+    constexpr int U5 = 2;
+    for (int v0 = tid; v0 < nA; v0 += U5 * NT) {
+        float vals[U5][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = (v < nA && k < nmem) ? A.pool_out[off + k * area] : 0.f;
-    };
-    float vnext[4];
-    vals_at(tid, vnext);
-    for (int v = tid; v < nA; v += NT) {
-        const int v1 = v / w, v2 = v - v1 * w;
-        const long long off = slot0 + (long long)v1 * stride + v2;
-        float vals[4];
+        for (int u = 0; u < U5; ++u) {
+            const int v = v0 + u * NT, v1 = v / w;
+            const long long off = slot0 + (long long)v1 * stride + (v - v1 * w);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) vals[k] = vnext[k];
-        vals_at(v + NT, vnext);
-        if (A.pre) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < nmem) A.pre[off + k * area] = vals[k];
+            for (int k = 0; k < 4; ++k) vals[u][k] = (v < nA && k < nmem) ? A.pool_out[off + k * area] : 0.f;
         }
-        const float y1 = (float)(v1 - bc1), y2 = (float)(v2 - bc2);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j >= nmem) break;
-            float nv = 0.f;
+        for (int u = 0; u < U5; ++u) {
+            const int v = v0 + u * NT;
+            if (v >= nA) break;
+            const int v1 = v / w, v2 = v - v1 * w;
+            const long long off = slot0 + (long long)v1 * stride + v2;
+            if (A.pre) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) nv += cf[j][k] * vals[k];
-            if (!(nv >= A.trunc)) nv = 0.f;
-            A.pool_out[off + j * area] = nv;
-            if (nv > 0.f) {
-                bb[j][0] = min(bb[j][0], v1); bb[j][1] = max(bb[j][1], v1);
-                bb[j][2] = min(bb[j][2], v2); bb[j][3] = max(bb[j][3], v2);
-                momf[4 * j + 0] += nv;
-                momf[4 * j + 1] += nv * y1;
-                momf[4 * j + 2] += nv * y2;
-                momf[4 * j + 3] += nv * (y1 * y1 + y2 * y2);
+                for (int k = 0; k < 4; ++k)
+                    if (k < nmem) A.pre[off + k * area] = vals[u][k];
+            }
+            const float y1 = (float)(v1 - bc1), y2 = (float)(v2 - bc2);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nmem) break;
+                float nv = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nv += cf[j][k] * vals[u][k];
+                if (!(nv >= A.trunc)) nv = 0.f;
+                A.pool_out[off + j * area] = nv;
+                if (nv > 0.f) {
+                    bb[j][0] = min(bb[j][0], v1); bb[j][1] = max(bb[j][1], v1);
+                    bb[j][2] = min(bb[j][2], v2); bb[j][3] = max(bb[j][3], v2);
+                    momf[4 * j + 0] += nv;
+                    momf[4 * j + 1] += nv * y1;
+                    momf[4 * j + 2] += nv * y2;
+                    momf[4 * j + 3] += nv * (y1 * y1 + y2 * y2);
+                }
             }
         }
     }
@@ -2129,56 +2131,91 @@ __device__ void c2b_cell(const HalfArgs& A, int J, const C2bSmem& S, const float
 
     // ---- compaction in place (dst index never exceeds src index) --------
     // Each member is rescaled to its basic mass m_i after truncation, so that
-    // the removed entries do not leave later cell problems unbalanced.
-    for (int k = 0; k < nmem; ++k) {
+    // the removed entries do not leave later cell problems unbalanced. Thread k
+    // does member k's scale, header and moments; then one pass compacts all
+    // members (their slot regions are disjoint).
+    if (tid < nmem) {
+        const int k = tid;
         const int rlo = S.ctl[4 + 4 * k + 0], rhi = S.ctl[4 + 4 * k + 1];
         const int clo = S.ctl[4 + 4 * k + 2], chi = S.ctl[4 + 4 * k + 3];
         const bool empty = rhi < 0;
         const int hh = empty ? 0 : rhi - rlo + 1, ww = empty ? 0 : chi - clo + 1;
-        const int st = (ww + 3) & ~3;
-        const double msum = mom[4 * k + 0];
-        const float fsc = msum > 0.0 ? (float)(A.m[mem[k]] / msum) : 1.f;
-        float* sl = A.pool_out + slot0 + k * area;
-        const int n = hh * st;
-        // kC2bBatch strides of NT entries per barrier pair: every read of a batch
-        // precedes its writes, and later batches read only beyond its last write
-        for (int base = 0; base < n; base += kC2bBatch * NT) {
-            float val[kC2bBatch];
-#pragma unroll
-            for (int j = 0; j < kC2bBatch; ++j) {
-                const int dI = base + j * NT + tid;
-                val[j] = 0.f;
-                if (dI < n) {
-                    const int rr = dI / st, cc = dI - rr * st;
-                    if (cc < ww) val[j] = sl[(long long)(rlo + rr) * stride + clo + cc] * fsc;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < kC2bBatch; ++j) {
-                const int dI = base + j * NT + tid;
-                if (dI < n) sl[dI] = val[j];
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            const int i = mem[k];
-            int32_t* bo = A.bhdr_out + BH_N * i;
-            bo[BH_O1] = empty ? 0 : o1 + rlo;
-            bo[BH_O2] = empty ? 0 : o2 + clo;
-            bo[BH_H] = hh;
-            bo[BH_W] = ww;
-            bo[BH_STRIDE] = st;
-            bo[BH_START] = (int32_t)(slot0 + k * area);
-            double* bm = A.bmom + BM_N * i;
-            const double ms = mom[4 * k + 0];
-            const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
-            bm[BM_MASS] = ms > 0 ? A.m[i] : 0.0;
-            bm[BM_Y1] = o1 + bc1 + m1;
-            bm[BM_Y2] = o2 + bc2 + m2;
-            bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
-        }
+        const int i = mem[k];
+        const double ms = mom[4 * k + 0], mi = A.m[i];
+        S.coef[k] = ms > 0.0 ? (float)(mi / ms) : 1.f;
+        int32_t* bo = A.bhdr_out + BH_N * i;
+        bo[BH_O1] = empty ? 0 : o1 + rlo;
+        bo[BH_O2] = empty ? 0 : o2 + clo;
+        bo[BH_H] = hh;
+        bo[BH_W] = ww;
+        bo[BH_STRIDE] = (ww + 3) & ~3;
+        bo[BH_START] = (int32_t)(slot0 + k * area);
+        double* bm = A.bmom + BM_N * i;
+        const double m1 = ms > 0 ? mom[4 * k + 1] / ms : 0.0, m2 = ms > 0 ? mom[4 * k + 2] / ms : 0.0;
+        bm[BM_MASS] = ms > 0 ? mi : 0.0;
+        bm[BM_Y1] = o1 + bc1 + m1;
+        bm[BM_Y2] = o2 + bc2 + m2;
+        bm[BM_VAR] = ms > 0 ? mom[4 * k + 3] / ms - m1 * m1 - m2 * m2 : 0.0;
     }
+    __syncthreads();
+    int nk[4], pre[5], rlo[4], clo[4], wk[4], stk[4];
+    float fsc[4];
+    pre[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool live = k < nmem && S.ctl[4 + 4 * k + 1] >= 0;
+        rlo[k] = S.ctl[4 + 4 * k + 0];
+        clo[k] = S.ctl[4 + 4 * k + 2];
+        const int hh = live ? S.ctl[4 + 4 * k + 1] - rlo[k] + 1 : 0;
+        wk[k] = live ? S.ctl[4 + 4 * k + 3] - clo[k] + 1 : 0;
+        stk[k] = (wk[k] + 3) & ~3;
+        nk[k] = hh * stk[k];
+        fsc[k] = k < nmem ? S.coef[k] : 1.f;
+        pre[k + 1] = pre[k] + nk[k];
+    }
+    const int ntot = pre[4];
+    // kC2bBatch strides of NT entries per barrier pair: every read of a batch
+    // precedes its writes, and later batches read only beyond a member's last write
+    for (int base = 0; base < ntot; base += kC2bBatch * NT) {
+        float val[kC2bBatch];
+        int kd[kC2bBatch];
+#pragma unroll
+        for (int j = 0; j < kC2bBatch; ++j) {
+            const int dI = base + j * NT + tid;
+            val[j] = 0.f;
+            kd[j] = -1;
+            if (dI < ntot) {
+                const int k = (dI >= pre[1]) + (dI >= pre[2]) + (dI >= pre[3]);
+                int p0 = pre[0], st = stk[0], wwk = wk[0], r0k = rlo[0], c0k = clo[0];
+                float f = fsc[0];
+#pragma unroll
+                for (int t = 1; t < 4; ++t)
+                    if (k == t) { p0 = pre[t]; st = stk[t]; wwk = wk[t]; r0k = rlo[t]; c0k = clo[t]; f = fsc[t]; }
+                const int d = dI - p0, rr = d / st, cc = d - rr * st;
+                const float* sl = A.pool_out + slot0 + (long long)k * area;
+                if (cc < wwk) val[j] = sl[(long long)(r0k + rr) * stride + c0k + cc] * f;
+                kd[j] = k;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kC2bBatch; ++j) {
+            const int dI = base + j * NT + tid;
+            if (kd[j] < 0) continue;
+            int p0 = pre[0];
+#pragma unroll
+            for (int t = 1; t < 4; ++t)
+                if (kd[j] == t) p0 = pre[t];
+            A.pool_out[slot0 + (long long)kd[j] * area + (dI - p0)] = val[j];
+        }
+        __syncthreads();
+    }
+}
+
+// the solving CTA's call (k_sink with A.fused): not inlined, so that the
+// solver's register allocation does not carry CompositeToBasic's
+__device__ __noinline__ void c2b_cell_fused(const HalfArgs& A, int J, const C2bSmem& S, const float* aC) {
+    c2b_cell(A, J, C2bSmem(S), aC);
 }
 
 __global__ void __launch_bounds__(kC2bThreads, 3) k_c2b(HalfArgs A) {
