@@ -46,7 +46,7 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # below (the step-kernel summary under profiles/). The bytes are those the cells read and
 # write (the composite boxes, the basic boxes, the duals), which the CTA sizes do
 # not change; the line names the configuration of the capture
-TRAFFIC_CELL_REGION = 18.59e6
+TRAFFIC_CELL_REGION = 19.06e6
 TRAFFIC_TUNING = dict(threads=[512, 64, 512], small_area=768, small_side=48, cl_size=2, cl_cells=8, sm_reserve=0)
 # cell solver of every arm: Anderson acceleration of the X-dual iteration
 # (memory 4; same fixed point, same stop; with it, eps-scaling inside each solve
