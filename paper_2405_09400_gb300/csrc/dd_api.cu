@@ -1117,6 +1117,12 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     cudaEvent_t* ev = c->gev + 3 * (stage - 1);
     // timing events inside a captured graph must be event-record nodes
     CK(cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal));
+    // the stop budgets depend only on the previous solves' iteration counts: they
+    // are computed on a side stream while the boxes are planned and classified
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side3, c->ev_fork, 0));
+    RET(launch_budget(c, part, c->side3));
+    CK(cudaEventRecord(c->ev_join3, c->side3));
     RET(launch_plan_half(c, part));
     c->n_launch += 1;
     if (mlp_active(c, part) || (c->opt.flags & DD_FLAG_COLLECT)) {
@@ -1130,7 +1136,7 @@ int enqueue_half_graph(dd_ctx* c, int part, int stage) {
     CK(cudaMemsetAsync(c->d_queue, 0, sizeof(int) * 4, c->stream));
     CK(cudaMemsetAsync(c->d_status + 8 * stage, 0, sizeof(int) * 8, c->stream));
     RET(launch_classify(c, part, stage));
-    RET(launch_budget(c, part));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join3, 0));
     c->n_launch += 2;
     CK(cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal));
     CK(cudaEventRecord(c->ev_fork, c->stream));

@@ -2368,10 +2368,10 @@ __global__ void k_rescale_alpha(int ncell, int amax, int N2, const int32_t* __re
 
 }  // namespace
 
-int launch_budget(dd_ctx* c, int part) {
+int launch_budget(dd_ctx* c, int part, cudaStream_t st) {
     const DevPart& P = c->part[part];
     if (P.ncell <= 0) return DD_OK;
-    k_budget<<<1, 1024, 0, c->stream>>>(P.ncell, P.mJ, P.iters, P.warm_valid ? 1 : 0, c->opt.tol, c->opt.tol_share,
+    k_budget<<<1, 1024, 0, st ? st : c->stream>>>(P.ncell, P.mJ, P.iters, P.warm_valid ? 1 : 0, c->opt.tol, c->opt.tol_share,
                                         P.mbar, c->opt.tol_gamma, P.budget);
     return launch_status(__func__);
 }

@@ -252,7 +252,7 @@ inline bool mlp_keeps_old(const dd_ctx* c) {
 int launch_pack_plan(dd_ctx* c, int dst, bool validate);
 int launch_unpack_plan(dd_ctx* c);
 // per-cell stop budgets of the next solves of `part` into P.budget (dd_options tol_share, tol_gamma)
-int launch_budget(dd_ctx* c, int part);
+int launch_budget(dd_ctx* c, int part, cudaStream_t st = nullptr);
 // stored X duals of a partition: a <- log2 mu + f (a - log2 mu) (eps change by 1 / f)
 int launch_rescale_alpha(dd_ctx* c, int part, double f);
 int half_occupancy(int threads, size_t smem);
