@@ -188,16 +188,26 @@ __global__ void k_plan_half(int ncell, const int32_t* __restrict__ members, cons
     __syncthreads();
     long long sa = 0, so = 0, ma = 0, mh = 0, mw = 0;
     for (int J = c0; J < c1; ++J) {
-        int lo1 = INT32_MAX, lo2 = INT32_MAX, hi1 = INT32_MIN, hi2 = INT32_MIN;
+        // the four members' header loads are independent: issue them together
+        int mi[4], bo1[4], bo2[4], bh[4], bw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mi[k] = members[4 * J + k];
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
-            int i = members[4 * J + k];
-            if (i < 0) continue;
-            const int32_t* b = bhdr + (size_t)BH_N * i;
-            if (b[BH_H] <= 0 || b[BH_W] <= 0) continue;
-            lo1 = min(lo1, b[BH_O1]);
-            lo2 = min(lo2, b[BH_O2]);
-            hi1 = max(hi1, b[BH_O1] + b[BH_H]);
-            hi2 = max(hi2, b[BH_O2] + b[BH_W]);
+            const int32_t* b = bhdr + (size_t)BH_N * (mi[k] < 0 ? 0 : mi[k]);
+            bo1[k] = mi[k] < 0 ? 0 : b[BH_O1];
+            bo2[k] = mi[k] < 0 ? 0 : b[BH_O2];
+            bh[k] = mi[k] < 0 ? 0 : b[BH_H];
+            bw[k] = mi[k] < 0 ? 0 : b[BH_W];
+        }
+        int lo1 = INT32_MAX, lo2 = INT32_MAX, hi1 = INT32_MIN, hi2 = INT32_MIN;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (bh[k] <= 0 || bw[k] <= 0) continue;
+            lo1 = min(lo1, bo1[k]);
+            lo2 = min(lo2, bo2[k]);
+            hi1 = max(hi1, bo1[k] + bh[k]);
+            hi2 = max(hi2, bo2[k] + bw[k]);
         }
         int h = 0, w = 0;
         if (hi1 > lo1) { h = hi1 - lo1; w = hi2 - lo2; } else { lo1 = lo2 = 0; }
